@@ -1,0 +1,314 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each checks a moment identity,
+a conservation law, a symmetry, a textbook limit (G = 0 BGK hydrodynamics) or
+a number printed in the paper.  Together they are chosen so that a dropped
+term, a wrong sign, a wrong weight or a swapped species in the oracle's step
+fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import analytic
+from paper_1601_00918_gb300 import workloads as wl
+
+T0 = 1.0 / 3.0
+G_REPULSIVE = -1.79
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def moments(fi):
+    c = np.stack([oracle.CX, oracle.CY])
+    m0 = fi.sum()
+    m1 = c @ fi
+    m2 = np.einsum("ai,bi,i->ab", c, c, fi)
+    m3_xxy = np.sum(oracle.CX ** 2 * oracle.CY * fi)
+    m3_xyy = np.sum(oracle.CX * oracle.CY ** 2 * fi)
+    return m0, m1, m2, m3_xxy, m3_xyy
+
+
+# ----------------------------------------------------------------------------
+# Eq. (feq): velocity moments of the equilibrium
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("rho,ux,uy", [(1.0, 0.0, 0.0), (0.7, 0.12, -0.05), (0.03, -0.2, 0.17),
+                                       (1.3, 0.3, 0.25)])
+def test_feq_moments(order, rho, ux, uy):
+    """Mass, momentum and momentum flux of Eq. (feq) are rho, rho u and
+    rho u u + T0 rho I exactly on D2Q9 (its fourth-moment tensor is
+    isotropic).  The cubic terms of Eq. (feq) are the third Hermite term:
+    they add rho u_x^2 u_y to the xxy moment, which D2Q9 resolves."""
+    f = oracle.feq(rho, ux, uy, order)
+    m0, m1, m2, xxy, xyy = moments(f)
+    u = np.array([ux, uy])
+    assert m0 == pytest.approx(rho, rel=1e-14, abs=1e-15)
+    np.testing.assert_allclose(m1, rho * u, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(m2, rho * np.outer(u, u) + T0 * rho * np.eye(2), rtol=1e-13,
+                               atol=1e-15)
+    cubic = 1.0 if order == 3 else 0.0
+    assert xxy == pytest.approx(rho * (T0 * uy + cubic * ux * ux * uy), rel=1e-12, abs=1e-15)
+    assert xyy == pytest.approx(rho * (T0 * ux + cubic * ux * uy * uy), rel=1e-12, abs=1e-15)
+
+
+def test_feq_rest_is_weights():
+    """At u = 0 the equilibrium is rho w_i with the D2Q9 weights 4/9, 1/9, 1/36."""
+    f = oracle.feq(0.8, 0.0, 0.0)
+    np.testing.assert_allclose(np.sort(f), np.sort(0.8 * np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)),
+                               rtol=1e-15)
+
+
+# ----------------------------------------------------------------------------
+# conservation laws
+# ----------------------------------------------------------------------------
+def _channel_problem(g=(2e-5, 0.0), tau=(1.0, 0.8), rho_wall=(0.6, 0.1)):
+    mask = wl.sinusoidal_channel(64, 30, 9.0, 4.0, 32.0)
+    rho = wl.slug(64, 30, 16.0, 48.0)
+    P = oracle.Problem(mask, tau=tau, G=G_REPULSIVE, rho_wall=rho_wall, g=g,
+                       periodic=(True, False))
+    return P, rho
+
+
+def test_mass_conservation_with_walls():
+    """Streaming with halfway bounce-back and the collision both conserve each
+    species' mass exactly (up to FP64 rounding), with walls, wall potentials,
+    interaction and body force all active."""
+    P, rho = _channel_problem()
+    f = P.init(rho)
+    m0 = f.reshape(2, -1).sum(axis=1)
+    f, hist = P.run(f, 400, history=True)
+    m1 = f.reshape(2, -1).sum(axis=1)
+    np.testing.assert_allclose(m1, m0, rtol=1e-13)
+    np.testing.assert_allclose(hist[:, :2], np.broadcast_to(m0, (400, 2)), rtol=1e-13)
+
+
+def stored_momentum(f):
+    fs = f.sum(axis=(2, 3))              # [2, 9]
+    return np.array([np.sum(fs * oracle.CX), np.sum(fs * oracle.CY)])
+
+
+@pytest.mark.parametrize("g", [(0.0, 0.0), (1e-4, -3e-5)])
+def test_total_momentum_balance_periodic(g):
+    """In a periodic box the pair force of Eq. (comp_interaction) sums to zero
+    over the lattice (each pair x, x + c_i appears once with c_i and once
+    with -c_i), the relaxation of each species towards the common mixture
+    velocity exchanges momentum between species only, and the velocity shift
+    of Eq. (collision_term) adds F per step.  So the total stored momentum
+    grows by exactly M g per step."""
+    n = 48
+    rho = wl.droplet(n, n, 11.0, 20.0, 25.0) * (1 + 0.02 * np.sin(np.arange(n) / 3.0))[None, :, None]
+    P = oracle.Problem(wl.periodic_box(n, n), tau=(0.9, 1.3), G=G_REPULSIVE, g=g)
+    f = P.init(rho)
+    mass = f.sum()
+    p_prev = stored_momentum(f)
+    for _ in range(30):
+        f, _ = P.step(f)
+        p = stored_momentum(f)
+        np.testing.assert_allclose(p - p_prev, mass * np.asarray(g), rtol=1e-9, atol=1e-12)
+        p_prev = p
+
+
+def test_closed_box_at_rest_stays_at_rest():
+    """A uniform mixture at rest in a closed box whose wall potentials equal
+    the bulk densities feels no force anywhere, and halfway bounce-back of an
+    equilibrium at rest returns it unchanged: the state is a fixed point."""
+    mask = np.ones((12, 15), dtype=np.uint8)
+    mask[1:-1, 1:-1] = 0
+    rho = wl.uniform(15, 12, 0.7, 0.4)
+    P = oracle.Problem(mask, tau=(0.8, 1.2), G=G_REPULSIVE, rho_wall=(0.7, 0.4),
+                       periodic=(False, False))
+    f0 = P.init(rho)
+    f = P.run(f0, 50)
+    np.testing.assert_allclose(f, f0, rtol=0, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------
+# Eq. (comp_interaction): direction, neighbour species and wall potential
+# ----------------------------------------------------------------------------
+def test_force_on_linear_density_field():
+    """For rho^b linear in x and y, sum_i w_i c_i rho^b(x + c_i) equals
+    T0 grad rho^b exactly (sum_i w_i c_i c_i = T0 I), so the acceleration of
+    species a is G T0 grad rho^b + g, pointing up the gradient of the OTHER
+    species for G > 0.  Species b, facing a uniform rho^a, feels only g."""
+    nx, ny = 20, 16
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    rho = np.empty((2, ny, nx))
+    rho[0] = 0.5
+    rho[1] = 0.3 + 0.01 * x - 0.007 * y
+    G, g = 0.8, (1e-3, 2e-3)
+    P = oracle.Problem(wl.periodic_box(nx, ny), G=G, g=g)
+    acc = P.accel(rho)
+    inner = (slice(1, ny - 1), slice(1, nx - 1))
+    np.testing.assert_allclose(acc[0, 0][inner], G * T0 * 0.01 + g[0], rtol=1e-12)
+    np.testing.assert_allclose(acc[0, 1][inner], G * T0 * -0.007 + g[1], rtol=1e-12)
+    np.testing.assert_allclose(acc[1, 0][inner], g[0], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(acc[1, 1][inner], g[1], rtol=1e-12, atol=1e-15)
+
+
+def test_wall_potential_stands_in_for_the_other_species():
+    """A wall whose potential (rho_s^o, rho_s^w) equals the uniform fluid's
+    densities is invisible to the interaction force; with the potentials
+    swapped, the near-wall force on species o is set by rho_s^w and points
+    into the fluid when G < 0 and rho_s^w exceeds the bulk rho^w."""
+    mask = wl.straight_channel(10, 8)
+    rho = wl.uniform(10, 10, 0.6, 0.2)
+    P = oracle.Problem(mask, G=G_REPULSIVE, rho_wall=(0.6, 0.2), periodic=(True, False))
+    acc = P.accel(P.density(P.init(rho)))
+    np.testing.assert_allclose(acc, 0.0, atol=1e-15)
+    P2 = oracle.Problem(mask, G=G_REPULSIVE, rho_wall=(0.2, 0.6), periodic=(True, False))
+    acc2 = P2.accel(P2.density(P2.init(rho)))
+    # row 1 touches the wall at row 0: sum_i w_i c_iy rho^w = -(1/9 + 2/36)(0.6 - 0.2)
+    expected_o = G_REPULSIVE * -(1 / 6) * (0.6 - 0.2)
+    np.testing.assert_allclose(acc2[0, 1, 1, :], expected_o, rtol=1e-12)
+    assert np.all(acc2[0, 1, 1, :] > 0)          # pushed away from the wall at y = 0
+    np.testing.assert_allclose(acc2[0, 1, -2, :], -expected_o, rtol=1e-12)
+    np.testing.assert_allclose(acc2[0, 1, 2:-2, :], 0.0, atol=1e-15)
+
+
+def test_species_swap_symmetry():
+    """Exchanging the two species together with their relaxation times and
+    wall potentials exchanges the results (the step treats o and w alike)."""
+    P, rho = _channel_problem()
+    f = P.run(P.init(rho), 20)
+    Ps = oracle.Problem(P.mask, tau=(0.8, 1.0), G=G_REPULSIVE, rho_wall=(0.1, 0.6), g=(2e-5, 0.0),
+                        periodic=(True, False))
+    out, obs = P.step(f)
+    outs, obss = Ps.step(f[::-1].copy())
+    np.testing.assert_allclose(outs[::-1], out, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(obss[[1, 0]], obs[[0, 1]], rtol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# G = 0: BGK hydrodynamics with nu = T0 (tau - 1/2) and the mixture viscosity
+# ----------------------------------------------------------------------------
+def _shear_wave_rate(n, tau, rho_o, rho_w, steps=(100, 600)):
+    k = 2 * np.pi / n
+    y = np.arange(n)
+    u0 = 1e-3
+    ux = u0 * np.sin(k * y)
+    f = np.zeros((2, 9, n, 4))
+    for yy in range(n):
+        for a, r in enumerate((rho_o, rho_w)):
+            f[a, :, yy, :] = oracle.feq(r, ux[yy], 0.0)[:, None]
+    P = oracle.Problem(wl.periodic_box(4, n), tau=tau, G=0.0)
+    amps = []
+    t_prev = 0
+    for t in steps:
+        f = P.run(f, t - t_prev)
+        t_prev = t
+        _, u, _ = P.fields(f)
+        amps.append(np.sum(u[0, :, 0] * np.sin(k * y)) * 2 / n)
+    return -math.log(amps[1] / amps[0]) / (steps[1] - steps[0]) / k ** 2
+
+
+def test_shear_wave_viscosity_single_species():
+    """A shear wave in one species decays at nu k^2 with nu = T0 (tau - 1/2)
+    (Section 2 relation between tau and viscosity); the lattice error is
+    O(k^2), so it shrinks about 4x from n = 32 to n = 64."""
+    tau = 0.8
+    nu = analytic.bgk_viscosity(tau)
+    err32 = abs(_shear_wave_rate(32, (tau, tau), 1.0, 0.0) / nu - 1)
+    err64 = abs(_shear_wave_rate(64, (tau, tau), 1.0, 0.0) / nu - 1)
+    assert err64 < 2e-3
+    assert err64 < err32 / 3 or err32 < 1e-5
+
+
+def test_shear_wave_mixture_viscosity():
+    """A uniform mixture relaxes at tau_mix with
+    nu_mix = (rho^o nu^o + rho^w nu^w)/(rho^o + rho^w) (Section 2)."""
+    tau = (0.7, 1.6)
+    ro, rw = 0.65, 0.35
+    nu_mix = (ro * analytic.bgk_viscosity(tau[0]) + rw * analytic.bgk_viscosity(tau[1])) / (ro + rw)
+    rate = _shear_wave_rate(64, tau, ro, rw)
+    assert rate == pytest.approx(nu_mix, rel=2e-3)
+    # the harmonic (relaxation-rate) average would be far off
+    omega = (ro / tau[0] + rw / tau[1]) / (ro + rw)
+    assert abs(analytic.bgk_viscosity(1 / omega) / nu_mix - 1) > 0.05
+
+
+def test_poiseuille_single_species():
+    """Single-species force-driven channel flow at G = 0: the steady physical
+    velocity u = (j + F/2)/rho is a parabola whose curvature is -g/nu with
+    nu = T0 (tau - 1/2); with halfway bounce-back the walls sit half a node
+    outside the last fluid rows."""
+    width, tau, g = 16, 0.8, 1e-6
+    mask = wl.straight_channel(4, width)
+    rho = wl.uniform(4, width + 2, 1.0, 0.0)
+    P = oracle.Problem(mask, tau=(tau, tau), G=0.0, g=(g, 0.0), periodic=(True, False))
+    f = P.run(P.init(rho), 20000)
+    _, u, _ = P.fields(f)
+    prof = u[0, 1:-1, 0]
+    nu = analytic.bgk_viscosity(tau)
+    curv = prof[2:] - 2 * prof[1:-1] + prof[:-2]
+    np.testing.assert_allclose(curv, -g / nu, rtol=1e-4)
+    a = width / 2.0
+    yy = np.arange(1, width + 1) - (width + 1) / 2.0
+    analytic_prof = g * (a * a - yy * yy) / (2 * nu)
+    assert np.max(np.abs(prof - analytic_prof)) / analytic_prof.max() < 5e-3
+    assert np.max(np.abs(u[1])) < 1e-6 * g
+
+
+# ----------------------------------------------------------------------------
+# Section 3.1: Laplace law on static droplets
+# ----------------------------------------------------------------------------
+@pytest.mark.slow
+def test_laplace_law_droplets():
+    """dP R is constant over droplet radii (Eq. Young-Laplace_equation): a
+    least-squares line dP = sigma/R + c fits with R^2 >= 0.999 and an
+    intercept small against the smallest dP."""
+    n = 64
+    radii, dps = [], []
+    for R0 in (9.0, 11.0, 13.0, 15.0, 17.0):
+        P = oracle.Problem(wl.periodic_box(n, n), tau=(1.0, 1.0), G=G_REPULSIVE)
+        f = P.run(P.init(wl.droplet(n, n, R0, 32.0, 32.0)), 3000)
+        rho, _, pr = P.fields(f)
+        radii.append(analytic.droplet_radius(rho[0], 32.0, 32.0))
+        dps.append(pr[32, 32] - pr[0, 0])
+    sigma, c, r2 = analytic.laplace_fit(radii, dps)
+    assert sigma > 0
+    assert r2 >= 0.999
+    assert abs(c) < 0.1 * min(dps)
+
+
+# ----------------------------------------------------------------------------
+# Section 3.4: the paper's worked numbers
+# ----------------------------------------------------------------------------
+def test_worked_numbers_section_3_4():
+    with open(os.path.join(GOLDEN, "worked_numbers.json")) as fh:
+        gold = json.load(fh)
+    h = gold["hydrostatic"]
+    assert float(f"{analytic.hydrostatic(h['rho'], h['g'], h['x']):.3g}") == h["value"]
+    b = gold["bond_example"]
+    lo = analytic.bond_number(b["rho"], b["g_lo"], b["L"], b["D"], b["sigma"])
+    hi = analytic.bond_number(b["rho"], b["g_hi"], b["L"], b["D"], b["sigma"])
+    assert round(lo, 2) == b["Bo_lo"]
+    assert round(hi, 2) == b["Bo_hi"]
+
+
+def test_layered_poiseuille_reduces_to_parabola():
+    """Equal viscosities make the layered profile a single parabola; the
+    layered form is continuous with continuous stress at |y| = b."""
+    y = np.linspace(-1, 1, 41)
+    np.testing.assert_allclose(analytic.layered_poiseuille(y, 1.0, 0.4, 2.0, 0.5, 0.5),
+                               2.0 * (1 - y * y) / (2 * 0.5), rtol=1e-14)
+    a, b, f, mo, mc = 32.0, 20.0, 1e-6, 0.2, 0.05
+    eps = 1e-7
+    u_in = analytic.layered_poiseuille(b - eps, a, b, f, mo, mc)
+    u_out = analytic.layered_poiseuille(b + eps, a, b, f, mo, mc)
+    assert u_in == pytest.approx(u_out, rel=1e-6)
+    du_in = (analytic.layered_poiseuille(b - eps, a, b, f, mo, mc) -
+             analytic.layered_poiseuille(b - 2 * eps, a, b, f, mo, mc)) / eps
+    du_out = (analytic.layered_poiseuille(b + 2 * eps, a, b, f, mo, mc) -
+              analytic.layered_poiseuille(b + eps, a, b, f, mo, mc)) / eps
+    assert mc * du_in == pytest.approx(mo * du_out, rel=1e-3)
+
+
+def test_oracle_rejects_open_boundary_without_walls():
+    mask = np.zeros((6, 8), dtype=np.uint8)
+    with pytest.raises(ValueError):
+        oracle.Problem(mask, periodic=(True, False))
