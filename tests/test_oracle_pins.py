@@ -286,8 +286,9 @@ def test_worked_numbers_section_3_4():
     b = gold["bond_example"]
     lo = analytic.bond_number(b["rho"], b["g_lo"], b["L"], b["D"], b["sigma"])
     hi = analytic.bond_number(b["rho"], b["g_hi"], b["L"], b["D"], b["sigma"])
-    assert round(lo, 2) == b["Bo_lo"]
-    assert round(hi, 2) == b["Bo_hi"]
+    # the paper prints two decimals (1.5651 appears as 1.56): allow one unit
+    assert abs(lo - b["Bo_lo"]) < 0.01
+    assert abs(hi - b["Bo_hi"]) < 0.01
 
 
 def test_layered_poiseuille_reduces_to_parabola():
