@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark: two-component D2Q9 lattice updates per second (GLUPS) on one
+GB300, with the HBM roofline fraction of the step kernel.
+
+Workload: the sinusoidal channel with an oil slug, 8192 x 1170 nodes
+(h(x) = 384 - 192 cos(2 pi x / 2048), slug 2560 nodes long centred on a neck),
+FP32 populations, G = -1.79, tau = 1, wall potentials (0.5, 0.05), body force
+1e-5.  One step = one launch of the fused step kernel (pull, densities,
+interaction and wall forces, BGK collision, bounce-back, observables).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32]
+  python bench.py --impl reference   # the FP64 CPU oracle on the host cores
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank runs an
+independent replica on its own GPU (the step has no cross-GPU exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2-comp D2Q9 GLUPS (fluid-node updates/s)"
+UNIT = "GLUPS"
+G_INTERACTION = -1.79
+PHYS = dict(tau=(1.0, 1.0), G=G_INTERACTION, rho_wall=(0.5, 0.05), g=(1e-5, 0.0))
+BYTES_PER_POP = {"fp64": 8, "fp32": 4, "fp16s": 2, "bf16s": 2}
+DTYPE_NAME = {"fp64": "f64", "fp32": "f32", "fp16s": "f16-shifted storage, f32 math",
+              "bf16s": "bf16-shifted storage, f32 math"}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_1601_00918_gb300", "csrc", "lbm_step.cuh")
+
+
+def workload():
+    from paper_1601_00918_gb300 import workloads as wl
+    return wl.sinusoidal_slug(scale=8)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def recorded_traffic(precision, wname):
+    """DRAM bytes per step-kernel launch from a committed ncu capture, or None
+    when it was taken on another kernel source, precision or workload."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+        e = d.get(f"{wname}/{precision}")
+        if e and e.get("kernel_sha") == kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ----------------------------------------------------------------------------
+class OracleSample:
+    """The FP64 oracle, unmodified, on a periodic crop of the workload (full
+    height, the first `cols` columns); step() times one oracle step."""
+
+    def __init__(self, w, cols):
+        import oracle
+        self.cols = int(cols)
+        mask = np.ascontiguousarray(w.mask[:, :self.cols])
+        rho = np.ascontiguousarray(w.rho[:, :, :self.cols])
+        self.P = oracle.Problem(mask, periodic=w.periodic, **PHYS)
+        self.f = self.P.init(rho)
+        self.n_fluid = int(np.count_nonzero(mask == 0))
+
+    def step(self):
+        t0 = time.perf_counter()
+        self.f, _ = self.P.step(self.f)
+        return time.perf_counter() - t0
+
+
+def oracle_sample_for(w, seconds_per_step, min_cols=64):
+    """Crop width whose oracle step takes about seconds_per_step."""
+    ny, nx = w.mask.shape
+    probe = OracleSample(w, min_cols)
+    dt = probe.step()
+    per_col = dt / min_cols
+    cols = int(min(nx, max(min_cols, seconds_per_step / max(per_col, 1e-12))))
+    return OracleSample(w, cols)
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload()
+    ny, nx = w.mask.shape
+    per_step = max(0.3, 150.0 / max(1, args.steps + args.warmup))
+    s = oracle_sample_for(w, per_step)
+    for _ in range(args.warmup):
+        s.step()
+    times = [s.step() for _ in range(args.steps)]
+    total = sum(times)
+    value = s.n_fluid * args.steps / total / 1e9
+    sample = (f"FP64 oracle, single thread: one step over a periodic crop of the first {s.cols} of "
+              f"{nx} columns (full {ny} rows, {s.n_fluid} fluid nodes) per timed step")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "precision": "fp64", "cols_sampled": s.cols},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(w, seconds):
+    """Oracle GLUPS on a bounded sample: a crop stepped for about `seconds`."""
+    ny, nx = w.mask.shape
+    s = oracle_sample_for(w, min(seconds, 5.0))
+    total, steps = 0.0, 0
+    while total < seconds and steps < 100:
+        total += s.step()
+        steps += 1
+    return {"value": s.n_fluid * steps / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle, single thread, {steps} steps over a periodic crop of the first "
+                      f"{s.cols} of {nx} columns (full {ny} rows, {s.n_fluid} fluid nodes), "
+                      f"{total:.1f} s"}
+
+
+# ----------------------------------------------------------------------------
+# native arm
+# ----------------------------------------------------------------------------
+def native_arm(args):
+    import torch
+    from paper_1601_00918_gb300 import build, lbm
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    build.build()
+    lbm.library()
+    w = workload()
+    ny, nx = w.mask.shape
+    n_fluid = int(np.count_nonzero(w.mask == 0))
+    prec = args.precision
+
+    sim = lbm.Simulation(w.mask, w.rho, precision=prec, periodic=w.periodic, device=local, **PHYS)
+    stream = torch.cuda.current_stream()
+    sim.step(args.warmup)
+    obs0 = sim.observables()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    obs1 = sim.observables()
+    assert obs1["step"] == obs0["step"] + args.steps and obs1["nan_flag"] == 0
+    sim.close()
+    del sim
+
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * n_fluid * args.steps / (ms * 1e-3) / 1e9
+
+    # roofline of the step kernel: algorithmic bytes = read + write of the 18
+    # populations of every fluid node per launch
+    alg_bytes = n_fluid * 18 * 2 * BYTES_PER_POP[prec]
+    per_launch_s = ms * 1e-3 / args.steps
+    achieved = alg_bytes / per_launch_s / 1e9
+    peak, peak_src = peaks()
+    traffic = recorded_traffic(prec, w.name)
+
+    # end to end through the C ABI with host buffers
+    e2e = e2e_arm(args, w, prec, local, n_fluid) if rank == 0 else None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[prec],
+                "data": "synthetic",
+                "config": {"workload": w.name, "nodes": nx * ny, "fluid_nodes": n_fluid,
+                           "precision": prec, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                           "l2": "state 2 x %.2f GB ping-pong > 129 MB L2: no flush needed" %
+                                 (nx * ny * 18 * BYTES_PER_POP[prec] / 1e9)},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                             "kernel": "step_kernel", "alg_bytes_per_launch": alg_bytes},
+                "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def e2e_arm(args, w, prec, device, n_fluid):
+    """GLUPS through the C ABI with host buffers: lbm_create from pinned host
+    arrays (H2D of mask and densities), then every step lbm_step(1) and
+    lbm_observables (D2H of the observables), then lbm_get_fields (D2H of
+    rho, u, p) and lbm_destroy, all inside the timed region."""
+    import torch
+    from paper_1601_00918_gb300 import lbm
+    ny, nx = w.mask.shape
+    mask_h = torch.empty((ny, nx), dtype=torch.uint8, pin_memory=True).numpy()
+    rho_h = torch.empty((2, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    mask_h[...] = w.mask
+    rho_h[...] = w.rho
+    steps = max(1, min(args.steps, args.e2e_steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p = lbm.make_params(nx, ny, periodic=w.periodic, precision=prec,
+                        stream=torch.cuda.current_stream().cuda_stream, **PHYS)
+    h = lbm.lbm_create(mask_h, rho_h, p)
+    for _ in range(steps):
+        lbm.lbm_step(h, 1)
+        lbm.lbm_observables(h)
+    lbm.lbm_get_fields(h, nx, ny)
+    lbm.lbm_destroy(h)
+    dt = time.perf_counter() - t0
+    n = nx * ny
+    h2d = n * (1 + 16)
+    d2h = n * 40
+    obs_bytes = 64
+    return {"value": n_fluid * steps / dt / 1e9, "unit": UNIT, "steps": steps,
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps + obs_bytes,
+            "timed": "lbm_create (H2D mask + rho) + steps x (lbm_step(1) + lbm_observables) "
+                     "+ lbm_get_fields (D2H rho, u, p) + lbm_destroy"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_POP))
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return reference_arm(args)
+    return native_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

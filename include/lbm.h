@@ -1,0 +1,145 @@
+/*
+ * lbm.h -- C ABI of the two-component D2Q9 lattice-Boltzmann library for
+ * GB300 (sm_103a).
+ *
+ * The library advances two immiscible species ("o", oil, index 0 and "w",
+ * water, index 1) on a 2-D lattice with the method of Otomo et al.,
+ * "Simulation of residual oil displacement in a sinusoidal channel with the
+ * lattice Boltzmann method", Section 2:
+ *   - BGK relaxation at the per-node mixture relaxation time
+ *     tau_mix = nu_mix/T0 + 1/2, nu_mix = (rho^o nu^o + rho^w nu^w)/rho,
+ *     nu^a = T0 (tau^a - 1/2), T0 = 1/3 (Eq. LBM_BGK and the two relations
+ *     after it);
+ *   - the third-order equilibrium of Eq. (feq);
+ *   - the inter-component force of Eq. (comp_interaction),
+ *     F^a(x) = G rho^a(x) sum_i w_i c_i rho^b(x + c_i), with the wall
+ *     potentials rho_s^a replacing the density of solid neighbours;
+ *   - the force carried by the equilibrium velocity shift of
+ *     Eq. (collision_term), u_mix + F^a/rho^a, with u_mix the mixture
+ *     velocity; the non-equilibrium part is f - f^eq(rho^a, u_mix);
+ *   - the homogeneous body-force acceleration g of Section 3.4;
+ *   - halfway bounce-back at solid nodes of a wall mask.
+ *
+ * Conventions shared by every call:
+ *   - Host arrays are owned by the caller and are read or written
+ *     synchronously before the call returns.
+ *   - Device memory is owned by the library, or carved from a caller-owned
+ *     device arena (lbm_params.workspace) that must outlive the handle.
+ *   - Every call returns an lbm_status; none aborts the process.  The text of
+ *     the last error of a handle is available from lbm_last_error(h); errors
+ *     of lbm_create (no handle yet) are kept per thread and read with
+ *     lbm_last_error(NULL).
+ *   - Grids are [ny][nx] row-major with x fastest.  A node mask byte is 0 for
+ *     fluid and non-zero for solid.  A direction that is not periodic must
+ *     have solid nodes on both of its boundary lines (else LBM_EINVAL).
+ */
+#ifndef GB300_LBM_H
+#define GB300_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_t lbm_t; /* opaque handle */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,    /* bad argument, size, mask or parameter */
+    LBM_ENOMEM = -2,    /* device allocation failed or arena too small */
+    LBM_ECUDA = -3,     /* a CUDA call failed; see lbm_last_error */
+    LBM_EUNSTABLE = -4, /* a fluid node reached a NaN or negative density */
+    LBM_ETIMEOUT = -5   /* a bounded device wait gave up */
+} lbm_status;
+
+/* Storage of the populations.  Arithmetic is FP64 for LBM_FP64 and FP32
+ * otherwise.  The 16-bit formats store f_i - w_i rho_ref^a, the population
+ * minus the rest equilibrium at the species' reference density rho_ref^a
+ * (the mean initial density of the species over fluid nodes). */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_precision;
+
+typedef struct {
+    int32_t nx, ny;                 /* lattice size, both >= 1 */
+    int32_t periodic_x, periodic_y; /* 1 = periodic in that direction */
+    double tau[2];                  /* tau^o, tau^w, each > 1/2 (Section 2) */
+    double G;                       /* Eq. (comp_interaction); repulsive when G < 0 */
+    double rho_wall[2];             /* rho_s^o, rho_s^w (end of Section 2) */
+    double g[2];                    /* body-force acceleration (x, y) (Section 3.4) */
+    int32_t precision;              /* lbm_precision */
+    int32_t eq_order;               /* 3 = Eq. (feq) as printed, 2 = without cubic terms */
+    void *cuda_stream;              /* cudaStream_t for all work, or NULL = legacy default */
+    void *workspace;                /* optional device arena (>= lbm_workspace_size bytes,
+                                       256-byte aligned), or NULL: the library allocates */
+    size_t workspace_bytes;
+} lbm_params;
+
+/* Observables of the most recent step (Section 3.4 tracks the slug by its
+ * centre of oil mass). */
+typedef struct {
+    double mass[2];   /* sum over fluid nodes of rho^o, rho^w */
+    double oil_mom_x; /* sum over fluid nodes of j^o_x + F^o_x / 2 */
+    double oil_disp_x;/* running sum over all steps of oil_mom_x / mass[0]: the
+                         unwrapped x displacement of the oil centre of mass */
+    double max_u;     /* max over fluid nodes of |u|, u = (sum_a j^a + F^a/2)/rho */
+    int64_t step;     /* steps taken since lbm_create or the last lbm_load */
+    int32_t nan_flag; /* 1 once any fluid node had a NaN or negative density */
+    int32_t reserved;
+} lbm_obs;
+
+/* Bytes of device memory a handle with parameters p needs (for the
+ * workspace arena).  Returns LBM_EINVAL on bad sizes or precision. */
+int lbm_workspace_size(const lbm_params *p, size_t *bytes);
+
+/* Create a simulation.
+ *   mask     host uint8 [ny][nx], 1 = solid (required)
+ *   rho_init host double [2][ny][nx] initial densities of species o then w
+ *            at fluid nodes (values at solid nodes are ignored); the stored
+ *            state starts at the rest equilibrium f*_i = w_i rho_init
+ *   p        parameters; copied, so the caller may free it afterwards
+ *   out      receives the handle
+ * Errors: LBM_EINVAL (NULL pointer, size, tau <= 1/2, precision, eq_order,
+ * open boundary without solid lines, non-positive total density at a fluid
+ * node), LBM_ENOMEM, LBM_ECUDA. */
+int lbm_create(const uint8_t *mask, const double *rho_init, const lbm_params *p, lbm_t **out);
+
+/* Advance nsteps >= 0 time steps (Eq. basic_LBM_eq with the BGK collision of
+ * Eq. LBM_BGK), asynchronously on the handle's stream.  Returns the launch
+ * status; instability is reported by lbm_observables. */
+int lbm_step(lbm_t *h, int64_t nsteps);
+
+/* Synchronise the stream and copy the observables of the latest step.
+ * Returns LBM_EUNSTABLE (with *out filled) once nan_flag is set. */
+int lbm_observables(lbm_t *h, lbm_obs *out);
+
+/* Macroscopic fields of the current state (the state a next step would pull
+ * and collide), copied to host FP64 arrays; any pointer may be NULL:
+ *   rho [2][ny][nx]  species densities (rho_s^a at solid nodes)
+ *   u   [2][ny][nx]  mixture velocity planes u_x then u_y,
+ *                    u = (j^o + j^w + (F^o + F^w)/2)/(rho^o + rho^w), 0 at solid
+ *   p   [ny][nx]     pressure T0 (rho^o + rho^w) - G T0 rho^o rho^w, 0 at solid */
+int lbm_get_fields(lbm_t *h, double *rho, double *u, double *p);
+
+/* Change the body-force acceleration used by the following steps. */
+int lbm_set_body_force(lbm_t *h, double gx, double gy);
+
+/* Copy the stored post-collision populations to / from a host FP64 array
+ * f[2][9][ny][nx] (species, direction, y, x; directions c_0 = (0,0),
+ * c_1..c_4 = (1,0),(0,1),(-1,0),(0,-1), c_5..c_8 = (1,1),(-1,1),(-1,-1),(1,-1)).
+ * lbm_load also resets the observables (step count, displacement, NaN flag). */
+int lbm_save(lbm_t *h, double *f);
+int lbm_load(lbm_t *h, const double *f);
+
+/* Free the handle and the device memory it owns.  NULL is ignored. */
+void lbm_destroy(lbm_t *h);
+
+/* Text of the last error of h, or of the calling thread's last lbm_create
+ * when h is NULL.  Valid until the next call on the same handle / thread. */
+const char *lbm_last_error(const lbm_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_LBM_H */

@@ -1,0 +1,234 @@
+"""Python binding of the C ABI in include/lbm.h (ctypes; argument marshalling only).
+
+Every call goes to libgb300lbm.so, built in-tree by ``build.py``; there is no
+fallback: if the library is missing or no CUDA device is present the calls
+raise.  PyTorch is used only as the provider of device memory (the optional
+workspace arena) and of the CUDA stream.
+
+The functions keep the C names: ``lbm_create``, ``lbm_step``,
+``lbm_observables``, ``lbm_get_fields``, ``lbm_set_body_force``, ``lbm_save``,
+``lbm_load``, ``lbm_destroy``, ``lbm_last_error``, ``lbm_workspace_size``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgb300lbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5
+LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2, 3
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
+
+# symbols declared in include/lbm.h
+EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "lbm_get_fields",
+           "lbm_set_body_force", "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+                ("tau", ctypes.c_double * 2), ("G", ctypes.c_double),
+                ("rho_wall", ctypes.c_double * 2), ("g", ctypes.c_double * 2),
+                ("precision", ctypes.c_int32), ("eq_order", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double * 2), ("oil_mom_x", ctypes.c_double),
+                ("oil_disp_x", ctypes.c_double), ("max_u", ctypes.c_double),
+                ("step", ctypes.c_int64), ("nan_flag", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"mass": (self.mass[0], self.mass[1]), "oil_mom_x": self.oil_mom_x,
+                "oil_disp_x": self.oil_disp_x, "max_u": self.max_u, "step": self.step,
+                "nan_flag": self.nan_flag}
+
+
+_lib = None
+
+
+def library(path: str | None = None) -> ctypes.CDLL:
+    """Load libgb300lbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with paper_1601_00918_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    dp = P(ctypes.c_double)
+    lib.lbm_workspace_size.argtypes = [P(Params), P(ctypes.c_size_t)]
+    lib.lbm_create.argtypes = [P(ctypes.c_uint8), dp, P(Params), P(vp)]
+    lib.lbm_step.argtypes = [vp, ctypes.c_int64]
+    lib.lbm_observables.argtypes = [vp, P(Obs)]
+    lib.lbm_get_fields.argtypes = [vp, dp, dp, dp]
+    lib.lbm_set_body_force.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    lib.lbm_save.argtypes = [vp, dp]
+    lib.lbm_load.argtypes = [vp, dp]
+    lib.lbm_destroy.argtypes = [vp]
+    lib.lbm_destroy.restype = None
+    lib.lbm_last_error.argtypes = [vp]
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    for name in ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables",
+                 "lbm_get_fields", "lbm_set_body_force", "lbm_save", "lbm_load"):
+        getattr(lib, name).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc, handle=None):
+    if rc != LBM_OK:
+        msg = library().lbm_last_error(handle)
+        raise LbmError(rc, (msg or b"").decode())
+    return rc
+
+
+def make_params(nx, ny, tau=(1.0, 1.0), G=0.0, rho_wall=(0.0, 0.0), g=(0.0, 0.0),
+                periodic=(True, True), precision="fp32", eq_order=3, stream=None,
+                workspace=None, workspace_bytes=0) -> Params:
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return Params(int(nx), int(ny), int(periodic[0]), int(periodic[1]),
+                  (ctypes.c_double * 2)(*tau), float(G), (ctypes.c_double * 2)(*rho_wall),
+                  (ctypes.c_double * 2)(*g), prec, int(eq_order),
+                  ctypes.c_void_p(stream) if stream else None,
+                  ctypes.c_void_p(workspace) if workspace else None, int(workspace_bytes))
+
+
+def lbm_workspace_size(params: Params) -> int:
+    out = ctypes.c_size_t(0)
+    _check(library().lbm_workspace_size(ctypes.byref(params), ctypes.byref(out)))
+    return out.value
+
+
+def lbm_create(mask, rho_init, params: Params) -> int:
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    rho = np.ascontiguousarray(rho_init, dtype=np.float64)
+    if mask.shape != (params.ny, params.nx) or rho.shape != (2, params.ny, params.nx):
+        raise ValueError("mask must be [ny, nx] and rho_init [2, ny, nx]")
+    h = ctypes.c_void_p()
+    _check(library().lbm_create(mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dptr(rho),
+                                ctypes.byref(params), ctypes.byref(h)))
+    return h.value
+
+
+def lbm_step(h, nsteps: int):
+    _check(library().lbm_step(h, int(nsteps)), h)
+
+
+def lbm_observables(h, check=True) -> dict:
+    o = Obs()
+    rc = library().lbm_observables(h, ctypes.byref(o))
+    if check:
+        _check(rc, h)
+    d = o.as_dict()
+    d["status"] = rc
+    return d
+
+
+def lbm_get_fields(h, nx, ny):
+    rho = np.empty((2, ny, nx))
+    u = np.empty((2, ny, nx))
+    p = np.empty((ny, nx))
+    _check(library().lbm_get_fields(h, _dptr(rho), _dptr(u), _dptr(p)), h)
+    return rho, u, p
+
+
+def lbm_set_body_force(h, gx, gy=0.0):
+    _check(library().lbm_set_body_force(h, float(gx), float(gy)), h)
+
+
+def lbm_save(h, nx, ny):
+    f = np.empty((2, 9, ny, nx))
+    _check(library().lbm_save(h, _dptr(f)), h)
+    return f
+
+
+def lbm_load(h, f):
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    _check(library().lbm_load(h, _dptr(f)), h)
+
+
+def lbm_destroy(h):
+    if h:
+        library().lbm_destroy(h)
+
+
+def lbm_last_error(h=None) -> str:
+    return (library().lbm_last_error(h) or b"").decode()
+
+
+class Simulation:
+    """Owning wrapper: device arena from PyTorch, work on torch's current stream."""
+
+    def __init__(self, mask, rho_init, tau=(1.0, 1.0), G=0.0, rho_wall=(0.0, 0.0),
+                 g=(0.0, 0.0), periodic=(True, True), precision="fp32", eq_order=3,
+                 device=0, use_torch_arena=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        self.ny, self.nx = mask.shape
+        self.device = torch.device("cuda", device)
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            p = make_params(self.nx, self.ny, tau, G, rho_wall, g, periodic, precision, eq_order,
+                            stream=stream)
+            self._arena = None
+            if use_torch_arena:
+                nbytes = lbm_workspace_size(p)
+                self._arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+                base = self._arena.data_ptr()
+                aligned = (base + 255) // 256 * 256
+                p.workspace = ctypes.c_void_p(aligned)
+                p.workspace_bytes = nbytes
+            self.params = p
+            self.h = lbm_create(mask, rho_init, p)
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+
+    def observables(self, check=True):
+        return lbm_observables(self.h, check)
+
+    def fields(self):
+        return lbm_get_fields(self.h, self.nx, self.ny)
+
+    def set_body_force(self, gx, gy=0.0):
+        lbm_set_body_force(self.h, gx, gy)
+
+    def save(self):
+        return lbm_save(self.h, self.nx, self.ny)
+
+    def load(self, f):
+        lbm_load(self.h, f)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+        self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,131 @@
+"""Host-side checks of the C-ABI library and the input generators (no GPU).
+
+The library is compiled for sm_103a here (nvcc cross-compiles) and loaded;
+only calls that fail validation before touching the device are made.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1601_00918_gb300 import build, lbm, workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return lbm.library()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert {"lbm_create", "lbm_step", "lbm_observables", "lbm_destroy"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(lbm.EXPORTS) <= names
+
+
+def test_workspace_size_formula(lib):
+    p = lbm.make_params(100, 30, precision="fp32")
+    pitch = 128
+    buf = 18 * 30 * pitch * 4
+    buf = (buf + 255) // 256 * 256
+    links = (30 * pitch * 2 + 255) // 256 * 256
+    assert lbm.lbm_workspace_size(p) == 2 * buf + links + 3 * 256
+    assert lbm.lbm_workspace_size(lbm.make_params(100, 30, precision="fp16s")) < \
+        lbm.lbm_workspace_size(p)
+
+
+def test_too_large_grid_rejected(lib):
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_workspace_size(lbm.make_params(1 << 16, 1 << 12))
+    assert e.value.code == lbm.LBM_EINVAL
+
+
+@pytest.mark.parametrize("bad", [
+    dict(tau=(0.5, 1.0)),
+    dict(tau=(1.0, 0.3)),
+    dict(eq_order=4),
+    dict(precision=9),
+    dict(periodic=(True, False)),            # open in y without solid rows
+])
+def test_create_rejects_bad_parameters(lib, bad):
+    kw = dict(nx=16, ny=8)
+    p = lbm.make_params(**kw, **bad)
+    mask = wl.periodic_box(16, 8)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_create(mask, wl.uniform(16, 8, 1.0, 0.1), p)
+    assert e.value.code == lbm.LBM_EINVAL
+    assert lbm.lbm_last_error(None)
+
+
+def test_create_rejects_bad_densities(lib):
+    p = lbm.make_params(16, 8)
+    rho = wl.uniform(16, 8, 1.0, 0.1)
+    rho[0, 3, 3] = -0.1
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_create(wl.periodic_box(16, 8), rho, p)
+    rho = wl.uniform(16, 8, 0.0, 0.0)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_create(wl.periodic_box(16, 8), rho, p)
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
+    assert lib.lbm_observables(None, None) == lbm.LBM_EINVAL
+    lib.lbm_destroy(None)
+
+
+# ----------------------------------------------------------------------------
+# input generators
+# ----------------------------------------------------------------------------
+def test_sinusoidal_channel_rows():
+    """1024 x 146 channel, h(x) = 48 - 24 cos(2 pi x / 256), y_c = 72.5: rows
+    1..144 are fluid at a bulge, rows 49..96 (48 rows) at a neck."""
+    w = wl.sinusoidal_slug(scale=1)
+    assert w.mask.shape == (146, 1024)
+    bulge = np.nonzero(w.mask[:, 128] == 0)[0]
+    neck = np.nonzero(w.mask[:, 0] == 0)[0]
+    assert (bulge.min(), bulge.max()) == (1, 144)
+    assert (neck.min(), neck.max(), len(neck)) == (49, 96, 48)
+    assert np.all(w.mask[0] == 1) and np.all(w.mask[-1] == 1)
+    big = wl.sinusoidal_slug(scale=8)
+    assert big.mask.shape == (1170, 8192)
+    rows = np.nonzero(big.mask[:, 1024] == 0)[0]
+    assert (rows.min(), rows.max()) == (9, 1160)
+
+
+def test_droplet_and_slug_profiles():
+    r = wl.droplet(64, 64, 10.0, 32.0, 32.0)
+    assert r[0, 32, 32] == pytest.approx(1.0, abs=1e-3)
+    assert r[0, 0, 0] == pytest.approx(0.03, abs=1e-6)
+    np.testing.assert_allclose(r.sum(axis=0), 1.03)
+    s = wl.slug(100, 10, 30.0, 70.0)
+    assert s[0, 5, 50] == pytest.approx(1.0, abs=1e-6)
+    assert s[1, 5, 5] == pytest.approx(1.0, abs=1e-6)
+
+
+def test_sweep_specs_are_seeded():
+    a = wl.sweep_specs(16, seed=3)
+    b = wl.sweep_specs(16, seed=3)
+    assert a == b
+    for s in a:
+        assert s.lam in (128, 192, 256, 384, 512)
+        assert 0.2 <= s.amp_ratio <= 0.6 and 20 <= s.theta_deg <= 160
+        assert 0.2 <= s.visc_ratio <= 10
+        w = wl.channel_instance(s)
+        assert w.mask.shape == (s.ny, s.nx)

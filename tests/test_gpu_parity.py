@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 oracle.
+
+Tolerances (derived from the arithmetic, written here):
+* FP64 storage and math: the two sides evaluate the same formulas in a
+  different order, so they agree to a few ulps per step: 1e-12 absolute on
+  populations of size <= 0.5 after 100 steps.
+* FP32 storage and math, one step from the same state: each population goes
+  through ~60 FP32 operations on values <= ~1, each rounding by <= 6e-8, so
+  |gpu - oracle| <= 5e-6.
+* FP32 after 1000 steps: relative L-infinity <= 1e-5 on rho and u (|u| relative
+  to max |u|), mass drift <= 1e-6 relative.
+* FP16/BF16 shifted storage: parity is not fixed by the paper; the bound comes
+  from the storage rounding of |f - w rho_ref| <= w max|rho - rho_ref|
+  (2^-11 and 2^-8 relative), amplified over the run; the tests state it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_00918_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+G = -1.79
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1601_00918_gb300 import build
+    build.build()
+    from paper_1601_00918_gb300 import lbm as mod
+    mod.library()
+    return mod
+
+
+def gpu_run(lbm, mask, rho, steps, precision="fp32", **kw):
+    sim = lbm.Simulation(mask, rho, precision=precision, **kw)
+    try:
+        sim.step(steps)
+        obs = sim.observables(check=False)
+        f = sim.save()
+        fields = sim.fields()
+    finally:
+        sim.close()
+    return f, obs, fields
+
+
+def channel(nx=300, ny=40, lam=100.0):
+    mask = wl.sinusoidal_channel(nx, ny, 12.0, 5.0, lam)
+    rho = wl.slug(nx, ny, 0.3 * nx, 0.7 * nx)
+    kw = dict(tau=(1.0, 0.7), G=G, rho_wall=(0.6, 0.05), g=(2e-5, 0.0), periodic=(True, False))
+    return mask, rho, kw
+
+
+def droplet_case(n=128, R=20.0):
+    return wl.periodic_box(n, n), wl.droplet(n, n, R, n / 2.0, n / 2.0), dict(tau=(1.0, 1.0), G=G)
+
+
+# ----------------------------------------------------------------------------
+# FP64: near bit-level agreement over many tiles and a ragged tail
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("steps", [1, 10, 100])
+def test_fp64_channel_matches_oracle(lbm, steps):
+    mask, rho, kw = channel()        # 300 = 2 x 128 + 44: ragged last column tile
+    f_gpu, obs, (rho_g, u_g, p_g) = gpu_run(lbm, mask, rho, steps, "fp64", **kw)
+    P = oracle.Problem(mask, **kw)
+    f_ref, hist = P.run(P.init(rho), steps, history=True)
+    np.testing.assert_allclose(f_gpu, f_ref, rtol=0, atol=1e-12)
+    rho_r, u_r, p_r = P.fields(f_ref)
+    np.testing.assert_allclose(rho_g, rho_r, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(u_g, u_r, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(p_g, p_r, rtol=0, atol=1e-12)
+    assert obs["step"] == steps
+    np.testing.assert_allclose(obs["mass"], hist[-1, :2], rtol=1e-12)
+    np.testing.assert_allclose(obs["oil_mom_x"], hist[-1, 2], rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(obs["oil_disp_x"], np.sum(hist[:, 2] / hist[:, 0]), rtol=1e-9, atol=1e-14)
+    np.testing.assert_allclose(obs["max_u"], hist[-1, 3], rtol=1e-9, atol=1e-15)
+    assert obs["nan_flag"] == 0
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 5), (7, 33), (130, 9), (257, 6)])
+def test_fp64_small_and_odd_periodic_grids(lbm, shape):
+    """Degenerate and odd sizes (a 1 x 1 lattice, widths not a multiple of 32
+    or of the 128-column tile, fewer rows than a strip) in a fully periodic
+    box with a random mixture."""
+    ny, nx = shape
+    rho = wl.random_perturbed(nx, ny, seed=nx * 31 + ny, amp=0.2)
+    mask = wl.periodic_box(nx, ny)
+    kw = dict(tau=(0.9, 1.3), G=G, g=(1e-5, -2e-5))
+    f_gpu, obs, _ = gpu_run(lbm, mask, rho, 7, "fp64", **kw)
+    P = oracle.Problem(mask, **kw)
+    f_ref = P.run(P.init(rho), 7)
+    np.testing.assert_allclose(f_gpu, f_ref, rtol=0, atol=1e-12)
+
+
+def test_fp64_closed_box_and_eq_order_2(lbm):
+    """Walls on all four sides (neither direction periodic) and the
+    second-order equilibrium option."""
+    nx, ny = 45, 30
+    mask = np.ones((ny, nx), dtype=np.uint8)
+    mask[1:-1, 1:-1] = 0
+    mask[10:14, 20:26] = 1                       # an obstacle
+    rho = wl.droplet(nx, ny, 7.0, 12.0, 15.0)
+    kw = dict(tau=(0.8, 1.1), G=G, rho_wall=(0.1, 0.7), g=(0.0, -1e-5), periodic=(False, False),
+              eq_order=2)
+    f_gpu, _, _ = gpu_run(lbm, mask, rho, 30, "fp64", **kw)
+    P = oracle.Problem(mask, **kw)
+    f_ref = P.run(P.init(rho), 30)
+    np.testing.assert_allclose(f_gpu, f_ref, rtol=0, atol=1e-12)
+
+
+def test_all_solid_grid(lbm):
+    mask = np.ones((8, 40), dtype=np.uint8)
+    rho = wl.uniform(40, 8, 1.0, 0.1)
+    f_gpu, obs, (rho_g, u_g, p_g) = gpu_run(lbm, mask, rho, 5, "fp32", rho_wall=(0.3, 0.2),
+                                            periodic=(False, False))
+    assert obs["step"] == 5
+    assert obs["mass"] == (0.0, 0.0)
+    assert np.all(f_gpu == 0)
+    np.testing.assert_allclose(rho_g[0], 0.3)
+    np.testing.assert_allclose(rho_g[1], 0.2)
+
+
+# ----------------------------------------------------------------------------
+# FP32
+# ----------------------------------------------------------------------------
+def test_fp32_one_step_channel(lbm):
+    mask, rho, kw = channel()
+    P = oracle.Problem(mask, **kw)
+    f0 = P.run(P.init(rho), 50).astype(np.float32).astype(np.float64)
+    sim = lbm.Simulation(mask, rho, precision="fp32", **kw)
+    try:
+        sim.load(f0)
+        sim.step(1)
+        f_gpu = sim.save()
+    finally:
+        sim.close()
+    f_ref, _ = P.step(f0)
+    np.testing.assert_allclose(f_gpu, f_ref, rtol=0, atol=5e-6)
+
+
+def test_fp32_droplet_1000_steps(lbm):
+    """Static droplet, 128 x 128 periodic, R = 20, tau = 1: after 1000 steps
+    the FP32 densities and velocities match the FP64 oracle to 1e-5 relative
+    L-infinity, and the per-species mass drifts by <= 1e-6."""
+    mask, rho, kw = droplet_case()
+    f_gpu, obs, (rho_g, u_g, _) = gpu_run(lbm, mask, rho, 1000, "fp32", **kw)
+    P = oracle.Problem(mask, **kw)
+    f_ref, hist = P.run(P.init(rho), 1000, history=True)
+    rho_r, u_r, _ = P.fields(f_ref)
+    err_rho = np.max(np.abs(rho_g - rho_r)) / np.max(np.abs(rho_r))
+    err_u = np.max(np.abs(u_g - u_r)) / np.max(np.abs(u_r))
+    assert err_rho <= 1e-5, err_rho
+    assert err_u <= 1e-5, err_u
+    m0 = rho.reshape(2, -1).sum(axis=1)
+    drift = np.abs(np.asarray(obs["mass"]) - m0) / m0
+    assert np.all(drift <= 1e-6), drift
+    assert obs["step"] == 1000 and obs["nan_flag"] == 0
+
+
+def test_fp32_channel_observables(lbm):
+    mask, rho, kw = channel()
+    _, obs, _ = gpu_run(lbm, mask, rho, 200, "fp32", **kw)
+    P = oracle.Problem(mask, **kw)
+    _, hist = P.run(P.init(rho), 200, history=True)
+    np.testing.assert_allclose(obs["mass"], hist[-1, :2], rtol=1e-6)
+    np.testing.assert_allclose(obs["oil_disp_x"], np.sum(hist[:, 2] / hist[:, 0]), rtol=1e-3, atol=1e-7)
+    np.testing.assert_allclose(obs["max_u"], hist[-1, 3], rtol=1e-3)
+
+
+def test_set_body_force_and_save_load_roundtrip(lbm):
+    mask, rho, kw = channel(nx=200, ny=40, lam=100.0)
+    P = oracle.Problem(mask, **kw)
+    sim = lbm.Simulation(mask, rho, precision="fp64", **kw)
+    try:
+        sim.step(5)
+        f5 = sim.save()
+        sim.load(f5)
+        np.testing.assert_array_equal(sim.save(), f5)
+        sim.set_body_force(-3e-5, 1e-6)
+        sim.step(5)
+        f10 = sim.save()
+        obs = sim.observables()
+    finally:
+        sim.close()
+    assert obs["step"] == 5                      # load resets the counters
+    P2 = oracle.Problem(mask, **{**kw, "g": (-3e-5, 1e-6)})
+    np.testing.assert_allclose(f10, P2.run(P.run(P.init(rho), 5), 5), rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# 16-bit shifted storage (parity not fixed by the paper; bounds stated)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,bound", [("fp16s", 3e-3), ("bf16s", 2.5e-2)])
+def test_shifted_16bit_storage_error(lbm, precision, bound):
+    """Error of the 16-bit shifted storage against the FP64 oracle on the
+    channel after 200 steps: relative L-infinity on rho below `bound`
+    (about 6x the storage rounding of the largest shifted value) and exact
+    mass conservation up to the rounding of the stored populations."""
+    mask, rho, kw = channel()
+    _, obs, (rho_g, _, _) = gpu_run(lbm, mask, rho, 200, precision, **kw)
+    P = oracle.Problem(mask, **kw)
+    rho_r, _, _ = P.fields(P.run(P.init(rho), 200))
+    err = np.max(np.abs(rho_g - rho_r)) / np.max(rho_r)
+    assert err < bound, err
+    assert obs["nan_flag"] == 0
+
+
+# ----------------------------------------------------------------------------
+# full size: 8192 x 1170 sinusoidal channel, the benchmark's launch shape
+# ----------------------------------------------------------------------------
+def test_full_size_sampled_nodes(lbm):
+    """At the benchmark workload (8192 x 1170, FP32), one step from a state
+    reached on the GPU is checked node by node on a sample: every node of
+    two rows that cross CTA strips, the first/last fluid rows, CTA column
+    edges and 3000 random fluid nodes, against the oracle's per-node step."""
+    w = wl.sinusoidal_slug(scale=8)
+    kw = dict(tau=(1.0, 1.0), G=G, rho_wall=(0.5, 0.05), g=(1e-5, 0.0), periodic=w.periodic)
+    sim = lbm.Simulation(w.mask, w.rho, precision="fp32", **kw)
+    try:
+        sim.step(20)
+        f0 = sim.save()
+        sim.step(1)
+        f1 = sim.save()
+        obs = sim.observables()
+    finally:
+        sim.close()
+    assert obs["nan_flag"] == 0
+    ny, nx = w.mask.shape
+    rng = np.random.default_rng(7)
+    fy, fx = np.nonzero(w.mask == 0)
+    pick = rng.choice(len(fx), 3000, replace=False)
+    xs = [fx[pick]]
+    ys = [fy[pick]]
+    for row in (ny // 2, 584, 585, 10, ny - 11):
+        xs.append(np.arange(nx))
+        ys.append(np.full(nx, row))
+    edge = np.concatenate([np.arange(0, nx, 128), np.arange(127, nx, 128)])
+    xs.append(edge)
+    ys.append(np.full(len(edge), ny // 2 + 3))
+    xs = np.concatenate(xs).astype(np.int32)
+    ys = np.concatenate(ys).astype(np.int32)
+    P = oracle.Problem(w.mask, **kw)
+    ref = P.step_nodes(f0, xs, ys)                       # [k, 2, 9]
+    got = f1[:, :, ys, xs].transpose(2, 0, 1)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=5e-6)
