@@ -224,7 +224,9 @@ def native_arm(args):
     n_fluid = int(np.count_nonzero(w.mask == 0))
     prec = args.precision
 
-    sim = lbm.Simulation(w.mask, w.rho, precision=prec, periodic=w.periodic, device=local, **PHYS)
+    sim = lbm.Simulation(w.mask, w.rho, precision=prec, periodic=w.periodic, device=local,
+                         variant=args.variant, **PHYS)
+    kinfo = sim.kernel_info()
     stream = torch.cuda.current_stream()
     sim.step(args.warmup)
     obs0 = sim.observables()
@@ -277,13 +279,15 @@ def native_arm(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[prec],
                 "data": "synthetic",
                 "config": {"workload": w.name, "nodes": nx * ny, "fluid_nodes": n_fluid,
-                           "precision": prec, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                           "precision": prec, "kernel": kinfo,
+                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "l2": "state 2 x %.2f GB ping-pong > 129 MB L2: no flush needed" %
                                  (nx * ny * 18 * BYTES_PER_POP[prec] / 1e9)},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic,
                              "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
-                             "kernel": "step_kernel", "alg_bytes_per_launch": alg_bytes},
+                             "kernel": "step_%s_kernel" % kinfo["variant"],
+                             "alg_bytes_per_launch": alg_bytes},
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -306,7 +310,7 @@ def e2e_arm(args, w, prec, device, n_fluid):
     steps = max(1, min(args.steps, args.e2e_steps))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    p = lbm.make_params(nx, ny, periodic=w.periodic, precision=prec,
+    p = lbm.make_params(nx, ny, periodic=w.periodic, precision=prec, variant=args.variant,
                         stream=torch.cuda.current_stream().cuda_stream, **PHYS)
     h = lbm.lbm_create(mask_h, rho_h, p)
     for _ in range(steps):
@@ -332,6 +336,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_POP))
+    ap.add_argument("--variant", default="auto", choices=["auto", "simple", "staged"])
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

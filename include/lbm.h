@@ -69,6 +69,9 @@ typedef struct {
     double g[2];                    /* body-force acceleration (x, y) (Section 3.4) */
     int32_t precision;              /* lbm_precision */
     int32_t eq_order;               /* 3 = Eq. (feq) as printed, 2 = without cubic terms */
+    int32_t variant;                /* step kernel: 0 = autotuned, 1 = simple (register pull),
+                                       2 = staged (TMA row pipeline); results are identical */
+    int32_t reserved;               /* must be 0 */
     void *cuda_stream;              /* cudaStream_t for all work, or NULL = legacy default */
     void *workspace;                /* optional device arena (>= lbm_workspace_size bytes,
                                        256-byte aligned), or NULL: the library allocates */
@@ -85,7 +88,7 @@ typedef struct {
     double max_u;     /* max over fluid nodes of |u|, u = (sum_a j^a + F^a/2)/rho */
     int64_t step;     /* steps taken since lbm_create or the last lbm_load */
     int32_t nan_flag; /* 1 once any fluid node had a NaN or negative density */
-    int32_t reserved;
+    int32_t timeout_flag; /* 1 once a bounded device wait gave up (that step's data invalid) */
 } lbm_obs;
 
 /* Bytes of device memory a handle with parameters p needs (for the
@@ -110,7 +113,8 @@ int lbm_create(const uint8_t *mask, const double *rho_init, const lbm_params *p,
 int lbm_step(lbm_t *h, int64_t nsteps);
 
 /* Synchronise the stream and copy the observables of the latest step.
- * Returns LBM_EUNSTABLE (with *out filled) once nan_flag is set. */
+ * Returns LBM_ETIMEOUT once timeout_flag is set, else LBM_EUNSTABLE once
+ * nan_flag is set (*out is filled in both cases). */
 int lbm_observables(lbm_t *h, lbm_obs *out);
 
 /* Macroscopic fields of the current state (the state a next step would pull
@@ -130,6 +134,13 @@ int lbm_set_body_force(lbm_t *h, double gx, double gy);
  * lbm_load also resets the observables (step count, displacement, NaN flag). */
 int lbm_save(lbm_t *h, double *f);
 int lbm_load(lbm_t *h, const double *f);
+
+/* Launch configuration the autotuner chose for the step kernel:
+ * info[0] = variant (1 simple, 2 staged), info[1] = rows in flight (staged),
+ * info[2] = rows per CTA strip (simple), info[3] = strips per column block
+ * (staged).  Not part of the paper's method: a report of this library's
+ * tuning. */
+int lbm_kernel_info(const lbm_t *h, int32_t info[4]);
 
 /* Free the handle and the device memory it owns.  NULL is ignored. */
 void lbm_destroy(lbm_t *h);

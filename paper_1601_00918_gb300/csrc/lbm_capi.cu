@@ -1,44 +1,81 @@
 // Runtime and C ABI (include/lbm.h) of the two-component D2Q9 library.
 //
-// A handle owns: two population buffers A/B (ping-pong, layout
-// f[species][direction][y][pitch], x fastest, pitch = nx rounded up to 32
-// elements so every row starts 128-byte aligned), a 16-bit link word per node
-// (bit i set when the pull source x - c_i is solid, bit 15 when the node itself
-// is solid), the device parameter block, the per-step reduction accumulators
-// and the finalised observables.  All device memory comes from one arena,
-// either allocated here or supplied by the caller.
+// A handle owns, in one device arena (allocated here or supplied by the
+// caller):
+//   - two population buffers A/B (ping-pong), layout
+//     f[species][direction][y][pitch] with 8 ghost columns on each side of
+//     every row (see lbm_common.cuh), pitch a multiple of 32 elements;
+//   - a 16-bit link word per node (bit i: the pull source x - c_i is solid,
+//     bit 15: the node is solid), same row layout;
+//   - the fluid row range of every 128-column block (the staged kernel
+//     marches only over rows that hold fluid in its columns);
+//   - the device parameter block, the per-step reduction accumulators and
+//     the finalised observables (plus a spare pair used while autotuning).
+// Steps run as one kernel launch each; runs of 32 steps are replayed from a
+// captured CUDA graph.  The step kernel and its launch shape are picked by
+// timing candidates on the handle's own data (autotuner, cached per grid
+// shape, precision and periodicity).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_step.cuh"
+#include "lbm_step_tma.cuh"
 
 using namespace gb300lbm;
+
+namespace {
+
+constexpr int kBX = 128;         // columns per CTA (both kernels)
+constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity is kept)
+
+struct Tuned {
+    int variant = 1;   // 1 simple, 2 staged
+    int depth = 2;     // staged: rows in flight
+    int rpb = 16;      // simple: rows per CTA strip
+    int strips = 1;    // staged: strips per column block
+};
+
+}  // namespace
 
 struct lbm_t {
     lbm_params p{};
     int pitch = 0;
+    int ncb = 0;                  // 128-column blocks
     size_t elem = 0;              // bytes per stored population
     size_t buf_bytes = 0;         // one population buffer
     void* arena = nullptr;
     bool own_arena = false;
-    void* f[2] = {nullptr, nullptr};
-    int cur = 0;                  // f[cur] holds the current stored state
-    uint16_t* links = nullptr;
+    char* fbase[2] = {nullptr, nullptr};   // buffer starts (storage column 0)
+    int cur = 0;                  // fbase[cur] holds the current stored state
+    uint16_t* links = nullptr;    // storage column 0 of row 0
+    int2* rows = nullptr;
     StepParams* dprm = nullptr;
     ObsAccum* dacc = nullptr;
     ObsState* dobs = nullptr;
+    ObsAccum* tacc = nullptr;     // autotuning scratch
+    ObsState* tobs = nullptr;
     StepParams hprm{};
     cudaStream_t stream = nullptr;
-    int rows_per_block = 0;
+    cudaStream_t capture = nullptr;       // private stream for graph capture
+    CUtensorMap fmap[2];
+    CUtensorMap lmap;
+    bool maps_ok = false;
+    Tuned tune;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t fluid_nodes = 0;
     std::string err;
 };
@@ -46,8 +83,6 @@ struct lbm_t {
 namespace {
 
 thread_local std::string g_create_err;
-
-constexpr int kBX = 128;
 
 int fail(lbm_t* h, int code, const char* fmt, ...) {
     char buf[512];
@@ -82,36 +117,50 @@ size_t elem_size(int prec) {
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    int pitch;
-    size_t buf, links, prm, acc, obs, total;
+    int pitch, ncb;
+    size_t buf, links, rows, prm, acc, obs, total;
 };
 
 bool layout_of(const lbm_params* p, Layout* L) {
     const size_t es = elem_size(p->precision);
     if (es == 0 || p->nx < 1 || p->ny < 1) return false;
-    L->pitch = (p->nx + 31) / 32 * 32;
+    if (p->nx > (1 << 24) || p->ny > (1 << 24)) return false;
+    L->pitch = (p->nx + 2 * kGhost + 31) / 32 * 32;
+    L->ncb = (p->nx + kBX - 1) / kBX;
     const size_t plane = (size_t)p->ny * L->pitch;
-    // kernel indices are 32-bit: all 18 planes must fit below 2^31 elements
+    // kernel indices are 32-bit: all 18 planes must stay below 2^31 elements
     if (plane * 18 >= (size_t(1) << 31)) return false;
     L->buf = align256(plane * 18 * es);
     L->links = align256(plane * sizeof(uint16_t));
+    L->rows = align256((size_t)L->ncb * sizeof(int2));
     L->prm = align256(sizeof(StepParams));
     L->acc = align256(sizeof(ObsAccum));
     L->obs = align256(sizeof(ObsState));
-    L->total = 2 * L->buf + L->links + L->prm + L->acc + L->obs;
+    L->total = 2 * L->buf + L->links + L->rows + L->prm + 2 * L->acc + 2 * L->obs;
     return true;
 }
 
 // ---------------------------------------------------------------------------
 // set-up kernels
 // ---------------------------------------------------------------------------
+// Logical column of a storage column, or INT_MIN when it holds nothing
+// (padding, or a ghost of a non-periodic grid).
+__device__ __forceinline__ int logical_col(int sc, int nx, int periodic) {
+    const int x = sc - kGhost;
+    if (x >= 0 && x < nx) return x;
+    if (!periodic || x < -kGhost || x >= nx + kGhost) return INT_MIN;
+    int m = x % nx;
+    return m < 0 ? m + nx : m;
+}
+
 __global__ void links_kernel(const uint8_t* __restrict__ mask, uint16_t* __restrict__ links, int nx,
-                             int ny, int pitch) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+                             int ny, int pitch, int periodic) {
+    const int sc = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    if (x >= pitch || y >= ny) return;
-    if (x >= nx) {
-        links[y * pitch + x] = uint16_t(1u << kSolidBit);
+    if (sc >= pitch || y >= ny) return;
+    const int x = logical_col(sc, nx, periodic);
+    if (x == INT_MIN) {
+        links[y * pitch + sc] = uint16_t(1u << kSolidBit);
         return;
     }
     unsigned w = mask[y * nx + x] ? (1u << kSolidBit) : 0u;
@@ -121,25 +170,27 @@ __global__ void links_kernel(const uint8_t* __restrict__ mask, uint16_t* __restr
         sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
         if (mask[sy * nx + sx]) w |= 1u << i;
     }
-    links[y * pitch + x] = uint16_t(w);
+    links[y * pitch + sc] = uint16_t(w);
 }
 
 template <typename S>
 __global__ void init_kernel(const double* __restrict__ rho, const uint16_t* __restrict__ links,
-                            S* __restrict__ f, int nx, int ny, int pitch, double ref0, double ref1) {
+                            S* __restrict__ f, int nx, int ny, int pitch, int periodic, double ref0,
+                            double ref1) {
     using R = typename Codec<S>::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sc = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    if (x >= pitch || y >= ny) return;
+    if (sc >= pitch || y >= ny) return;
     const int plane = ny * pitch;
-    const bool solid = x >= nx || (links[y * pitch + x] & (1u << kSolidBit));
+    const int x = logical_col(sc, nx, periodic);
+    const bool solid = x == INT_MIN || (links[y * pitch + sc] & (1u << kSolidBit));
     for (int a = 0; a < 2; a++) {
         const double r = solid ? 0.0 : rho[(size_t)a * nx * ny + (size_t)y * nx + x];
         const double ref = a ? ref1 : ref0;
         for (int i = 0; i < 9; i++) {
             const double w = weight_of<double>(i);
-            S* dst = f + (a * 9 + i) * plane + y * pitch + x;
-            // solid nodes and padding hold the stored value 0
+            S* dst = f + (a * 9 + i) * plane + y * pitch + sc;
+            // solid nodes, padding and unused ghosts hold the stored value 0
             if (solid)
                 Codec<S>::store(dst, R(0), R(0));
             else
@@ -148,45 +199,231 @@ __global__ void init_kernel(const double* __restrict__ rho, const uint16_t* __re
     }
 }
 
-template <typename S>
-void launch_step(lbm_t* h, const void* fin, void* fout, bool fields, double* out, int row_begin,
-                 int row_end) {
+// ---------------------------------------------------------------------------
+// launches
+// ---------------------------------------------------------------------------
+Grid make_grid(const lbm_t* h, int row_begin, int row_end) {
     Grid g;
     g.nx = h->p.nx;
     g.ny = h->p.ny;
     g.pitch = h->pitch;
-    g.rows_per_block = h->rows_per_block;
+    g.periodic_x = h->p.periodic_x;
+    g.rows_per_block = h->tune.rpb;
     g.row_begin = row_begin;
     g.row_end = row_end;
-    dim3 grid((h->p.nx + kBX - 1) / kBX, (row_end - row_begin + g.rows_per_block - 1) / g.rows_per_block);
-    if (fields)
-        step_kernel<S, kBX, true><<<grid, kBX, 0, h->stream>>>(
-            (const S*)fin, (S*)fout, h->links, h->dprm, h->dacc, h->dobs, out, g);
-    else
-        step_kernel<S, kBX, false><<<grid, kBX, 0, h->stream>>>(
-            (const S*)fin, (S*)fout, h->links, h->dprm, h->dacc, h->dobs, out, g);
+    g.strips = h->tune.strips;
+    return g;
 }
 
-void dispatch_step(lbm_t* h, const void* fin, void* fout, bool fields, double* out, int rb, int re) {
+template <typename S>
+S* at_col0(char* base) {
+    return (S*)base + kGhost;
+}
+
+template <typename S, int D>
+cudaError_t launch_staged(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs,
+                          cudaStream_t st) {
+    using Plan = StagedPlan<S, kBX, D>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(step_staged_kernel<S, kBX, D>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Plan::kBytes);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    Grid g = make_grid(h, 0, h->p.ny);
+    g.strips = tn.strips;
+    dim3 grid(h->ncb, tn.strips);
+    step_staged_kernel<S, kBX, D><<<grid, kBX, Plan::kBytes, st>>>(
+        h->fmap[src], h->lmap, at_col0<S>(h->fbase[1 - src]), h->rows, h->dprm, acc, obs, g);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_one(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs, cudaStream_t st) {
+    if (tn.variant == 2) {
+        if (tn.depth >= 4) return launch_staged<S, 4>(h, src, tn, acc, obs, st);
+        return launch_staged<S, 2>(h, src, tn, acc, obs, st);
+    }
+    Grid g = make_grid(h, 0, h->p.ny);
+    g.rows_per_block = tn.rpb;
+    dim3 grid(h->ncb, (h->p.ny + tn.rpb - 1) / tn.rpb);
+    step_simple_kernel<S, kBX, false><<<grid, kBX, 0, st>>>(
+        at_col0<S>(h->fbase[src]), at_col0<S>(h->fbase[1 - src]), h->links + kGhost, h->dprm, acc, obs,
+        nullptr, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs, cudaStream_t st) {
     switch (h->p.precision) {
-        case LBM_FP64: launch_step<double>(h, fin, fout, fields, out, rb, re); break;
-        case LBM_FP32: launch_step<float>(h, fin, fout, fields, out, rb, re); break;
-        case LBM_FP16S: launch_step<__half>(h, fin, fout, fields, out, rb, re); break;
-        case LBM_BF16S: launch_step<__nv_bfloat16>(h, fin, fout, fields, out, rb, re); break;
+        case LBM_FP64: return launch_one<double>(h, src, tn, acc, obs, st);
+        case LBM_FP32: return launch_one<float>(h, src, tn, acc, obs, st);
+        case LBM_FP16S: return launch_one<__half>(h, src, tn, acc, obs, st);
+        default: return launch_one<__nv_bfloat16>(h, src, tn, acc, obs, st);
     }
 }
 
-// Rows per CTA strip: enough CTAs to fill the 152 SMs several times over,
-// but strips long enough that the two halo rows stay a small overhead.
-int choose_rows_per_block(int nx, int ny) {
-    const int cols = (nx + kBX - 1) / kBX;
-    const int target_ctas = 152 * 8;
-    int rpb = (int)((int64_t)cols * ny / std::max(target_ctas, 1));
-    rpb = std::max(4, std::min(rpb, 128));
-    return std::min(rpb, ny);
+template <typename S>
+cudaError_t launch_fields_t(lbm_t* h, double* out, int rb, int re) {
+    Grid g = make_grid(h, rb, re);
+    g.rows_per_block = 8;
+    dim3 grid(h->ncb, (re - rb + 7) / 8);
+    step_simple_kernel<S, kBX, true><<<grid, kBX, 0, h->stream>>>(
+        at_col0<S>(h->fbase[h->cur]), nullptr, h->links + kGhost, h->dprm, h->dacc, h->dobs, out, g);
+    return cudaGetLastError();
 }
 
-// host conversions for save/load
+cudaError_t launch_fields(lbm_t* h, double* out, int rb, int re) {
+    switch (h->p.precision) {
+        case LBM_FP64: return launch_fields_t<double>(h, out, rb, re);
+        case LBM_FP32: return launch_fields_t<float>(h, out, rb, re);
+        case LBM_FP16S: return launch_fields_t<__half>(h, out, rb, re);
+        default: return launch_fields_t<__nv_bfloat16>(h, out, rb, re);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tensor maps for the staged kernel
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+bool make_maps(lbm_t* h) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    CUtensorMapDataType dt;
+    switch (h->p.precision) {
+        case LBM_FP64: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
+        case LBM_FP32: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+        case LBM_FP16S: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
+        default: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
+    }
+    const cuuint32_t W = kBX + 2 * kGhost;
+    for (int b = 0; b < 2; b++) {
+        cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)h->p.ny, 18};
+        cuuint64_t strides[2] = {(cuuint64_t)h->pitch * h->elem, (cuuint64_t)h->p.ny * h->pitch * h->elem};
+        cuuint32_t box[3] = {W, 1, 18};
+        cuuint32_t es[3] = {1, 1, 1};
+        if (fn(&h->fmap[b], dt, 3, h->fbase[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)h->pitch, (cuuint64_t)h->p.ny};
+    cuuint64_t strides[1] = {(cuuint64_t)h->pitch * 2};
+    cuuint32_t box[2] = {W, 1};
+    cuuint32_t es[2] = {1, 1};
+    return fn(&h->lmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h->links, dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int64_t>, Tuned> g_tune_cache;
+
+int sms_of_device() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 152;
+}
+
+std::vector<Tuned> candidates(const lbm_t* h) {
+    std::vector<Tuned> out;
+    const int sms = sms_of_device();
+    const int ny = h->p.ny;
+    const int req = h->p.variant;
+    if (req == 0 || req == 1) {
+        for (int ctas_per_sm : {4, 8, 16}) {
+            Tuned t;
+            t.variant = 1;
+            t.rpb = (int)std::max<int64_t>(4, std::min<int64_t>(ny, (int64_t)h->ncb * ny / (sms * ctas_per_sm)));
+            out.push_back(t);
+        }
+    }
+    if ((req == 0 || req == 2) && h->maps_ok) {
+        for (int depth : {2, 4}) {
+            for (int waves : {1, 2, 4}) {
+                Tuned t;
+                t.variant = 2;
+                t.depth = depth;
+                const int resident = sms * (depth >= 4 ? 2 : 3);
+                t.strips = std::max(1, std::min(ny, waves * resident / std::max(1, h->ncb)));
+                out.push_back(t);
+            }
+        }
+    }
+    // dedupe
+    std::vector<Tuned> u;
+    for (auto& t : out) {
+        bool dup = false;
+        for (auto& v : u)
+            dup |= v.variant == t.variant && v.depth == t.depth && v.rpb == t.rpb && v.strips == t.strips;
+        if (!dup) u.push_back(t);
+    }
+    return u;
+}
+
+int autotune(lbm_t* h) {
+    auto key = std::make_tuple(h->p.nx, h->p.ny, h->p.precision, h->p.periodic_x, h->p.variant, h->fluid_nodes);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            h->tune = it->second;
+            return LBM_OK;
+        }
+    }
+    std::vector<Tuned> cand = candidates(h);
+    if (cand.empty()) return fail(nullptr, LBM_ECUDA, "no step kernel available (tensor maps failed)");
+    Tuned best = cand[0];
+    if (cand.size() > 1) {
+        cudaEvent_t e0, e1;
+        CUDA_TRY(nullptr, cudaEventCreate(&e0));
+        CUDA_TRY(nullptr, cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        // candidates step from the current buffer into the other one, with
+        // scratch accumulators: the stored state and the observables are untouched
+        for (const Tuned& t : cand) {
+            CUDA_TRY(nullptr, cudaMemsetAsync(h->tacc, 0, sizeof(ObsAccum), h->stream));
+            CUDA_TRY(nullptr, launch_step(h, h->cur, t, h->tacc, h->tobs, h->stream));
+            CUDA_TRY(nullptr, cudaEventRecord(e0, h->stream));
+            for (int k = 0; k < 3; k++) CUDA_TRY(nullptr, launch_step(h, h->cur, t, h->tacc, h->tobs, h->stream));
+            CUDA_TRY(nullptr, cudaEventRecord(e1, h->stream));
+            CUDA_TRY(nullptr, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_TRY(nullptr, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    h->tune = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// misc host helpers
+// ---------------------------------------------------------------------------
 double to_double(const void* base, size_t k, int prec) {
     switch (prec) {
         case LBM_FP64: return ((const double*)base)[k];
@@ -205,17 +442,18 @@ void from_double(void* base, size_t k, int prec, double v) {
     }
 }
 
-double host_weight(int i) { return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0); }
-
 int validate(const lbm_params* p, const uint8_t* mask) {
     if (!p) return fail(nullptr, LBM_EINVAL, "params is NULL");
     if (p->nx < 1 || p->ny < 1) return fail(nullptr, LBM_EINVAL, "nx, ny must be >= 1");
     if (elem_size(p->precision) == 0) return fail(nullptr, LBM_EINVAL, "unknown precision %d", p->precision);
     if (p->eq_order != 2 && p->eq_order != 3) return fail(nullptr, LBM_EINVAL, "eq_order must be 2 or 3");
+    if (p->variant < 0 || p->variant > 2) return fail(nullptr, LBM_EINVAL, "variant must be 0, 1 or 2");
     for (int a = 0; a < 2; a++)
-        if (!(p->tau[a] > 0.5)) return fail(nullptr, LBM_EINVAL, "tau[%d] must exceed 1/2", a);
-    if (!std::isfinite(p->G) || !std::isfinite(p->g[0]) || !std::isfinite(p->g[1]))
-        return fail(nullptr, LBM_EINVAL, "G and g must be finite");
+        if (!(p->tau[a] > 0.5) || !std::isfinite(p->tau[a]))
+            return fail(nullptr, LBM_EINVAL, "tau[%d] must be finite and exceed 1/2", a);
+    if (!std::isfinite(p->G) || !std::isfinite(p->g[0]) || !std::isfinite(p->g[1]) ||
+        !std::isfinite(p->rho_wall[0]) || !std::isfinite(p->rho_wall[1]))
+        return fail(nullptr, LBM_EINVAL, "G, g and rho_wall must be finite");
     Layout L;
     if (!layout_of(p, &L)) return fail(nullptr, LBM_EINVAL, "grid %d x %d too large", p->nx, p->ny);
     if (mask) {
@@ -238,9 +476,41 @@ void fill_params(lbm_t* h) {
         s.nu[a] = (h->p.tau[a] - 0.5) / 3.0;
         s.rho_wall[a] = h->p.rho_wall[a];
         s.g[a] = h->p.g[a];
+        s.rho_ref[a] = 0.0;
     }
     s.G = h->p.G;
     s.k3 = h->p.eq_order >= 3 ? 4.5 : 0.0;
+}
+
+void drop_graphs(lbm_t* h) {
+    for (auto& g : h->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Capture kGraphSteps launches starting from buffer `src` on the private
+// capture stream.
+int build_graph(lbm_t* h, int src) {
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    int s = src;
+    for (int k = 0; k < kGraphSteps && le == cudaSuccess; k++) {
+        le = launch_step(h, s, h->tune, h->dacc, h->dobs, h->capture);
+        s = 1 - s;
+    }
+    cudaError_t ce = cudaStreamEndCapture(h->capture, &g);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(h, LBM_ECUDA, "graph capture failed: %s",
+                    cudaGetErrorString(le != cudaSuccess ? le : ce));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&h->graph[src], g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return fail(h, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ie));
+    return LBM_OK;
 }
 
 }  // namespace
@@ -264,30 +534,38 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
     const int nx = p->nx, ny = p->ny;
     const size_t n = (size_t)nx * ny;
 
-    // host checks and the reference densities of the 16-bit storage shift
+    // host checks, reference densities of the 16-bit shift, fluid row ranges
     double sum[2] = {0.0, 0.0};
     int64_t nfluid = 0;
-    for (size_t k = 0; k < n; k++) {
-        if (mask[k]) continue;
-        const double a = rho_init[k], b = rho_init[n + k];
-        if (!(a >= 0.0) || !(b >= 0.0) || !(a + b > 0.0) || !std::isfinite(a + b))
-            return fail(nullptr, LBM_EINVAL, "rho_init must be finite, >= 0, with positive total at fluid nodes");
-        sum[0] += a;
-        sum[1] += b;
-        nfluid++;
-    }
+    Layout L;
+    layout_of(p, &L);
+    std::vector<int2> rows(L.ncb, int2{1, 0});
+    for (int cb = 0; cb < L.ncb; cb++) rows[cb] = int2{ny, -1};
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            const size_t k = (size_t)y * nx + x;
+            if (mask[k]) continue;
+            const double a = rho_init[k], b = rho_init[n + k];
+            if (!(a >= 0.0) || !(b >= 0.0) || !(a + b > 0.0) || !std::isfinite(a + b))
+                return fail(nullptr, LBM_EINVAL,
+                            "rho_init must be finite, >= 0, with positive total at fluid nodes");
+            sum[0] += a;
+            sum[1] += b;
+            nfluid++;
+            int2& r = rows[x / kBX];
+            r.x = std::min(r.x, y);
+            r.y = std::max(r.y, y);
+        }
 
     lbm_t* h = new (std::nothrow) lbm_t();
     if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
     h->p = *p;
     h->stream = (cudaStream_t)p->cuda_stream;
     h->fluid_nodes = nfluid;
-    Layout L;
-    layout_of(p, &L);
     h->pitch = L.pitch;
+    h->ncb = L.ncb;
     h->elem = elem_size(p->precision);
     h->buf_bytes = L.buf;
-    h->rows_per_block = choose_rows_per_block(nx, ny);
 
     if (p->workspace) {
         if (p->workspace_bytes < L.total || ((uintptr_t)p->workspace & 255)) {
@@ -304,23 +582,29 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
         h->own_arena = true;
     }
     char* base = (char*)h->arena;
-    h->f[0] = base;
-    h->f[1] = base + L.buf;
-    h->links = (uint16_t*)(base + 2 * L.buf);
-    h->dprm = (StepParams*)(base + 2 * L.buf + L.links);
-    h->dacc = (ObsAccum*)(base + 2 * L.buf + L.links + L.prm);
-    h->dobs = (ObsState*)(base + 2 * L.buf + L.links + L.prm + L.acc);
+    size_t off = 0;
+    h->fbase[0] = base + off;
+    off += L.buf;
+    h->fbase[1] = base + off;
+    off += L.buf;
+    h->links = (uint16_t*)(base + off);
+    off += L.links;
+    h->rows = (int2*)(base + off);
+    off += L.rows;
+    h->dprm = (StepParams*)(base + off);
+    off += L.prm;
+    h->dacc = (ObsAccum*)(base + off);
+    off += L.acc;
+    h->tacc = (ObsAccum*)(base + off);
+    off += L.acc;
+    h->dobs = (ObsState*)(base + off);
+    off += L.obs;
+    h->tobs = (ObsState*)(base + off);
 
     fill_params(h);
-    if (p->precision == LBM_FP16S || p->precision == LBM_BF16S) {
+    if (p->precision == LBM_FP16S || p->precision == LBM_BF16S)
         for (int a = 0; a < 2; a++) h->hprm.rho_ref[a] = nfluid ? sum[a] / nfluid : 0.0;
-    }
 
-    // stage rho_init (FP64) and the mask in buffer B, build links, init A
-    const size_t rho_bytes = n * 2 * sizeof(double);
-    char* stage = (char*)h->f[1];
-    double* d_rho = (double*)stage;
-    uint8_t* d_mask = (uint8_t*)(stage + align256(rho_bytes));
     auto bail = [&](int code) {
         std::string msg = g_create_err;
         lbm_destroy(h);
@@ -335,26 +619,41 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
             return bail(LBM_ECUDA);                                                               \
         }                                                                                         \
     } while (0)
+    CREATE_TRY(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking));
+    // stage rho_init (FP64) and the mask in buffer B, build links, init A
+    const size_t rho_bytes = n * 2 * sizeof(double);
+    char* stage = h->fbase[1];
+    double* d_rho = (double*)stage;
+    uint8_t* d_mask = (uint8_t*)(stage + align256(rho_bytes));
     CREATE_TRY(cudaMemcpyAsync(d_rho, rho_init, rho_bytes, cudaMemcpyHostToDevice, h->stream));
     CREATE_TRY(cudaMemcpyAsync(d_mask, mask, n, cudaMemcpyHostToDevice, h->stream));
-    CREATE_TRY(cudaMemsetAsync(h->dacc, 0, sizeof(ObsAccum), h->stream));
-    CREATE_TRY(cudaMemsetAsync(h->dobs, 0, sizeof(ObsState), h->stream));
+    CREATE_TRY(cudaMemcpyAsync(h->rows, rows.data(), rows.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
+    CREATE_TRY(cudaMemsetAsync(h->dacc, 0, 2 * L.acc, h->stream));
+    CREATE_TRY(cudaMemsetAsync(h->dobs, 0, 2 * L.obs, h->stream));
     CREATE_TRY(cudaMemcpyAsync(h->dprm, &h->hprm, sizeof(StepParams), cudaMemcpyHostToDevice, h->stream));
     dim3 blk(256), grd((h->pitch + 255) / 256, ny);
-    links_kernel<<<grd, blk, 0, h->stream>>>(d_mask, h->links, nx, ny, h->pitch);
+    links_kernel<<<grd, blk, 0, h->stream>>>(d_mask, h->links, nx, ny, h->pitch, p->periodic_x);
     const double r0 = h->hprm.rho_ref[0], r1 = h->hprm.rho_ref[1];
+    const int px = p->periodic_x;
     switch (p->precision) {
-        case LBM_FP64: init_kernel<double><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (double*)h->f[0], nx, ny, h->pitch, r0, r1); break;
-        case LBM_FP32: init_kernel<float><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (float*)h->f[0], nx, ny, h->pitch, r0, r1); break;
-        case LBM_FP16S: init_kernel<__half><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (__half*)h->f[0], nx, ny, h->pitch, r0, r1); break;
-        default: init_kernel<__nv_bfloat16><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (__nv_bfloat16*)h->f[0], nx, ny, h->pitch, r0, r1); break;
+        case LBM_FP64: init_kernel<double><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (double*)h->fbase[0], nx, ny, h->pitch, px, r0, r1); break;
+        case LBM_FP32: init_kernel<float><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (float*)h->fbase[0], nx, ny, h->pitch, px, r0, r1); break;
+        case LBM_FP16S: init_kernel<__half><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (__half*)h->fbase[0], nx, ny, h->pitch, px, r0, r1); break;
+        default: init_kernel<__nv_bfloat16><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (__nv_bfloat16*)h->fbase[0], nx, ny, h->pitch, px, r0, r1); break;
     }
     CREATE_TRY(cudaGetLastError());
-    // B must hold the same zeros at solid nodes and padding as A
-    CREATE_TRY(cudaMemcpyAsync(h->f[1], h->f[0], L.buf, cudaMemcpyDeviceToDevice, h->stream));
+    // B holds the same zeros at solid nodes, padding and unused ghosts as A
+    CREATE_TRY(cudaMemcpyAsync(h->fbase[1], h->fbase[0], L.buf, cudaMemcpyDeviceToDevice, h->stream));
     CREATE_TRY(cudaStreamSynchronize(h->stream));
 #undef CREATE_TRY
+    h->maps_ok = make_maps(h);
     h->cur = 0;
+    if (p->variant == 2 && !h->maps_ok) {
+        fail(nullptr, LBM_ECUDA, "tensor-map encoding failed: the staged kernel is unavailable");
+        return bail(LBM_ECUDA);
+    }
+    rc = autotune(h);
+    if (rc) return bail(rc);
     *out = h;
     return LBM_OK;
 }
@@ -362,11 +661,21 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
 int lbm_step(lbm_t* h, int64_t nsteps) {
     if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
     if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
-    for (int64_t s = 0; s < nsteps; s++) {
-        dispatch_step(h, h->f[h->cur], h->f[1 - h->cur], false, nullptr, 0, h->p.ny);
+    int64_t left = nsteps;
+    if (left >= kGraphSteps) {
+        if (!h->graph[h->cur]) {
+            int rc = build_graph(h, h->cur);
+            if (rc) return rc;
+        }
+        while (left >= kGraphSteps) {
+            CUDA_TRY(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+            left -= kGraphSteps;   // an even number of steps: the parity is unchanged
+        }
+    }
+    for (; left > 0; left--) {
+        CUDA_TRY(h, launch_step(h, h->cur, h->tune, h->dacc, h->dobs, h->stream));
         h->cur = 1 - h->cur;
     }
-    CUDA_TRY(h, cudaGetLastError());
     return LBM_OK;
 }
 
@@ -382,7 +691,8 @@ int lbm_observables(lbm_t* h, lbm_obs* out) {
     out->max_u = s.umax;
     out->step = s.step;
     out->nan_flag = s.nan_flag;
-    out->reserved = 0;
+    out->timeout_flag = s.timeout_flag;
+    if (s.timeout_flag) return fail(h, LBM_ETIMEOUT, "a bounded device wait gave up");
     if (s.nan_flag) return fail(h, LBM_EUNSTABLE, "a fluid node reached a NaN or negative density");
     return LBM_OK;
 }
@@ -394,26 +704,25 @@ int lbm_get_fields(lbm_t* h, double* rho, double* u, double* pr) {
     // fields of a window of rows are written to the free buffer, 5 doubles a node
     const int max_rows = (int)std::min<size_t>(ny, h->buf_bytes / (5 * sizeof(double) * nx));
     if (max_rows < 1) return fail(h, LBM_EINVAL, "grid row too long for the staging buffer");
-    double* stage = (double*)h->f[1 - h->cur];
+    double* stage = (double*)h->fbase[1 - h->cur];
     std::vector<double> tmp;
     for (int y0 = 0; y0 < ny; y0 += max_rows) {
         const int y1 = std::min(ny, y0 + max_rows);
         const size_t cnt = (size_t)nx * (y1 - y0);
-        dispatch_step(h, h->f[h->cur], nullptr, true, stage, y0, y1);
-        CUDA_TRY(h, cudaGetLastError());
+        CUDA_TRY(h, launch_fields(h, stage, y0, y1));
         tmp.resize(cnt * 5);
         CUDA_TRY(h, cudaMemcpyAsync(tmp.data(), stage, cnt * 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-        const size_t off = (size_t)y0 * nx;
+        const size_t o = (size_t)y0 * nx;
         if (rho) {
-            memcpy(rho + off, tmp.data(), cnt * sizeof(double));
-            memcpy(rho + n + off, tmp.data() + cnt, cnt * sizeof(double));
+            memcpy(rho + o, tmp.data(), cnt * sizeof(double));
+            memcpy(rho + n + o, tmp.data() + cnt, cnt * sizeof(double));
         }
         if (u) {
-            memcpy(u + off, tmp.data() + 2 * cnt, cnt * sizeof(double));
-            memcpy(u + n + off, tmp.data() + 3 * cnt, cnt * sizeof(double));
+            memcpy(u + o, tmp.data() + 2 * cnt, cnt * sizeof(double));
+            memcpy(u + n + o, tmp.data() + 3 * cnt, cnt * sizeof(double));
         }
-        if (pr) memcpy(pr + off, tmp.data() + 4 * cnt, cnt * sizeof(double));
+        if (pr) memcpy(pr + o, tmp.data() + 4 * cnt, cnt * sizeof(double));
     }
     return LBM_OK;
 }
@@ -435,21 +744,21 @@ int lbm_save(lbm_t* h, double* f) {
     if (!h || !f) return fail(h, LBM_EINVAL, "NULL argument");
     const int nx = h->p.nx, ny = h->p.ny, pitch = h->pitch;
     std::vector<char> raw(h->buf_bytes);
-    CUDA_TRY(h, cudaMemcpyAsync(raw.data(), h->f[h->cur], h->buf_bytes, cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    const bool shifted = h->p.precision == LBM_FP16S || h->p.precision == LBM_BF16S;
     std::vector<uint16_t> lk((size_t)ny * pitch);
-    CUDA_TRY(h, cudaMemcpy(lk.data(), h->links, lk.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpyAsync(raw.data(), h->fbase[h->cur], h->buf_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(lk.data(), h->links, lk.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     for (int a = 0; a < 2; a++)
-        for (int i = 0; i < 9; i++)
+        for (int i = 0; i < 9; i++) {
+            const double sh = weight_of<double>(i) * h->hprm.rho_ref[a];
             for (int y = 0; y < ny; y++)
                 for (int x = 0; x < nx; x++) {
-                    const size_t k = ((size_t)(a * 9 + i) * ny + y) * pitch + x;
-                    const bool solid = lk[(size_t)y * pitch + x] & (1u << kSolidBit);
-                    double v = to_double(raw.data(), k, h->p.precision);
-                    if (shifted && !solid) v += host_weight(i) * h->hprm.rho_ref[a];
-                    f[((size_t)(a * 9 + i) * ny + y) * nx + x] = solid ? 0.0 : v;
+                    const size_t k = ((size_t)(a * 9 + i) * ny + y) * pitch + kGhost + x;
+                    const bool solid = lk[(size_t)y * pitch + kGhost + x] & (1u << kSolidBit);
+                    f[((size_t)(a * 9 + i) * ny + y) * nx + x] =
+                        solid ? 0.0 : to_double(raw.data(), k, h->p.precision) + sh;
                 }
+        }
     return LBM_OK;
 }
 
@@ -457,24 +766,38 @@ int lbm_load(lbm_t* h, const double* f) {
     if (!h || !f) return fail(h, LBM_EINVAL, "NULL argument");
     const int nx = h->p.nx, ny = h->p.ny, pitch = h->pitch;
     std::vector<uint16_t> lk((size_t)ny * pitch);
-    CUDA_TRY(h, cudaMemcpy(lk.data(), h->links, lk.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpyAsync(lk.data(), h->links, lk.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     std::vector<char> raw(h->buf_bytes, 0);
-    const bool shifted = h->p.precision == LBM_FP16S || h->p.precision == LBM_BF16S;
     for (int a = 0; a < 2; a++)
-        for (int i = 0; i < 9; i++)
+        for (int i = 0; i < 9; i++) {
+            const double sh = weight_of<double>(i) * h->hprm.rho_ref[a];
             for (int y = 0; y < ny; y++)
-                for (int x = 0; x < nx; x++) {
-                    const size_t k = ((size_t)(a * 9 + i) * ny + y) * pitch + x;
-                    const bool solid = lk[(size_t)y * pitch + x] & (1u << kSolidBit);
-                    double v = f[((size_t)(a * 9 + i) * ny + y) * nx + x];
-                    if (solid) v = 0.0;
-                    else if (shifted) v -= host_weight(i) * h->hprm.rho_ref[a];
-                    from_double(raw.data(), k, h->p.precision, v);
+                for (int sc = 0; sc < pitch; sc++) {
+                    // storage column sc holds logical column x, or a periodic image
+                    int x = sc - kGhost;
+                    if (x < 0 || x >= nx) {
+                        if (!h->p.periodic_x || x < -kGhost || x >= nx + kGhost) continue;
+                        x = ((x % nx) + nx) % nx;
+                    }
+                    if (lk[(size_t)y * pitch + kGhost + x] & (1u << kSolidBit)) continue;
+                    const size_t k = ((size_t)(a * 9 + i) * ny + y) * pitch + sc;
+                    from_double(raw.data(), k, h->p.precision, f[((size_t)(a * 9 + i) * ny + y) * nx + x] - sh);
                 }
-    CUDA_TRY(h, cudaMemcpyAsync(h->f[h->cur], raw.data(), h->buf_bytes, cudaMemcpyHostToDevice, h->stream));
+        }
+    CUDA_TRY(h, cudaMemcpyAsync(h->fbase[h->cur], raw.data(), h->buf_bytes, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->dacc, 0, sizeof(ObsAccum), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->dobs, 0, sizeof(ObsState), h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm_kernel_info(const lbm_t* h, int32_t info[4]) {
+    if (!h || !info) return fail(nullptr, LBM_EINVAL, "NULL argument");
+    info[0] = h->tune.variant;
+    info[1] = h->tune.depth;
+    info[2] = h->tune.rpb;
+    info[3] = h->tune.strips;
     return LBM_OK;
 }
 
@@ -482,6 +805,8 @@ void lbm_destroy(lbm_t* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
+    drop_graphs(h);
+    if (h->capture) cudaStreamDestroy(h->capture);
     if (h->own_arena && h->arena) cudaFree(h->arena);
     delete h;
 }

@@ -1,0 +1,396 @@
+// Device code shared by the step kernels: storage codecs, the D2Q9 lattice,
+// the equilibrium of Eq. (feq), the per-node force + collision, and the
+// per-step observables reduction.
+//
+// Storage layout (every population plane and the link-word plane):
+//   element (x, y) of a plane lives at  y * pitch + kGhost + x,
+// for logical columns x in [-kGhost, nx + kGhost).  Columns -2, -1, nx, nx + 1
+// are "ghost" copies of nx - 2, nx - 1, 0, 1 when x is periodic (written by
+// the step that writes the original column), so a row window
+// [x0 - kGhost, x0 + BX + kGhost) never needs a wrap-around patch; this is
+// what lets a single TMA box stage a row.  pitch >= nx + 2 kGhost, rounded up
+// to 32 elements, so every row starts 128-byte aligned.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace gb300lbm {
+
+constexpr int kGhost = 8;       // ghost columns on each side (16-byte aligned for 2-byte types)
+constexpr int kSolidBit = 15;   // link word: bit i (1..8) = pull source x - c_i is solid
+
+// Device-resident parameters (read each launch, so captured graphs follow
+// lbm_set_body_force).
+struct StepParams {
+    double nu[2];        // nu^a = T0 (tau^a - 1/2)
+    double G;
+    double g[2];
+    double rho_wall[2];
+    double k3;           // 4.5 with the cubic terms of Eq. (feq), 0 without
+    double rho_ref[2];   // shift of the 16-bit storage: stored = f - w_i rho_ref^a
+};
+
+// Per-step reduction targets; reset by the last CTA of each step.
+struct ObsAccum {
+    double mass[2];
+    double px;
+    unsigned long long umax2_bits;
+    unsigned int bad;
+    unsigned int blocks_done;
+};
+
+// Observables as of the latest step (host-visible copy in lbm_obs).
+struct ObsState {
+    double mass[2];
+    double px;
+    double disp;
+    double umax;
+    long long step;
+    int nan_flag;
+    int timeout_flag;    // a bounded device wait gave up (data of that step invalid)
+};
+
+struct Grid {
+    int nx, ny, pitch;
+    int periodic_x;
+    int rows_per_block;   // simple kernel: rows per CTA strip
+    int row_begin;        // first row handled by blockIdx.y == 0 (fields windows)
+    int row_end;          // one past the last row handled by this launch
+    int strips;           // staged kernel: strips per column block (gridDim.y)
+};
+
+// ---------------------------------------------------------------------------
+// storage codecs: plain FP64 / FP32, or 16-bit shifted by w_i rho_ref^a
+// ---------------------------------------------------------------------------
+template <typename S>
+struct Codec;
+
+template <>
+struct Codec<double> {
+    using R = double;
+    static __device__ __forceinline__ double decode(double v, double) { return v; }
+    static __device__ __forceinline__ double load(const double* p, double s) { return decode(__ldg(p), s); }
+    static __device__ __forceinline__ void store(double* p, double v, double) { *p = v; }
+};
+
+template <>
+struct Codec<float> {
+    using R = float;
+    static __device__ __forceinline__ float decode(float v, float) { return v; }
+    static __device__ __forceinline__ float load(const float* p, float s) { return decode(__ldg(p), s); }
+    static __device__ __forceinline__ void store(float* p, float v, float) { *p = v; }
+};
+
+template <>
+struct Codec<__half> {
+    using R = float;
+    static __device__ __forceinline__ float decode(__half v, float shift) { return __half2float(v) + shift; }
+    static __device__ __forceinline__ float load(const __half* p, float s) { return decode(__ldg(p), s); }
+    static __device__ __forceinline__ void store(__half* p, float v, float shift) {
+        *p = __float2half_rn(v - shift);
+    }
+};
+
+template <>
+struct Codec<__nv_bfloat16> {
+    using R = float;
+    static __device__ __forceinline__ float decode(__nv_bfloat16 v, float shift) {
+        return __bfloat162float(v) + shift;
+    }
+    static __device__ __forceinline__ float load(const __nv_bfloat16* p, float s) { return decode(__ldg(p), s); }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, float v, float shift) {
+        *p = __float2bfloat16_rn(v - shift);
+    }
+};
+
+// D2Q9, textbook order: c_0 = (0,0); c_1..c_4 = (1,0),(0,1),(-1,0),(0,-1);
+// c_5..c_8 = (1,1),(-1,1),(-1,-1),(1,-1).  opp = {0,3,4,1,2,7,8,5,6}.
+__host__ __device__ __forceinline__ int d2q9_cx(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ __forceinline__ int d2q9_cy(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ __forceinline__ int d2q9_opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ R weight_of(int i) {
+    return i == 0 ? R(4.0 / 9.0) : (i <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+}
+
+// Lattice weights in the arithmetic type.  In FP32 the correctly rounded
+// values of 4/9, 1/9 and 1/36 sum to 1 + 7.45e-9, which would create mass at
+// every node and step (a drift of ~7e-6 relative after 1000 steps); taking
+// 1/36 one ulp below its rounded value makes the nine FP32 weights sum to
+// exactly 1, so the equilibrium conserves mass in FP32.  FP64 keeps the
+// rounded values (their sum is off by < 1e-16).
+template <typename R>
+struct Weights {
+    static __device__ __forceinline__ R w0() { return R(4.0 / 9.0); }
+    static __device__ __forceinline__ R w1() { return R(1.0 / 9.0); }
+    static __device__ __forceinline__ R w5() { return R(1.0 / 36.0); }
+};
+template <>
+struct Weights<float> {
+    static __device__ __forceinline__ float w0() { return __int_as_float(0x3EE38E39); }  // 4/9
+    static __device__ __forceinline__ float w1() { return __int_as_float(0x3DE38E39); }  // 1/9
+    static __device__ __forceinline__ float w5() { return __int_as_float(0x3CE38E38); }  // 1/36 - 1 ulp
+};
+
+// Eq. (feq) with T0 = 1/3, written by parity of c_i.u:
+//   f_i^eq = w_i rho [E + O],  E = 1 - 1.5 u^2 + 4.5 (c.u)^2,
+//                              O = (c.u) (3 - k3 u^2 + k3 (c.u)^2),
+// k3 = 4.5 for the cubic equilibrium; opposite directions share E and flip O.
+template <typename R>
+__device__ __forceinline__ void equilibrium(R rho, R ux, R uy, R k3, R (&out)[9]) {
+    const R uu = ux * ux + uy * uy;
+    const R A = R(1) - R(1.5) * uu;
+    const R B = R(3) - k3 * uu;
+    const R w0 = rho * Weights<R>::w0(), w1 = rho * Weights<R>::w1(), w5 = rho * Weights<R>::w5();
+    out[0] = w0 * A;
+    {
+        const R c = ux, c2 = c * c, e = A + R(4.5) * c2, o = c * (B + k3 * c2);
+        out[1] = w1 * (e + o);
+        out[3] = w1 * (e - o);
+    }
+    {
+        const R c = uy, c2 = c * c, e = A + R(4.5) * c2, o = c * (B + k3 * c2);
+        out[2] = w1 * (e + o);
+        out[4] = w1 * (e - o);
+    }
+    {
+        const R c = ux + uy, c2 = c * c, e = A + R(4.5) * c2, o = c * (B + k3 * c2);
+        out[5] = w5 * (e + o);
+        out[7] = w5 * (e - o);
+    }
+    {
+        const R c = uy - ux, c2 = c * c, e = A + R(4.5) * c2, o = c * (B + k3 * c2);
+        out[6] = w5 * (e + o);
+        out[8] = w5 * (e - o);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_max(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Parameters of one launch in the arithmetic type, loaded once per thread.
+template <typename R>
+struct NodeParams {
+    R G, gx, gy, rw0, rw1, nu0, nu1, k3;
+    R sh0[3], sh1[3];   // storage shifts w rho_ref for weight classes 0 (rest), 1, 2 (diagonal)
+    __device__ __forceinline__ void load(const StepParams* __restrict__ p) {
+        G = R(p->G);
+        gx = R(p->g[0]);
+        gy = R(p->g[1]);
+        rw0 = R(p->rho_wall[0]);
+        rw1 = R(p->rho_wall[1]);
+        nu0 = R(p->nu[0]);
+        nu1 = R(p->nu[1]);
+        k3 = R(p->k3);
+        const R r0 = R(p->rho_ref[0]), r1 = R(p->rho_ref[1]);
+        sh0[0] = r0 * R(4.0 / 9.0);
+        sh0[1] = r0 * R(1.0 / 9.0);
+        sh0[2] = r0 * R(1.0 / 36.0);
+        sh1[0] = r1 * R(4.0 / 9.0);
+        sh1[1] = r1 * R(1.0 / 9.0);
+        sh1[2] = r1 * R(1.0 / 36.0);
+    }
+};
+
+__host__ __device__ __forceinline__ int weight_class(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
+
+// Per-thread observables of one step.
+template <typename R>
+struct ObsLocal {
+    R m0 = R(0), m1 = R(0), px = R(0), umax2 = R(0);
+    bool bad = false;
+};
+
+// Force, moments and BGK collision at one fluid node, then the store of the
+// 18 post-collision populations (and of their periodic ghost images).
+//   f[a][i]   pulled populations, rho0/rho1 their sums
+//   nb[b][k]  rho^b at the 8 neighbours x + c_k (k = 1..8 in index k-1)
+//   dst       pointer to element (x, y) of plane (species 0, direction 0)
+//   x, nx     the node's column and the grid width (ghost images when periodic)
+template <typename S, typename R>
+__device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1, const R (&nb)[2][8],
+                                              const NodeParams<R>& P, S* __restrict__ dst, int plane,
+                                              int x, int nx, int periodic, ObsLocal<R>& ob) {
+    using C = Codec<S>;
+    // sum_i w_i c_i rho^b(x + c_i), neighbours in direction order 1..8
+    R sx[2], sy[2];
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        const R e = nb[b][0], n = nb[b][1], wv = nb[b][2], so = nb[b][3];
+        const R ne = nb[b][4], nw = nb[b][5], sw = nb[b][6], se = nb[b][7];
+        sx[b] = (e - wv) * R(1.0 / 9.0) + (ne - nw - sw + se) * R(1.0 / 36.0);
+        sy[b] = (n - so) * R(1.0 / 9.0) + (ne + nw - sw - se) * R(1.0 / 36.0);
+    }
+    const R ax0 = P.G * sx[1] + P.gx, ay0 = P.G * sy[1] + P.gy;   // species o feels rho^w
+    const R ax1 = P.G * sx[0] + P.gx, ay1 = P.G * sy[0] + P.gy;   // species w feels rho^o
+
+    R jx[2], jy[2];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        jx[a] = (f[a][1] - f[a][3]) + (f[a][5] - f[a][7]) + (f[a][8] - f[a][6]);
+        jy[a] = (f[a][2] - f[a][4]) + (f[a][5] - f[a][7]) + (f[a][6] - f[a][8]);
+    }
+    const R rt = rho0 + rho1;
+    const R inv_rt = R(1) / rt;
+    const R ux = (jx[0] + jx[1]) * inv_rt;
+    const R uy = (jy[0] + jy[1]) * inv_rt;
+    const R nu_mix = (rho0 * P.nu0 + rho1 * P.nu1) * inv_rt;
+    const R om1 = R(1) - R(1) / (R(3) * nu_mix + R(0.5));   // 1 - 1/tau_mix
+    R out[2][9];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        const R rho = a ? rho1 : rho0;
+        const R ax = a ? ax1 : ax0, ay = a ? ay1 : ay0;
+        R fu[9], fs[9];
+        equilibrium<R>(rho, ux, uy, P.k3, fu);
+        equilibrium<R>(rho, ux + ax, uy + ay, P.k3, fs);
+        S* d = dst + a * 9 * plane;
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            out[a][i] = fs[i] + om1 * (f[a][i] - fu[i]);
+            C::store(d + i * plane, out[a][i], a ? P.sh1[weight_class(i)] : P.sh0[weight_class(i)]);
+        }
+    }
+    // periodic ghost images of columns 0, 1, nx - 2, nx - 1 (ghost columns
+    // -2, -1, nx, nx + 1 hold columns (nx - 2, nx - 1, 0, 1) mod nx)
+    if (periodic && (x < 2 || x >= nx - 2)) {
+        const int gcols[4] = {-2, -1, nx, nx + 1};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int m = gcols[k] % nx;
+            if (m < 0) m += nx;
+            if (m != x) continue;
+            const int off = gcols[k] - x;
+#pragma unroll
+            for (int a = 0; a < 2; a++)
+#pragma unroll
+                for (int i = 0; i < 9; i++)
+                    C::store(dst + a * 9 * plane + i * plane + off, out[a][i],
+                             a ? P.sh1[weight_class(i)] : P.sh0[weight_class(i)]);
+        }
+    }
+    ob.m0 += rho0;
+    ob.m1 += rho1;
+    ob.px += jx[0] + R(0.5) * rho0 * ax0;
+    const R vx = ux + R(0.5) * (rho0 * ax0 + rho1 * ax1) * inv_rt;
+    const R vy = uy + R(0.5) * (rho0 * ay0 + rho1 * ay1) * inv_rt;
+    ob.umax2 = fmax(ob.umax2, vx * vx + vy * vy);
+    ob.bad = ob.bad || !(rho0 >= R(0) && rho1 >= R(0));
+}
+
+// Macroscopic fields at one node (fields mode).
+template <typename R>
+__device__ __forceinline__ void node_fields(const R (&f)[2][9], R rho0, R rho1, const R (&nb)[2][8],
+                                            const NodeParams<R>& P, double* __restrict__ out,
+                                            size_t fplane) {
+    R sx[2], sy[2];
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+        const R e = nb[b][0], n = nb[b][1], wv = nb[b][2], so = nb[b][3];
+        const R ne = nb[b][4], nw = nb[b][5], sw = nb[b][6], se = nb[b][7];
+        sx[b] = (e - wv) * R(1.0 / 9.0) + (ne - nw - sw + se) * R(1.0 / 36.0);
+        sy[b] = (n - so) * R(1.0 / 9.0) + (ne + nw - sw - se) * R(1.0 / 36.0);
+    }
+    const R ax0 = P.G * sx[1] + P.gx, ay0 = P.G * sy[1] + P.gy;
+    const R ax1 = P.G * sx[0] + P.gx, ay1 = P.G * sy[0] + P.gy;
+    R jx = R(0), jy = R(0);
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        jx += (f[a][1] - f[a][3]) + (f[a][5] - f[a][7]) + (f[a][8] - f[a][6]);
+        jy += (f[a][2] - f[a][4]) + (f[a][5] - f[a][7]) + (f[a][6] - f[a][8]);
+    }
+    const R rt = rho0 + rho1;
+    const R inv_rt = R(1) / rt;
+    out[0] = double(rho0);
+    out[fplane] = double(rho1);
+    out[2 * fplane] = double((jx + R(0.5) * (rho0 * ax0 + rho1 * ax1)) * inv_rt);
+    out[3 * fplane] = double((jy + R(0.5) * (rho0 * ay0 + rho1 * ay1)) * inv_rt);
+    out[4 * fplane] = double(R(1.0 / 3.0) * rt - P.G * R(1.0 / 3.0) * rho0 * rho1);
+}
+
+// Block reduction of the per-thread observables, FP64 atomics into `acc`, and
+// finalisation of the step by the last CTA to arrive.
+template <typename R, int NT>
+__device__ __forceinline__ void reduce_observables(ObsLocal<R> ob, ObsAccum* __restrict__ acc,
+                                                   ObsState* __restrict__ obs, bool timed_out) {
+    __shared__ R red[NT / 32][4];
+    __shared__ unsigned red_bad;
+    __shared__ bool is_last;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) red_bad = timed_out ? 2u : 0u;
+    R m0 = warp_sum(ob.m0), m1 = warp_sum(ob.m1), px = warp_sum(ob.px), u2 = warp_max(ob.umax2);
+    const unsigned any_bad = __any_sync(0xffffffffu, ob.bad);
+    __syncthreads();
+    if (lane == 0) {
+        red[warp][0] = m0;
+        red[warp][1] = m1;
+        red[warp][2] = px;
+        red[warp][3] = u2;
+        if (any_bad) atomicOr(&red_bad, 1u);
+    }
+    __syncthreads();
+    if (t == 0) {
+        double a = 0.0, b = 0.0, c = 0.0, d = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; w++) {
+            a += double(red[w][0]);
+            b += double(red[w][1]);
+            c += double(red[w][2]);
+            d = fmax(d, double(red[w][3]));
+        }
+        atomicAdd(&acc->mass[0], a);
+        atomicAdd(&acc->mass[1], b);
+        atomicAdd(&acc->px, c);
+        atomicMax(&acc->umax2_bits, (unsigned long long)__double_as_longlong(d));
+        if (red_bad) atomicOr(&acc->bad, red_bad);
+        __threadfence();
+        const unsigned ticket = atomicAdd(&acc->blocks_done, 1u);
+        is_last = ticket == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (is_last && t == 0) {
+        __threadfence();
+        const double ma = __ldcg(&acc->mass[0]);
+        const double mb = __ldcg(&acc->mass[1]);
+        const double p = __ldcg(&acc->px);
+        const double u2s = __longlong_as_double((long long)__ldcg(&acc->umax2_bits));
+        const unsigned nb = __ldcg(&acc->bad);
+        obs->mass[0] = ma;
+        obs->mass[1] = mb;
+        obs->px = p;
+        obs->umax = sqrt(u2s);
+        if (ma > 0.0) obs->disp += p / ma;
+        obs->step += 1;
+        if (nb & 1u) obs->nan_flag = 1;
+        if (nb & 2u) obs->timeout_flag = 1;
+        acc->mass[0] = 0.0;
+        acc->mass[1] = 0.0;
+        acc->px = 0.0;
+        acc->umax2_bits = 0ull;
+        acc->bad = 0u;
+        __threadfence();
+        acc->blocks_done = 0u;
+    }
+}
+
+}  // namespace gb300lbm

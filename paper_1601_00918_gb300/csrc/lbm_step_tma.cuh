@@ -1,0 +1,322 @@
+// Two-component D2Q9 time step, "staged" variant: rows of all 18 population
+// planes are moved from HBM to shared memory by the Tensor Memory Accelerator.
+//
+// Same method and same marching structure as the simple variant (see
+// lbm_step.cuh): a CTA owns BX columns and marches down a strip of rows,
+// pulling row r + 1 while colliding row r.  The difference is where the
+// pulled values come from.  One elected thread keeps D + 3 row stages in a
+// shared-memory ring: each stage is ONE cp.async.bulk.tensor.3d copy of a
+// box {BX + 16 columns, 1 row, 18 planes} plus one 2-D copy of the row's
+// link words, both completing on the stage's mbarrier.  Stages are issued up
+// to D rows ahead, so the loads of the next rows are in flight while the
+// CTA computes; the pull itself (with bounce-back) reads shared memory.  The
+// 8-column ghost margins of the layout make every box a plain rectangle:
+// periodic wrap in x needs no patch, and rows wrap in y by coordinate.
+//
+// Each column block only stages and marches over the rows that contain
+// fluid in its columns (a per-block row range computed at set-up), so the
+// solid bands of a channel are neither read nor written.
+//
+// Every wait on an mbarrier is bounded; a wait that gives up marks the step
+// (ObsState.timeout_flag) and the CTA carries on to its end without hanging
+// the barriers of the other threads, then waits (bounded) for its own copies
+// in flight before it exits.
+#pragma once
+
+#include <cuda.h>
+
+#include "lbm_common.cuh"
+
+namespace gb300lbm {
+
+constexpr unsigned kWaitLimit = 1u << 20;   // try_wait polls before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false if the phase did not complete within kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (unsigned i = 0; i < kWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Shared-memory plan of the staged kernel (host and device agree on it).
+template <typename S, int BX, int D>
+struct StagedPlan {
+    static constexpr int kW = BX + 2 * kGhost;            // staged columns per row
+    static constexpr int kStages = D + 3;                 // ring: rows r..r+2 in use + D ahead
+    static constexpr int kPopBytes = 18 * kW * (int)sizeof(S);
+    static constexpr int kPopSlot = (kPopBytes + 127) / 128 * 128;
+    static constexpr int kLinkSlot = (kW * 2 + 127) / 128 * 128;
+    static constexpr int kSlot = kPopSlot + kLinkSlot;
+    static constexpr int kRhoBytes = 4 * 2 * (BX + 2) * (int)sizeof(typename Codec<S>::R);
+    static constexpr int kBarOffset = kStages * kSlot;
+    static constexpr int kRhoOffset = kBarOffset + ((kStages * 8 + 127) / 128) * 128;
+    static constexpr int kBytes = kRhoOffset + kRhoBytes + 128;   // + alignment slack
+    static constexpr uint32_t kTxBytes = (uint32_t)(kPopBytes + kW * 2);
+};
+
+// One time step fin -> fout.  fmap views fin as [18 planes][ny][pitch],
+// lmap views the link words as [ny][pitch]; fout points at logical column 0
+// of row 0.  rows[cb] = (first, last) row with fluid in column block cb.
+template <typename S, int BX, int D>
+__global__ void __launch_bounds__(BX) step_staged_kernel(const __grid_constant__ CUtensorMap fmap,
+                                                         const __grid_constant__ CUtensorMap lmap,
+                                                         S* __restrict__ fout,
+                                                         const int2* __restrict__ rows,
+                                                         const StepParams* __restrict__ prm,
+                                                         ObsAccum* __restrict__ acc,
+                                                         ObsState* __restrict__ obs, Grid grid) {
+    using C = Codec<S>;
+    using R = typename C::R;
+    using Plan = StagedPlan<S, BX, D>;
+    constexpr int W = Plan::kW;
+    constexpr int NS = Plan::kStages;
+    constexpr unsigned kSolid = 1u << kSolidBit;
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    uint64_t* bars = (uint64_t*)(smem + Plan::kBarOffset);
+    R(*s_rho)[2][BX + 2] = (R(*)[2][BX + 2])(smem + Plan::kRhoOffset);
+    auto pops = [&](int stage) { return (const S*)(smem + (stage % NS) * Plan::kSlot); };
+    auto lnks = [&](int stage) {
+        return (const uint16_t*)(smem + (stage % NS) * Plan::kSlot + Plan::kPopSlot);
+    };
+
+    const int nx = grid.nx, ny = grid.ny, pitch = grid.pitch;
+    const int plane = ny * pitch;
+    const int t = threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    const int cb = blockIdx.x;
+    const int x0 = cb * BX;
+
+    // this CTA's strip of the block's fluid rows
+    const int2 rr = rows[cb];
+    const int nrows = rr.y - rr.x + 1;
+    const int rpb = nrows > 0 ? (nrows + grid.strips - 1) / grid.strips : 0;
+    const int y0 = rr.x + blockIdx.y * rpb;
+    const int y1 = min(y0 + rpb, rr.y + 1);
+    const bool empty = nrows <= 0 || y0 >= y1;
+    const int n_stage = empty ? 0 : (y1 - y0) + 4;   // rows y0 - 2 .. y1 + 1
+
+    NodeParams<R> P;
+    P.load(prm);
+
+    const int gxc = x0 + t;
+    const bool active = gxc < nx;
+    const bool rho_col = gxc <= nx;                 // thread nx - x0 pulls the image column nx
+    const int wi = t + kGhost;                      // this thread's column in the staged window
+
+    auto wrap_y = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
+    auto slot = [&](int r) { return (r - y0 + 1) & 3; };
+
+    bool timed_out = false;
+    int next_issue = 0;                             // used by thread 0 only
+    auto issue = [&](int j) {
+        uint64_t* bar = &bars[j % NS];
+        const int row = wrap_y(y0 - 2 + j);
+        mbar_expect_tx(bar, Plan::kTxBytes);
+        tma_load_3d((void*)pops(j), &fmap, x0, row, 0, bar);
+        tma_load_2d((void*)lnks(j), &lmap, x0, row, bar);
+    };
+    // after one wait gave up the data is invalid anyway: skip the others
+    auto wait_stage = [&](int j) {
+        if (!timed_out && !mbar_wait(&bars[j % NS], (uint32_t)((j / NS) & 1))) timed_out = true;
+    };
+
+    // Pull the populations of the row held by stage jc (rows above/below in
+    // jm/jp) at window column w.  Returns true at a solid node.
+    auto pull = [&](int jm, int jc, int jp, int w, R(&f)[2][9], R& r0, R& r1) -> bool {
+        const unsigned lk = lnks(jc)[w];
+        if (lk & kSolid) {
+            r0 = P.rw0;
+            r1 = P.rw1;
+            return true;
+        }
+        const S* pm = pops(jm);
+        const S* pc = pops(jc);
+        const S* pp = pops(jp);
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            const int b = a * 9 * W;
+            const R* sh = a ? P.sh1 : P.sh0;
+            // direction i pulls from (x - c_ix, y - c_iy); bounced: own opp(i)
+            f[a][0] = C::decode(pc[b + 0 * W + w], sh[0]);
+            f[a][1] = C::decode((lk & (1u << 1)) ? pc[b + 3 * W + w] : pc[b + 1 * W + w - 1], sh[1]);
+            f[a][2] = C::decode((lk & (1u << 2)) ? pc[b + 4 * W + w] : pm[b + 2 * W + w], sh[1]);
+            f[a][3] = C::decode((lk & (1u << 3)) ? pc[b + 1 * W + w] : pc[b + 3 * W + w + 1], sh[1]);
+            f[a][4] = C::decode((lk & (1u << 4)) ? pc[b + 2 * W + w] : pp[b + 4 * W + w], sh[1]);
+            f[a][5] = C::decode((lk & (1u << 5)) ? pc[b + 7 * W + w] : pm[b + 5 * W + w - 1], sh[2]);
+            f[a][6] = C::decode((lk & (1u << 6)) ? pc[b + 8 * W + w] : pm[b + 6 * W + w + 1], sh[2]);
+            f[a][7] = C::decode((lk & (1u << 7)) ? pc[b + 5 * W + w] : pp[b + 7 * W + w + 1], sh[2]);
+            f[a][8] = C::decode((lk & (1u << 8)) ? pc[b + 6 * W + w] : pp[b + 8 * W + w - 1], sh[2]);
+        }
+        R a = R(0), bsum = R(0);
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            a += f[0][i];
+            bsum += f[1][i];
+        }
+        r0 = a;
+        r1 = bsum;
+        return false;
+    };
+
+    // Densities of the halo columns x0 - 1 (warp 0) and x0 + BX (warp 1),
+    // lanes 0..8 species o, lanes 16..24 species w, from the staged window.
+    auto halo = [&](int jm, int jc, int jp, int sl) {
+        if (warp >= 2) return;
+        const bool right = warp == 1;
+        if (right && x0 + BX > nx) return;          // image column pulled by a thread instead
+        const int w = right ? BX + kGhost : kGhost - 1;
+        const unsigned lk = lnks(jc)[w];
+        const int sp = lane >> 4, i = lane & 15;
+        R v = R(0);
+        if (!(lk & kSolid) && i < 9) {
+            const S* src;
+            int col;
+            if (lk & (1u << i)) {
+                src = pops(jc) + (sp * 9 + d2q9_opp(i)) * W;
+                col = w;
+            } else {
+                const int cy = d2q9_cy(i);
+                src = (cy > 0 ? pops(jm) : (cy < 0 ? pops(jp) : pops(jc))) + (sp * 9 + i) * W;
+                col = w - d2q9_cx(i);
+            }
+            v = C::decode(src[col], weight_of<R>(i) * R(prm->rho_ref[sp]));
+        }
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        if ((lane & 15) == 0) s_rho[sl][sp][right ? BX + 1 : 0] = (lk & kSolid) ? (sp ? P.rw1 : P.rw0) : v;
+    };
+
+    if (t == 0) {
+        for (int s = 0; s < NS; s++) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    ObsLocal<R> ob;
+    if (!empty) {
+        if (t == 0) {
+            while (next_issue < NS && next_issue < n_stage) issue(next_issue++);
+        }
+        R cur[2][9], nxt[2][9];
+        R rc0 = R(0), rc1 = R(0), rn0 = R(0), rn1 = R(0);
+        bool solid_cur = true, solid_nxt = true;
+
+        // prologue: densities of rows y0 - 1 (stages 0,1,2) and y0 (1,2,3)
+        wait_stage(0);
+        wait_stage(1);
+        wait_stage(2);
+        if (rho_col) {
+            R tmp[2][9], a, b;
+            pull(0, 1, 2, wi, tmp, a, b);
+            s_rho[slot(y0 - 1)][0][t + 1] = a;
+            s_rho[slot(y0 - 1)][1][t + 1] = b;
+        }
+        halo(0, 1, 2, slot(y0 - 1));
+        wait_stage(3);
+        if (rho_col) {
+            solid_cur = pull(1, 2, 3, wi, cur, rc0, rc1);
+            s_rho[slot(y0)][0][t + 1] = rc0;
+            s_rho[slot(y0)][1][t + 1] = rc1;
+        }
+        halo(1, 2, 3, slot(y0));
+
+        for (int r = y0; r < y1; ++r) {
+            const int j = r - y0 + 2;                 // stages j, j+1, j+2 hold rows r, r+1, r+2
+            const int sn = slot(r + 1);
+            wait_stage(j + 2);
+            if (rho_col) {
+                solid_nxt = pull(j, j + 1, j + 2, wi, nxt, rn0, rn1);
+                s_rho[sn][0][t + 1] = rn0;
+                s_rho[sn][1][t + 1] = rn1;
+            }
+            halo(j, j + 1, j + 2, sn);
+            __syncthreads();
+            // every stage <= j is now free: refill the ring
+            if (t == 0) {
+                while (next_issue <= j + NS && next_issue < n_stage) issue(next_issue++);
+            }
+            if (active && !solid_cur) {
+                const int s0 = slot(r), sm = slot(r - 1), sp = sn;
+                R nb[2][8];
+#pragma unroll
+                for (int b = 0; b < 2; b++) {
+                    nb[b][0] = s_rho[s0][b][t + 2];   // c_1 = ( 1, 0)
+                    nb[b][1] = s_rho[sp][b][t + 1];   // c_2 = ( 0, 1)
+                    nb[b][2] = s_rho[s0][b][t];       // c_3 = (-1, 0)
+                    nb[b][3] = s_rho[sm][b][t + 1];   // c_4 = ( 0,-1)
+                    nb[b][4] = s_rho[sp][b][t + 2];   // c_5 = ( 1, 1)
+                    nb[b][5] = s_rho[sp][b][t];       // c_6 = (-1, 1)
+                    nb[b][6] = s_rho[sm][b][t];       // c_7 = (-1,-1)
+                    nb[b][7] = s_rho[sm][b][t + 2];   // c_8 = ( 1,-1)
+                }
+                collide_store<S, R>(cur, rc0, rc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx,
+                                    grid.periodic_x, ob);
+            }
+#pragma unroll
+            for (int a = 0; a < 2; a++)
+#pragma unroll
+                for (int i = 0; i < 9; i++) cur[a][i] = nxt[a][i];
+            rc0 = rn0;
+            rc1 = rn1;
+            solid_cur = solid_nxt;
+        }
+    }
+    const bool any_timeout = __syncthreads_or(timed_out) != 0;
+    if (any_timeout && t == 0) {
+        // a wait gave up: let the copies still in flight land before exit
+        for (int j = max(0, next_issue - NS); j < next_issue; j++) mbar_wait(&bars[j % NS], (uint32_t)((j / NS) & 1));
+    }
+    reduce_observables<R, BX>(ob, acc, obs, any_timeout);
+}
+
+}  // namespace gb300lbm

@@ -25,7 +25,8 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": L
 
 # symbols declared in include/lbm.h
 EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "lbm_get_fields",
-           "lbm_set_body_force", "lbm_save", "lbm_load", "lbm_destroy", "lbm_last_error")
+           "lbm_set_body_force", "lbm_save", "lbm_load", "lbm_kernel_info", "lbm_destroy",
+           "lbm_last_error")
 
 
 class LbmError(RuntimeError):
@@ -40,6 +41,7 @@ class Params(ctypes.Structure):
                 ("tau", ctypes.c_double * 2), ("G", ctypes.c_double),
                 ("rho_wall", ctypes.c_double * 2), ("g", ctypes.c_double * 2),
                 ("precision", ctypes.c_int32), ("eq_order", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -48,12 +50,12 @@ class Obs(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double * 2), ("oil_mom_x", ctypes.c_double),
                 ("oil_disp_x", ctypes.c_double), ("max_u", ctypes.c_double),
                 ("step", ctypes.c_int64), ("nan_flag", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("timeout_flag", ctypes.c_int32)]
 
     def as_dict(self):
         return {"mass": (self.mass[0], self.mass[1]), "oil_mom_x": self.oil_mom_x,
                 "oil_disp_x": self.oil_disp_x, "max_u": self.max_u, "step": self.step,
-                "nan_flag": self.nan_flag}
+                "nan_flag": self.nan_flag, "timeout_flag": self.timeout_flag}
 
 
 _lib = None
@@ -79,12 +81,13 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_set_body_force.argtypes = [vp, ctypes.c_double, ctypes.c_double]
     lib.lbm_save.argtypes = [vp, dp]
     lib.lbm_load.argtypes = [vp, dp]
+    lib.lbm_kernel_info.argtypes = [vp, P(ctypes.c_int32)]
     lib.lbm_destroy.argtypes = [vp]
     lib.lbm_destroy.restype = None
     lib.lbm_last_error.argtypes = [vp]
     lib.lbm_last_error.restype = ctypes.c_char_p
     for name in ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables",
-                 "lbm_get_fields", "lbm_set_body_force", "lbm_save", "lbm_load"):
+                 "lbm_get_fields", "lbm_set_body_force", "lbm_save", "lbm_load", "lbm_kernel_info"):
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -102,13 +105,17 @@ def _check(rc, handle=None):
     return rc
 
 
+VARIANTS = {"auto": 0, "simple": 1, "staged": 2}
+
+
 def make_params(nx, ny, tau=(1.0, 1.0), G=0.0, rho_wall=(0.0, 0.0), g=(0.0, 0.0),
                 periodic=(True, True), precision="fp32", eq_order=3, stream=None,
-                workspace=None, workspace_bytes=0) -> Params:
+                workspace=None, workspace_bytes=0, variant="auto") -> Params:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     return Params(int(nx), int(ny), int(periodic[0]), int(periodic[1]),
                   (ctypes.c_double * 2)(*tau), float(G), (ctypes.c_double * 2)(*rho_wall),
-                  (ctypes.c_double * 2)(*g), prec, int(eq_order),
+                  (ctypes.c_double * 2)(*g), prec, int(eq_order), var, 0,
                   ctypes.c_void_p(stream) if stream else None,
                   ctypes.c_void_p(workspace) if workspace else None, int(workspace_bytes))
 
@@ -167,6 +174,13 @@ def lbm_load(h, f):
     _check(library().lbm_load(h, _dptr(f)), h)
 
 
+def lbm_kernel_info(h) -> dict:
+    info = (ctypes.c_int32 * 4)()
+    _check(library().lbm_kernel_info(h, info), h)
+    return {"variant": {1: "simple", 2: "staged"}.get(info[0], str(info[0])), "depth": info[1],
+            "rows_per_cta": info[2], "strips": info[3]}
+
+
 def lbm_destroy(h):
     if h:
         library().lbm_destroy(h)
@@ -181,7 +195,7 @@ class Simulation:
 
     def __init__(self, mask, rho_init, tau=(1.0, 1.0), G=0.0, rho_wall=(0.0, 0.0),
                  g=(0.0, 0.0), periodic=(True, True), precision="fp32", eq_order=3,
-                 device=0, use_torch_arena=True):
+                 device=0, use_torch_arena=True, variant="auto"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -191,7 +205,7 @@ class Simulation:
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream
             p = make_params(self.nx, self.ny, tau, G, rho_wall, g, periodic, precision, eq_order,
-                            stream=stream)
+                            stream=stream, variant=variant)
             self._arena = None
             if use_torch_arena:
                 nbytes = lbm_workspace_size(p)
@@ -211,6 +225,9 @@ class Simulation:
 
     def fields(self):
         return lbm_get_fields(self.h, self.nx, self.ny)
+
+    def kernel_info(self):
+        return lbm_kernel_info(self.h)
 
     def set_body_force(self, gx, gy=0.0):
         lbm_set_body_force(self.h, gx, gy)

@@ -40,12 +40,19 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_workspace_size_formula(lib):
+    """Two population buffers with 8 ghost columns a side (pitch = nx + 16
+    rounded up to 32), the link words, one fluid-row range per 128 columns,
+    parameters, two accumulator and two observable blocks, each 256-aligned."""
     p = lbm.make_params(100, 30, precision="fp32")
     pitch = 128
     buf = 18 * 30 * pitch * 4
     buf = (buf + 255) // 256 * 256
     links = (30 * pitch * 2 + 255) // 256 * 256
-    assert lbm.lbm_workspace_size(p) == 2 * buf + links + 3 * 256
+    assert lbm.lbm_workspace_size(p) == 2 * buf + links + 256 + 256 + 2 * 256 + 2 * 256
+    p = lbm.make_params(113, 30, precision="fp32")          # 113 + 16 > 128: pitch 160
+    buf = (18 * 30 * 160 * 4 + 255) // 256 * 256
+    links = (30 * 160 * 2 + 255) // 256 * 256
+    assert lbm.lbm_workspace_size(p) == 2 * buf + links + 256 + 256 + 2 * 256 + 2 * 256
     assert lbm.lbm_workspace_size(lbm.make_params(100, 30, precision="fp16s")) < \
         lbm.lbm_workspace_size(p)
 
