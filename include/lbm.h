@@ -136,10 +136,10 @@ int lbm_save(lbm_t *h, double *f);
 int lbm_load(lbm_t *h, const double *f);
 
 /* Launch configuration the autotuner chose for the step kernel:
- * info[0] = variant (1 simple, 2 staged), info[1] = rows in flight (staged),
- * info[2] = rows per CTA strip (simple), info[3] = strips per column block
- * (staged).  Not part of the paper's method: a report of this library's
- * tuning. */
+ * info[0] = variant (1 simple, 2 staged); info[1] = rows in flight (staged);
+ * info[2] = rows per CTA strip (simple) or columns per CTA (staged);
+ * info[3] = strips per column block (staged).  Not part of the paper's
+ * method: a report of this library's tuning. */
 int lbm_kernel_info(const lbm_t *h, int32_t info[4]);
 
 /* Free the handle and the device memory it owns.  NULL is ignored. */

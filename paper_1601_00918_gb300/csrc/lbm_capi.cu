@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -39,7 +40,8 @@ using namespace gb300lbm;
 
 namespace {
 
-constexpr int kBX = 128;         // columns per CTA (both kernels)
+constexpr int kBX = 128;         // columns per CTA of the simple kernel
+constexpr int kRowBlock = 64;    // column granularity of the fluid-row table
 constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity is kept)
 
 struct Tuned {
@@ -47,6 +49,7 @@ struct Tuned {
     int depth = 2;     // staged: rows in flight
     int rpb = 16;      // simple: rows per CTA strip
     int strips = 1;    // staged: strips per column block
+    int bx = 128;      // staged: columns per CTA (64 or 128)
 };
 
 }  // namespace
@@ -55,6 +58,7 @@ struct lbm_t {
     lbm_params p{};
     int pitch = 0;
     int ncb = 0;                  // 128-column blocks
+    int nrb = 0;                  // 64-column blocks of the fluid-row table
     size_t elem = 0;              // bytes per stored population
     size_t buf_bytes = 0;         // one population buffer
     void* arena = nullptr;
@@ -71,8 +75,8 @@ struct lbm_t {
     StepParams hprm{};
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;       // private stream for graph capture
-    CUtensorMap fmap[2];
-    CUtensorMap lmap;
+    CUtensorMap fmap[2][2];       // [buffer][box width 64 + 16 or 128 + 16]
+    CUtensorMap lmap[2];
     bool maps_ok = false;
     Tuned tune;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -116,8 +120,12 @@ size_t elem_size(int prec) {
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
+// planes per buffer: 18 populations, plus the two density planes of the
+// 16-bit node-shifted formats
+int planes_of(int prec) { return (prec == LBM_FP16S || prec == LBM_BF16S) ? 20 : 18; }
+
 struct Layout {
-    int pitch, ncb;
+    int pitch, ncb, nrb;
     size_t buf, links, rows, prm, acc, obs, total;
 };
 
@@ -127,12 +135,14 @@ bool layout_of(const lbm_params* p, Layout* L) {
     if (p->nx > (1 << 24) || p->ny > (1 << 24)) return false;
     L->pitch = (p->nx + 2 * kGhost + 31) / 32 * 32;
     L->ncb = (p->nx + kBX - 1) / kBX;
+    L->nrb = (p->nx + kRowBlock - 1) / kRowBlock;
     const size_t plane = (size_t)p->ny * L->pitch;
-    // kernel indices are 32-bit: all 18 planes must stay below 2^31 elements
-    if (plane * 18 >= (size_t(1) << 31)) return false;
-    L->buf = align256(plane * 18 * es);
+    const size_t np = (size_t)planes_of(p->precision);
+    // kernel indices are 32-bit: all planes must stay below 2^31 elements
+    if (plane * np >= (size_t(1) << 31)) return false;
+    L->buf = align256(plane * np * es);
     L->links = align256(plane * sizeof(uint16_t));
-    L->rows = align256((size_t)L->ncb * sizeof(int2));
+    L->rows = align256((size_t)L->nrb * sizeof(int2));
     L->prm = align256(sizeof(StepParams));
     L->acc = align256(sizeof(ObsAccum));
     L->obs = align256(sizeof(ObsState));
@@ -175,27 +185,27 @@ __global__ void links_kernel(const uint8_t* __restrict__ mask, uint16_t* __restr
 
 template <typename S>
 __global__ void init_kernel(const double* __restrict__ rho, const uint16_t* __restrict__ links,
-                            S* __restrict__ f, int nx, int ny, int pitch, int periodic, double ref0,
-                            double ref1) {
-    using R = typename Codec<S>::R;
+                            S* __restrict__ f, int nx, int ny, int pitch, int periodic) {
+    using C = Codec<S>;
+    using R = typename C::R;
     const int sc = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (sc >= pitch || y >= ny) return;
     const int plane = ny * pitch;
     const int x = logical_col(sc, nx, periodic);
     const bool solid = x == INT_MIN || (links[y * pitch + sc] & (1u << kSolidBit));
+    S* node = f + y * pitch + sc;
     for (int a = 0; a < 2; a++) {
         const double r = solid ? 0.0 : rho[(size_t)a * nx * ny + (size_t)y * nx + x];
-        const double ref = a ? ref1 : ref0;
-        for (int i = 0; i < 9; i++) {
-            const double w = weight_of<double>(i);
-            S* dst = f + (a * 9 + i) * plane + y * pitch + sc;
-            // solid nodes, padding and unused ghosts hold the stored value 0
-            if (solid)
-                Codec<S>::store(dst, R(0), R(0));
-            else
-                Codec<S>::store(dst, R(w * r), R(w * ref));
+        // solid nodes, padding and unused ghosts hold the stored value 0
+        R rh = R(0);
+        if (C::kNodeShift) {
+            const S q = C::rho_store(R(r));
+            node[(18 + a) * plane] = q;
+            rh = C::rho_value(q);
         }
+        for (int i = 0; i < 9; i++)
+            node[(a * 9 + i) * plane] = C::encode(R(weight_of<double>(i) * r), wgt<R>(i), rh);
     }
 }
 
@@ -220,30 +230,35 @@ S* at_col0(char* base) {
     return (S*)base + kGhost;
 }
 
-template <typename S, int D>
+template <typename S, int BX, int D>
 cudaError_t launch_staged(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs,
                           cudaStream_t st) {
-    using Plan = StagedPlan<S, kBX, D>;
+    using Plan = StagedPlan<S, BX, D>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(step_staged_kernel<S, kBX, D>,
+        cudaError_t e = cudaFuncSetAttribute(step_staged_kernel<S, BX, D>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Plan::kBytes);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     Grid g = make_grid(h, 0, h->p.ny);
     g.strips = tn.strips;
-    dim3 grid(h->ncb, tn.strips);
-    step_staged_kernel<S, kBX, D><<<grid, kBX, Plan::kBytes, st>>>(
-        h->fmap[src], h->lmap, at_col0<S>(h->fbase[1 - src]), h->rows, h->dprm, acc, obs, g);
+    dim3 grid((h->p.nx + BX - 1) / BX, tn.strips);
+    step_staged_kernel<S, BX, D><<<grid, BX, Plan::kBytes, st>>>(
+        h->fmap[src][BX == 64 ? 0 : 1], h->lmap[BX == 64 ? 0 : 1], at_col0<S>(h->fbase[1 - src]), h->rows,
+        h->dprm, acc, obs, g);
     return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_one(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs, cudaStream_t st) {
     if (tn.variant == 2) {
-        if (tn.depth >= 4) return launch_staged<S, 4>(h, src, tn, acc, obs, st);
-        return launch_staged<S, 2>(h, src, tn, acc, obs, st);
+        if (tn.bx == 64) {
+            if (tn.depth >= 2) return launch_staged<S, 64, 2>(h, src, tn, acc, obs, st);
+            return launch_staged<S, 64, 1>(h, src, tn, acc, obs, st);
+        }
+        if (tn.depth >= 2) return launch_staged<S, 128, 2>(h, src, tn, acc, obs, st);
+        return launch_staged<S, 128, 1>(h, src, tn, acc, obs, st);
     }
     Grid g = make_grid(h, 0, h->p.ny);
     g.rows_per_block = tn.rpb;
@@ -309,24 +324,29 @@ bool make_maps(lbm_t* h) {
         case LBM_FP16S: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
         default: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
     }
-    const cuuint32_t W = kBX + 2 * kGhost;
-    for (int b = 0; b < 2; b++) {
-        cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)h->p.ny, 18};
-        cuuint64_t strides[2] = {(cuuint64_t)h->pitch * h->elem, (cuuint64_t)h->p.ny * h->pitch * h->elem};
-        cuuint32_t box[3] = {W, 1, 18};
-        cuuint32_t es[3] = {1, 1, 1};
-        if (fn(&h->fmap[b], dt, 3, h->fbase[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    const cuuint32_t np = (cuuint32_t)planes_of(h->p.precision);
+    for (int k = 0; k < 2; k++) {
+        const cuuint32_t W = (k ? 128 : 64) + 2 * kGhost;
+        for (int b = 0; b < 2; b++) {
+            cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)h->p.ny, np};
+            cuuint64_t strides[2] = {(cuuint64_t)h->pitch * h->elem, (cuuint64_t)h->p.ny * h->pitch * h->elem};
+            cuuint32_t box[3] = {W, 1, np};
+            cuuint32_t es[3] = {1, 1, 1};
+            if (fn(&h->fmap[b][k], dt, 3, h->fbase[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
+        }
+        cuuint64_t dims[2] = {(cuuint64_t)h->pitch, (cuuint64_t)h->p.ny};
+        cuuint64_t strides[1] = {(cuuint64_t)h->pitch * 2};
+        cuuint32_t box[2] = {W, 1};
+        cuuint32_t es[2] = {1, 1};
+        if (fn(&h->lmap[k], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h->links, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
     }
-    cuuint64_t dims[2] = {(cuuint64_t)h->pitch, (cuuint64_t)h->p.ny};
-    cuuint64_t strides[1] = {(cuuint64_t)h->pitch * 2};
-    cuuint32_t box[2] = {W, 1};
-    cuuint32_t es[2] = {1, 1};
-    return fn(&h->lmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h->links, dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -356,29 +376,58 @@ std::vector<Tuned> candidates(const lbm_t* h) {
         }
     }
     if ((req == 0 || req == 2) && h->maps_ok) {
-        for (int depth : {2, 4}) {
-            for (int waves : {1, 2, 4}) {
-                Tuned t;
-                t.variant = 2;
-                t.depth = depth;
-                const int resident = sms * (depth >= 4 ? 2 : 3);
-                t.strips = std::max(1, std::min(ny, waves * resident / std::max(1, h->ncb)));
-                out.push_back(t);
+        for (int bx : {64, 128}) {
+            const int ncols = (h->p.nx + bx - 1) / bx;
+            for (int depth : {1, 2}) {
+                for (int waves : {1, 2, 4}) {
+                    Tuned t;
+                    t.variant = 2;
+                    t.bx = bx;
+                    t.depth = depth;
+                    const int resident = sms * (bx == 64 ? 6 : 3);
+                    t.strips = std::max(1, std::min(ny, waves * resident / std::max(1, ncols)));
+                    out.push_back(t);
+                }
             }
         }
     }
-    // dedupe
     std::vector<Tuned> u;
     for (auto& t : out) {
         bool dup = false;
         for (auto& v : u)
-            dup |= v.variant == t.variant && v.depth == t.depth && v.rpb == t.rpb && v.strips == t.strips;
+            dup |= v.variant == t.variant && v.depth == t.depth && v.rpb == t.rpb && v.strips == t.strips &&
+                   v.bx == t.bx;
         if (!dup) u.push_back(t);
     }
     return u;
 }
 
+// GB300LBM_TUNE="staged,<cols per CTA>,<rows in flight>,<strips>" or
+// "simple,<rows per strip>" pins the launch configuration (no timing); used
+// to profile one configuration.
+bool tune_from_env(lbm_t* h) {
+    const char* e = getenv("GB300LBM_TUNE");
+    if (!e || !*e) return false;
+    Tuned t;
+    int a = 0, b = 0, c = 0;
+    if (sscanf(e, "staged,%d,%d,%d", &a, &b, &c) == 3 && (a == 64 || a == 128) && (b == 1 || b == 2) && c >= 1 &&
+        h->maps_ok) {
+        t.variant = 2;
+        t.bx = a;
+        t.depth = b;
+        t.strips = std::min(c, h->p.ny);
+    } else if (sscanf(e, "simple,%d", &a) == 1 && a >= 1) {
+        t.variant = 1;
+        t.rpb = std::min(a, h->p.ny);
+    } else {
+        return false;
+    }
+    h->tune = t;
+    return true;
+}
+
 int autotune(lbm_t* h) {
+    if (tune_from_env(h)) return LBM_OK;
     auto key = std::make_tuple(h->p.nx, h->p.ny, h->p.precision, h->p.periodic_x, h->p.variant, h->fluid_nodes);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -442,6 +491,17 @@ void from_double(void* base, size_t k, int prec, double v) {
     }
 }
 
+// FP32 lattice weights as the device uses them (1/36 one ulp low: the nine
+// sum to exactly 1 in FP32)
+float host_wf(int i) {
+    if (i == 0) return 4.0f / 9.0f;
+    if (i <= 4) return 1.0f / 9.0f;
+    uint32_t bits = 0x3CE38E38u;
+    float w;
+    memcpy(&w, &bits, sizeof w);
+    return w;
+}
+
 int validate(const lbm_params* p, const uint8_t* mask) {
     if (!p) return fail(nullptr, LBM_EINVAL, "params is NULL");
     if (p->nx < 1 || p->ny < 1) return fail(nullptr, LBM_EINVAL, "nx, ny must be >= 1");
@@ -476,7 +536,6 @@ void fill_params(lbm_t* h) {
         s.nu[a] = (h->p.tau[a] - 0.5) / 3.0;
         s.rho_wall[a] = h->p.rho_wall[a];
         s.g[a] = h->p.g[a];
-        s.rho_ref[a] = 0.0;
     }
     s.G = h->p.G;
     s.k3 = h->p.eq_order >= 3 ? 4.5 : 0.0;
@@ -534,13 +593,11 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
     const int nx = p->nx, ny = p->ny;
     const size_t n = (size_t)nx * ny;
 
-    // host checks, reference densities of the 16-bit shift, fluid row ranges
-    double sum[2] = {0.0, 0.0};
+    // host checks and the fluid row range of every column block
     int64_t nfluid = 0;
     Layout L;
     layout_of(p, &L);
-    std::vector<int2> rows(L.ncb, int2{1, 0});
-    for (int cb = 0; cb < L.ncb; cb++) rows[cb] = int2{ny, -1};
+    std::vector<int2> rows(L.nrb, int2{ny, -1});
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
             const size_t k = (size_t)y * nx + x;
@@ -549,10 +606,8 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
             if (!(a >= 0.0) || !(b >= 0.0) || !(a + b > 0.0) || !std::isfinite(a + b))
                 return fail(nullptr, LBM_EINVAL,
                             "rho_init must be finite, >= 0, with positive total at fluid nodes");
-            sum[0] += a;
-            sum[1] += b;
             nfluid++;
-            int2& r = rows[x / kBX];
+            int2& r = rows[x / kRowBlock];
             r.x = std::min(r.x, y);
             r.y = std::max(r.y, y);
         }
@@ -564,6 +619,7 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
     h->fluid_nodes = nfluid;
     h->pitch = L.pitch;
     h->ncb = L.ncb;
+    h->nrb = L.nrb;
     h->elem = elem_size(p->precision);
     h->buf_bytes = L.buf;
 
@@ -602,8 +658,6 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
     h->tobs = (ObsState*)(base + off);
 
     fill_params(h);
-    if (p->precision == LBM_FP16S || p->precision == LBM_BF16S)
-        for (int a = 0; a < 2; a++) h->hprm.rho_ref[a] = nfluid ? sum[a] / nfluid : 0.0;
 
     auto bail = [&](int code) {
         std::string msg = g_create_err;
@@ -633,13 +687,12 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
     CREATE_TRY(cudaMemcpyAsync(h->dprm, &h->hprm, sizeof(StepParams), cudaMemcpyHostToDevice, h->stream));
     dim3 blk(256), grd((h->pitch + 255) / 256, ny);
     links_kernel<<<grd, blk, 0, h->stream>>>(d_mask, h->links, nx, ny, h->pitch, p->periodic_x);
-    const double r0 = h->hprm.rho_ref[0], r1 = h->hprm.rho_ref[1];
     const int px = p->periodic_x;
     switch (p->precision) {
-        case LBM_FP64: init_kernel<double><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (double*)h->fbase[0], nx, ny, h->pitch, px, r0, r1); break;
-        case LBM_FP32: init_kernel<float><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (float*)h->fbase[0], nx, ny, h->pitch, px, r0, r1); break;
-        case LBM_FP16S: init_kernel<__half><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (__half*)h->fbase[0], nx, ny, h->pitch, px, r0, r1); break;
-        default: init_kernel<__nv_bfloat16><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (__nv_bfloat16*)h->fbase[0], nx, ny, h->pitch, px, r0, r1); break;
+        case LBM_FP64: init_kernel<double><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (double*)h->fbase[0], nx, ny, h->pitch, px); break;
+        case LBM_FP32: init_kernel<float><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (float*)h->fbase[0], nx, ny, h->pitch, px); break;
+        case LBM_FP16S: init_kernel<__half><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (__half*)h->fbase[0], nx, ny, h->pitch, px); break;
+        default: init_kernel<__nv_bfloat16><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (__nv_bfloat16*)h->fbase[0], nx, ny, h->pitch, px); break;
     }
     CREATE_TRY(cudaGetLastError());
     // B holds the same zeros at solid nodes, padding and unused ghosts as A
@@ -742,48 +795,64 @@ int lbm_set_body_force(lbm_t* h, double gx, double gy) {
 
 int lbm_save(lbm_t* h, double* f) {
     if (!h || !f) return fail(h, LBM_EINVAL, "NULL argument");
-    const int nx = h->p.nx, ny = h->p.ny, pitch = h->pitch;
+    const int nx = h->p.nx, ny = h->p.ny, pitch = h->pitch, prec = h->p.precision;
+    const size_t plane = (size_t)ny * pitch;
+    const bool shifted = planes_of(prec) == 20;
     std::vector<char> raw(h->buf_bytes);
-    std::vector<uint16_t> lk((size_t)ny * pitch);
+    std::vector<uint16_t> lk(plane);
     CUDA_TRY(h, cudaMemcpyAsync(raw.data(), h->fbase[h->cur], h->buf_bytes, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(lk.data(), h->links, lk.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    for (int a = 0; a < 2; a++)
-        for (int i = 0; i < 9; i++) {
-            const double sh = weight_of<double>(i) * h->hprm.rho_ref[a];
-            for (int y = 0; y < ny; y++)
-                for (int x = 0; x < nx; x++) {
-                    const size_t k = ((size_t)(a * 9 + i) * ny + y) * pitch + kGhost + x;
-                    const bool solid = lk[(size_t)y * pitch + kGhost + x] & (1u << kSolidBit);
-                    f[((size_t)(a * 9 + i) * ny + y) * nx + x] =
-                        solid ? 0.0 : to_double(raw.data(), k, h->p.precision) + sh;
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            const size_t node = (size_t)y * pitch + kGhost + x;
+            const bool solid = lk[node] & (1u << kSolidBit);
+            for (int a = 0; a < 2; a++) {
+                const float rh = shifted ? (float)to_double(raw.data(), (18 + a) * plane + node, prec) : 0.f;
+                for (int i = 0; i < 9; i++) {
+                    const double s = to_double(raw.data(), (a * 9 + i) * plane + node, prec);
+                    // the device decode: s + w_i rhohat as one fused multiply-add in FP32
+                    const double v = shifted ? (double)std::fma(host_wf(i), rh, (float)s) : s;
+                    f[((size_t)(a * 9 + i) * ny + y) * nx + x] = solid ? 0.0 : v;
                 }
+            }
         }
     return LBM_OK;
 }
 
 int lbm_load(lbm_t* h, const double* f) {
     if (!h || !f) return fail(h, LBM_EINVAL, "NULL argument");
-    const int nx = h->p.nx, ny = h->p.ny, pitch = h->pitch;
-    std::vector<uint16_t> lk((size_t)ny * pitch);
+    const int nx = h->p.nx, ny = h->p.ny, pitch = h->pitch, prec = h->p.precision;
+    const size_t plane = (size_t)ny * pitch;
+    const bool shifted = planes_of(prec) == 20;
+    std::vector<uint16_t> lk(plane);
     CUDA_TRY(h, cudaMemcpyAsync(lk.data(), h->links, lk.size() * sizeof(uint16_t), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     std::vector<char> raw(h->buf_bytes, 0);
-    for (int a = 0; a < 2; a++)
-        for (int i = 0; i < 9; i++) {
-            const double sh = weight_of<double>(i) * h->hprm.rho_ref[a];
-            for (int y = 0; y < ny; y++)
-                for (int sc = 0; sc < pitch; sc++) {
-                    // storage column sc holds logical column x, or a periodic image
-                    int x = sc - kGhost;
-                    if (x < 0 || x >= nx) {
-                        if (!h->p.periodic_x || x < -kGhost || x >= nx + kGhost) continue;
-                        x = ((x % nx) + nx) % nx;
-                    }
-                    if (lk[(size_t)y * pitch + kGhost + x] & (1u << kSolidBit)) continue;
-                    const size_t k = ((size_t)(a * 9 + i) * ny + y) * pitch + sc;
-                    from_double(raw.data(), k, h->p.precision, f[((size_t)(a * 9 + i) * ny + y) * nx + x] - sh);
+    for (int y = 0; y < ny; y++)
+        for (int sc = 0; sc < pitch; sc++) {
+            // storage column sc holds logical column x, or a periodic image
+            int x = sc - kGhost;
+            if (x < 0 || x >= nx) {
+                if (!h->p.periodic_x || x < -kGhost || x >= nx + kGhost) continue;
+                x = ((x % nx) + nx) % nx;
+            }
+            if (lk[(size_t)y * pitch + kGhost + x] & (1u << kSolidBit)) continue;
+            const size_t node = (size_t)y * pitch + sc;
+            for (int a = 0; a < 2; a++) {
+                float rh = 0.f;
+                if (shifted) {
+                    double r = 0.0;
+                    for (int i = 0; i < 9; i++) r += f[((size_t)(a * 9 + i) * ny + y) * nx + x];
+                    from_double(raw.data(), (18 + a) * plane + node, prec, r);
+                    rh = (float)to_double(raw.data(), (18 + a) * plane + node, prec);
                 }
+                for (int i = 0; i < 9; i++) {
+                    const double v = f[((size_t)(a * 9 + i) * ny + y) * nx + x];
+                    from_double(raw.data(), (a * 9 + i) * plane + node, prec,
+                                shifted ? (double)std::fma(-host_wf(i), rh, (float)v) : v);
+                }
+            }
         }
     CUDA_TRY(h, cudaMemcpyAsync(h->fbase[h->cur], raw.data(), h->buf_bytes, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->dacc, 0, sizeof(ObsAccum), h->stream));
@@ -795,9 +864,9 @@ int lbm_load(lbm_t* h, const double* f) {
 int lbm_kernel_info(const lbm_t* h, int32_t info[4]) {
     if (!h || !info) return fail(nullptr, LBM_EINVAL, "NULL argument");
     info[0] = h->tune.variant;
-    info[1] = h->tune.depth;
-    info[2] = h->tune.rpb;
-    info[3] = h->tune.strips;
+    info[1] = h->tune.variant == 2 ? h->tune.depth : 0;
+    info[2] = h->tune.variant == 1 ? h->tune.rpb : h->tune.bx;
+    info[3] = h->tune.variant == 2 ? h->tune.strips : 0;
     return LBM_OK;
 }
 

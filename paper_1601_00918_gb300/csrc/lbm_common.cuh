@@ -29,7 +29,6 @@ struct StepParams {
     double g[2];
     double rho_wall[2];
     double k3;           // 4.5 with the cubic terms of Eq. (feq), 0 without
-    double rho_ref[2];   // shift of the 16-bit storage: stored = f - w_i rho_ref^a
 };
 
 // Per-step reduction targets; reset by the last CTA of each step.
@@ -62,7 +61,15 @@ struct Grid {
 };
 
 // ---------------------------------------------------------------------------
-// storage codecs: plain FP64 / FP32, or 16-bit shifted by w_i rho_ref^a
+// storage codecs
+//
+// FP64 / FP32 store f_i as is (18 planes).  The 16-bit formats store
+//   s_i(x) = f*_i(x) - w_i rhohat^a(x)
+// where rhohat^a(x) is the writer node's own density rounded to the 16-bit
+// format and kept in two extra planes (18: species o, 19: species w).  The
+// reader of a population pulled from node x - c_i adds back w_i rhohat^a of
+// that source node, which it reads from the same planes, so the shift is
+// exact and only the small non-equilibrium part s_i is rounded to 16 bits.
 // ---------------------------------------------------------------------------
 template <typename S>
 struct Codec;
@@ -70,39 +77,54 @@ struct Codec;
 template <>
 struct Codec<double> {
     using R = double;
-    static __device__ __forceinline__ double decode(double v, double) { return v; }
-    static __device__ __forceinline__ double load(const double* p, double s) { return decode(__ldg(p), s); }
-    static __device__ __forceinline__ void store(double* p, double v, double) { *p = v; }
+    static constexpr bool kNodeShift = false;
+    static constexpr int kPlanes = 18;
+    static __device__ __forceinline__ double decode(double v, double, double) { return v; }
+    static __device__ __forceinline__ double encode(double v, double, double) { return v; }
+    static __device__ __forceinline__ double rho_store(double r) { return r; }
+    static __device__ __forceinline__ double rho_value(double s) { return s; }
 };
 
 template <>
 struct Codec<float> {
     using R = float;
-    static __device__ __forceinline__ float decode(float v, float) { return v; }
-    static __device__ __forceinline__ float load(const float* p, float s) { return decode(__ldg(p), s); }
-    static __device__ __forceinline__ void store(float* p, float v, float) { *p = v; }
+    static constexpr bool kNodeShift = false;
+    static constexpr int kPlanes = 18;
+    static __device__ __forceinline__ float decode(float v, float, float) { return v; }
+    static __device__ __forceinline__ float encode(float v, float, float) { return v; }
+    static __device__ __forceinline__ float rho_store(float r) { return r; }
+    static __device__ __forceinline__ float rho_value(float s) { return s; }
 };
 
 template <>
 struct Codec<__half> {
     using R = float;
-    static __device__ __forceinline__ float decode(__half v, float shift) { return __half2float(v) + shift; }
-    static __device__ __forceinline__ float load(const __half* p, float s) { return decode(__ldg(p), s); }
-    static __device__ __forceinline__ void store(__half* p, float v, float shift) {
-        *p = __float2half_rn(v - shift);
+    static constexpr bool kNodeShift = true;
+    static constexpr int kPlanes = 20;
+    // f = s + w rhohat and s = f - w rhohat, each one fused multiply-add
+    static __device__ __forceinline__ float decode(__half v, float w, float rh) {
+        return __fmaf_rn(w, rh, __half2float(v));
     }
+    static __device__ __forceinline__ __half encode(float v, float w, float rh) {
+        return __float2half_rn(__fmaf_rn(-w, rh, v));
+    }
+    static __device__ __forceinline__ __half rho_store(float r) { return __float2half_rn(r); }
+    static __device__ __forceinline__ float rho_value(__half s) { return __half2float(s); }
 };
 
 template <>
 struct Codec<__nv_bfloat16> {
     using R = float;
-    static __device__ __forceinline__ float decode(__nv_bfloat16 v, float shift) {
-        return __bfloat162float(v) + shift;
+    static constexpr bool kNodeShift = true;
+    static constexpr int kPlanes = 20;
+    static __device__ __forceinline__ float decode(__nv_bfloat16 v, float w, float rh) {
+        return __fmaf_rn(w, rh, __bfloat162float(v));
     }
-    static __device__ __forceinline__ float load(const __nv_bfloat16* p, float s) { return decode(__ldg(p), s); }
-    static __device__ __forceinline__ void store(__nv_bfloat16* p, float v, float shift) {
-        *p = __float2bfloat16_rn(v - shift);
+    static __device__ __forceinline__ __nv_bfloat16 encode(float v, float w, float rh) {
+        return __float2bfloat16_rn(__fmaf_rn(-w, rh, v));
     }
+    static __device__ __forceinline__ __nv_bfloat16 rho_store(float r) { return __float2bfloat16_rn(r); }
+    static __device__ __forceinline__ float rho_value(__nv_bfloat16 s) { return __bfloat162float(s); }
 };
 
 // D2Q9, textbook order: c_0 = (0,0); c_1..c_4 = (1,0),(0,1),(-1,0),(0,-1);
@@ -192,7 +214,6 @@ __device__ __forceinline__ R warp_max(R v) {
 template <typename R>
 struct NodeParams {
     R G, gx, gy, rw0, rw1, nu0, nu1, k3;
-    R sh0[3], sh1[3];   // storage shifts w rho_ref for weight classes 0 (rest), 1, 2 (diagonal)
     __device__ __forceinline__ void load(const StepParams* __restrict__ p) {
         G = R(p->G);
         gx = R(p->g[0]);
@@ -202,15 +223,14 @@ struct NodeParams {
         nu0 = R(p->nu[0]);
         nu1 = R(p->nu[1]);
         k3 = R(p->k3);
-        const R r0 = R(p->rho_ref[0]), r1 = R(p->rho_ref[1]);
-        sh0[0] = r0 * R(4.0 / 9.0);
-        sh0[1] = r0 * R(1.0 / 9.0);
-        sh0[2] = r0 * R(1.0 / 36.0);
-        sh1[0] = r1 * R(4.0 / 9.0);
-        sh1[1] = r1 * R(1.0 / 9.0);
-        sh1[2] = r1 * R(1.0 / 36.0);
     }
 };
+
+// Weight of direction i in the arithmetic type (the mass-exact set).
+template <typename R>
+__device__ __forceinline__ R wgt(int i) {
+    return i == 0 ? Weights<R>::w0() : (i <= 4 ? Weights<R>::w1() : Weights<R>::w5());
+}
 
 __host__ __device__ __forceinline__ int weight_class(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
 
@@ -265,10 +285,16 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
         equilibrium<R>(rho, ux, uy, P.k3, fu);
         equilibrium<R>(rho, ux + ax, uy + ay, P.k3, fs);
         S* d = dst + a * 9 * plane;
+        R rh = R(0);
+        if (C::kNodeShift) {
+            const S q = C::rho_store(rho);
+            dst[(18 + a) * plane] = q;
+            rh = C::rho_value(q);
+        }
 #pragma unroll
         for (int i = 0; i < 9; i++) {
             out[a][i] = fs[i] + om1 * (f[a][i] - fu[i]);
-            C::store(d + i * plane, out[a][i], a ? P.sh1[weight_class(i)] : P.sh0[weight_class(i)]);
+            d[i * plane] = C::encode(out[a][i], wgt<R>(i), rh);
         }
     }
     // periodic ghost images of columns 0, 1, nx - 2, nx - 1 (ghost columns
@@ -282,11 +308,17 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
             if (m != x) continue;
             const int off = gcols[k] - x;
 #pragma unroll
-            for (int a = 0; a < 2; a++)
+            for (int a = 0; a < 2; a++) {
+                R rh = R(0);
+                if (C::kNodeShift) {
+                    const S q = C::rho_store(a ? rho1 : rho0);
+                    dst[(18 + a) * plane + off] = q;
+                    rh = C::rho_value(q);
+                }
 #pragma unroll
                 for (int i = 0; i < 9; i++)
-                    C::store(dst + a * 9 * plane + i * plane + off, out[a][i],
-                             a ? P.sh1[weight_class(i)] : P.sh0[weight_class(i)]);
+                    dst[a * 9 * plane + i * plane + off] = C::encode(out[a][i], wgt<R>(i), rh);
+            }
         }
     }
     ob.m0 += rho0;

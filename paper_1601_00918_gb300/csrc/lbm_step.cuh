@@ -84,23 +84,33 @@ __global__ void __launch_bounds__(BX) step_simple_kernel(const S* __restrict__ f
         const int ym = y == 0 ? ny - 1 : y - 1;
         const int yp = y == ny - 1 ? 0 : y + 1;
         const int oy = y * pitch, oym = ym * pitch, oyp = yp * pitch;
-        int src[9];
-        src[0] = oy + cx;
-        src[1] = (lk & (1u << 1)) ? 3 * plane + oy + cx : 1 * plane + oy + xm;
-        src[2] = (lk & (1u << 2)) ? 4 * plane + oy + cx : 2 * plane + oym + cx;
-        src[3] = (lk & (1u << 3)) ? 1 * plane + oy + cx : 3 * plane + oy + xp;
-        src[4] = (lk & (1u << 4)) ? 2 * plane + oy + cx : 4 * plane + oyp + cx;
-        src[5] = (lk & (1u << 5)) ? 7 * plane + oy + cx : 5 * plane + oym + xm;
-        src[6] = (lk & (1u << 6)) ? 8 * plane + oy + cx : 6 * plane + oym + xp;
-        src[7] = (lk & (1u << 7)) ? 5 * plane + oy + cx : 7 * plane + oyp + xp;
-        src[8] = (lk & (1u << 8)) ? 6 * plane + oy + cx : 8 * plane + oyp + xm;
-        const S* f1 = fin + 9 * plane;
+        // node (offset within a plane) and plane of each pulled population;
+        // a bounced population is the node's own one of the opposite direction
+        const int own = oy + cx;
+        int nd[9], pl[9];
+        nd[0] = own;
+        pl[0] = 0;
+        const bool b1 = lk & (1u << 1), b2 = lk & (1u << 2), b3 = lk & (1u << 3), b4 = lk & (1u << 4);
+        const bool b5 = lk & (1u << 5), b6 = lk & (1u << 6), b7 = lk & (1u << 7), b8 = lk & (1u << 8);
+        nd[1] = b1 ? own : oy + xm;   pl[1] = b1 ? 3 : 1;
+        nd[2] = b2 ? own : oym + cx;  pl[2] = b2 ? 4 : 2;
+        nd[3] = b3 ? own : oy + xp;   pl[3] = b3 ? 1 : 3;
+        nd[4] = b4 ? own : oyp + cx;  pl[4] = b4 ? 2 : 4;
+        nd[5] = b5 ? own : oym + xm;  pl[5] = b5 ? 7 : 5;
+        nd[6] = b6 ? own : oym + xp;  pl[6] = b6 ? 8 : 6;
+        nd[7] = b7 ? own : oyp + xp;  pl[7] = b7 ? 5 : 7;
+        nd[8] = b8 ? own : oyp + xm;  pl[8] = b8 ? 6 : 8;
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            // a bounced population comes from the opposite direction, whose
-            // weight (and so whose storage shift) is the same
-            f[0][i] = C::load(fin + src[i], P.sh0[weight_class(i)]);
-            f[1][i] = C::load(f1 + src[i], P.sh1[weight_class(i)]);
+            // 16-bit formats: shift by the source node's density (the same
+            // weight for i and opp(i))
+            R r0s = R(0), r1s = R(0);
+            if (C::kNodeShift) {
+                r0s = C::rho_value(__ldg(fin + 18 * plane + nd[i]));
+                r1s = C::rho_value(__ldg(fin + 19 * plane + nd[i]));
+            }
+            f[0][i] = C::decode(__ldg(fin + pl[i] * plane + nd[i]), wgt<R>(i), r0s);
+            f[1][i] = C::decode(__ldg(fin + (9 + pl[i]) * plane + nd[i]), wgt<R>(i), r1s);
         }
         R a = R(0), b = R(0);
 #pragma unroll
@@ -128,9 +138,12 @@ __global__ void __launch_bounds__(BX) step_simple_kernel(const S* __restrict__ f
             int sxp = hx - d2q9_cx(i);
             sxp = sxp < 0 ? sxp + nx : (sxp >= nx ? sxp - nx : sxp);
             const int syp = wrap_y(y - d2q9_cy(i));
-            const int idx = (lk & (1u << i)) ? d2q9_opp(i) * plane + y * pitch + hx
-                                             : i * plane + syp * pitch + sxp;
-            v = C::load(fin + sp * 9 * plane + idx, weight_of<R>(i) * R(prm->rho_ref[sp]));
+            const bool bb = lk & (1u << i);
+            const int node = bb ? y * pitch + hx : syp * pitch + sxp;
+            const int pln = bb ? d2q9_opp(i) : i;
+            R rs = R(0);
+            if (C::kNodeShift) rs = C::rho_value(__ldg(fin + (18 + sp) * plane + node));
+            v = C::decode(__ldg(fin + (sp * 9 + pln) * plane + node), wgt<R>(i), rs);
         }
         v += __shfl_xor_sync(0xffffffffu, v, 8);
         v += __shfl_xor_sync(0xffffffffu, v, 4);

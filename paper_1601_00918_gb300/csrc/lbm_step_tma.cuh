@@ -6,8 +6,9 @@
 // pulling row r + 1 while colliding row r.  The difference is where the
 // pulled values come from.  One elected thread keeps D + 3 row stages in a
 // shared-memory ring: each stage is ONE cp.async.bulk.tensor.3d copy of a
-// box {BX + 16 columns, 1 row, 18 planes} plus one 2-D copy of the row's
-// link words, both completing on the stage's mbarrier.  Stages are issued up
+// box {BX + 16 columns, 1 row, all planes} plus one 2-D copy of the row's
+// link words, both completing on the stage's mbarrier (the 16-bit formats
+// stage 20 planes: their two density planes ride in the same box).  Stages are issued up
 // to D rows ahead, so the loads of the next rows are in flight while the
 // CTA computes; the pull itself (with bounce-back) reads shared memory.  The
 // 8-column ghost margins of the layout make every box a plain rectangle:
@@ -89,7 +90,8 @@ template <typename S, int BX, int D>
 struct StagedPlan {
     static constexpr int kW = BX + 2 * kGhost;            // staged columns per row
     static constexpr int kStages = D + 3;                 // ring: rows r..r+2 in use + D ahead
-    static constexpr int kPopBytes = 18 * kW * (int)sizeof(S);
+    static constexpr int kPlanes = Codec<S>::kPlanes;        // 18, or 20 with the density planes
+    static constexpr int kPopBytes = kPlanes * kW * (int)sizeof(S);
     static constexpr int kPopSlot = (kPopBytes + 127) / 128 * 128;
     static constexpr int kLinkSlot = (kW * 2 + 127) / 128 * 128;
     static constexpr int kSlot = kPopSlot + kLinkSlot;
@@ -100,14 +102,15 @@ struct StagedPlan {
     static constexpr uint32_t kTxBytes = (uint32_t)(kPopBytes + kW * 2);
 };
 
-// One time step fin -> fout.  fmap views fin as [18 planes][ny][pitch],
+// One time step fin -> fout.  fmap views fin as [planes][ny][pitch],
 // lmap views the link words as [ny][pitch]; fout points at logical column 0
-// of row 0.  rows[cb] = (first, last) row with fluid in column block cb.
+// of row 0.  rows64[k] = (first, last) row with fluid in columns
+// [64 k, 64 k + 64); a CTA of BX columns merges BX / 64 of them.
 template <typename S, int BX, int D>
-__global__ void __launch_bounds__(BX) step_staged_kernel(const __grid_constant__ CUtensorMap fmap,
+__global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) step_staged_kernel(const __grid_constant__ CUtensorMap fmap,
                                                          const __grid_constant__ CUtensorMap lmap,
                                                          S* __restrict__ fout,
-                                                         const int2* __restrict__ rows,
+                                                         const int2* __restrict__ rows64,
                                                          const StepParams* __restrict__ prm,
                                                          ObsAccum* __restrict__ acc,
                                                          ObsState* __restrict__ obs, Grid grid) {
@@ -135,7 +138,15 @@ __global__ void __launch_bounds__(BX) step_staged_kernel(const __grid_constant__
     const int x0 = cb * BX;
 
     // this CTA's strip of the block's fluid rows
-    const int2 rr = rows[cb];
+    int2 rr = make_int2(ny, -1);
+    {
+        const int k0 = x0 / 64, k1 = min((x0 + BX + 63) / 64, (nx + 63) / 64);
+        for (int k = k0; k < k1; k++) {
+            const int2 q = rows64[k];
+            rr.x = min(rr.x, q.x);
+            rr.y = max(rr.y, q.y);
+        }
+    }
     const int nrows = rr.y - rr.x + 1;
     const int rpb = nrows > 0 ? (nrows + grid.strips - 1) / grid.strips : 0;
     const int y0 = rr.x + blockIdx.y * rpb;
@@ -151,14 +162,15 @@ __global__ void __launch_bounds__(BX) step_staged_kernel(const __grid_constant__
     const bool rho_col = gxc <= nx;                 // thread nx - x0 pulls the image column nx
     const int wi = t + kGhost;                      // this thread's column in the staged window
 
-    auto wrap_y = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
     auto slot = [&](int r) { return (r - y0 + 1) & 3; };
 
     bool timed_out = false;
     int next_issue = 0;                             // used by thread 0 only
     auto issue = [&](int j) {
         uint64_t* bar = &bars[j % NS];
-        const int row = wrap_y(y0 - 2 + j);
+        // full modulo: with ny < 3 the stage rows y0 - 2 .. y1 + 1 wrap more than once
+        int row = (y0 - 2 + j) % ny;
+        row = row < 0 ? row + ny : row;
         mbar_expect_tx(bar, Plan::kTxBytes);
         tma_load_3d((void*)pops(j), &fmap, x0, row, 0, bar);
         tma_load_2d((void*)lnks(j), &lmap, x0, row, bar);
@@ -180,20 +192,30 @@ __global__ void __launch_bounds__(BX) step_staged_kernel(const __grid_constant__
         const S* pm = pops(jm);
         const S* pc = pops(jc);
         const S* pp = pops(jp);
+        // (plane, stage, column) of each pulled population; bounced: own opp(i)
+        const bool b1 = lk & (1u << 1), b2 = lk & (1u << 2), b3 = lk & (1u << 3), b4 = lk & (1u << 4);
+        const bool b5 = lk & (1u << 5), b6 = lk & (1u << 6), b7 = lk & (1u << 7), b8 = lk & (1u << 8);
+        const S* rowp[9];
+        int col[9], pl[9];
+        rowp[0] = pc; col[0] = w;                     pl[0] = 0;
+        rowp[1] = pc; col[1] = b1 ? w : w - 1;        pl[1] = b1 ? 3 : 1;
+        rowp[2] = b2 ? pc : pm; col[2] = w;           pl[2] = b2 ? 4 : 2;
+        rowp[3] = pc; col[3] = b3 ? w : w + 1;        pl[3] = b3 ? 1 : 3;
+        rowp[4] = b4 ? pc : pp; col[4] = w;           pl[4] = b4 ? 2 : 4;
+        rowp[5] = b5 ? pc : pm; col[5] = b5 ? w : w - 1; pl[5] = b5 ? 7 : 5;
+        rowp[6] = b6 ? pc : pm; col[6] = b6 ? w : w + 1; pl[6] = b6 ? 8 : 6;
+        rowp[7] = b7 ? pc : pp; col[7] = b7 ? w : w + 1; pl[7] = b7 ? 5 : 7;
+        rowp[8] = b8 ? pc : pp; col[8] = b8 ? w : w - 1; pl[8] = b8 ? 6 : 8;
 #pragma unroll
-        for (int a = 0; a < 2; a++) {
-            const int b = a * 9 * W;
-            const R* sh = a ? P.sh1 : P.sh0;
-            // direction i pulls from (x - c_ix, y - c_iy); bounced: own opp(i)
-            f[a][0] = C::decode(pc[b + 0 * W + w], sh[0]);
-            f[a][1] = C::decode((lk & (1u << 1)) ? pc[b + 3 * W + w] : pc[b + 1 * W + w - 1], sh[1]);
-            f[a][2] = C::decode((lk & (1u << 2)) ? pc[b + 4 * W + w] : pm[b + 2 * W + w], sh[1]);
-            f[a][3] = C::decode((lk & (1u << 3)) ? pc[b + 1 * W + w] : pc[b + 3 * W + w + 1], sh[1]);
-            f[a][4] = C::decode((lk & (1u << 4)) ? pc[b + 2 * W + w] : pp[b + 4 * W + w], sh[1]);
-            f[a][5] = C::decode((lk & (1u << 5)) ? pc[b + 7 * W + w] : pm[b + 5 * W + w - 1], sh[2]);
-            f[a][6] = C::decode((lk & (1u << 6)) ? pc[b + 8 * W + w] : pm[b + 6 * W + w + 1], sh[2]);
-            f[a][7] = C::decode((lk & (1u << 7)) ? pc[b + 5 * W + w] : pp[b + 7 * W + w + 1], sh[2]);
-            f[a][8] = C::decode((lk & (1u << 8)) ? pc[b + 6 * W + w] : pp[b + 8 * W + w - 1], sh[2]);
+        for (int i = 0; i < 9; i++) {
+            const S* q = rowp[i] + col[i];
+            R r0s = R(0), r1s = R(0);
+            if (C::kNodeShift) {
+                r0s = C::rho_value(q[18 * W]);
+                r1s = C::rho_value(q[19 * W]);
+            }
+            f[0][i] = C::decode(q[pl[i] * W], wgt<R>(i), r0s);
+            f[1][i] = C::decode(q[(9 + pl[i]) * W], wgt<R>(i), r1s);
         }
         R a = R(0), bsum = R(0);
 #pragma unroll
@@ -217,17 +239,19 @@ __global__ void __launch_bounds__(BX) step_staged_kernel(const __grid_constant__
         const int sp = lane >> 4, i = lane & 15;
         R v = R(0);
         if (!(lk & kSolid) && i < 9) {
-            const S* src;
-            int col;
+            const S* q;
+            int pln;
             if (lk & (1u << i)) {
-                src = pops(jc) + (sp * 9 + d2q9_opp(i)) * W;
-                col = w;
+                q = pops(jc) + w;
+                pln = d2q9_opp(i);
             } else {
                 const int cy = d2q9_cy(i);
-                src = (cy > 0 ? pops(jm) : (cy < 0 ? pops(jp) : pops(jc))) + (sp * 9 + i) * W;
-                col = w - d2q9_cx(i);
+                q = (cy > 0 ? pops(jm) : (cy < 0 ? pops(jp) : pops(jc))) + w - d2q9_cx(i);
+                pln = i;
             }
-            v = C::decode(src[col], weight_of<R>(i) * R(prm->rho_ref[sp]));
+            R rs = R(0);
+            if (C::kNodeShift) rs = C::rho_value(q[(18 + sp) * W]);
+            v = C::decode(q[(sp * 9 + pln) * W], wgt<R>(i), rs);
         }
         v += __shfl_xor_sync(0xffffffffu, v, 8);
         v += __shfl_xor_sync(0xffffffffu, v, 4);

@@ -177,8 +177,9 @@ def lbm_load(h, f):
 def lbm_kernel_info(h) -> dict:
     info = (ctypes.c_int32 * 4)()
     _check(library().lbm_kernel_info(h, info), h)
-    return {"variant": {1: "simple", 2: "staged"}.get(info[0], str(info[0])), "depth": info[1],
-            "rows_per_cta": info[2], "strips": info[3]}
+    if info[0] == 1:
+        return {"variant": "simple", "rows_per_cta": info[2]}
+    return {"variant": "staged", "depth": info[1], "cols_per_cta": info[2], "strips": info[3]}
 
 
 def lbm_destroy(h):
