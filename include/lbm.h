@@ -149,6 +149,109 @@ void lbm_destroy(lbm_t *h);
  * when h is NULL.  Valid until the next call on the same handle / thread. */
 const char *lbm_last_error(const lbm_t *h);
 
+/* ---------------------------------------------------------------------------
+ * Batches of independent channels and the critical body force (Section 3.4)
+ *
+ * The paper's question: the smallest homogeneous body force g at which a
+ * static oil slug in a sinusoidal channel starts to move (the critical Bond
+ * number Bo = rho g L D / sigma, Eq. Bo_number).  The paper ramps g in small
+ * increments (Section 3.4); here each instance is bisected on g instead:
+ * every probe restarts from the state equilibrated at g = 0, runs t_obs
+ * steps at the probe value, and calls the slug moving when its oil centre of
+ * mass travelled more than the instance's disp_threshold.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_batch_t lbm_batch_t; /* opaque */
+
+typedef struct {
+    int32_t nx, ny;
+    int32_t periodic_x, periodic_y;
+    double tau[2];          /* tau^o, tau^w (> 1/2) */
+    double G;               /* Eq. (comp_interaction) */
+    double rho_wall[2];     /* rho_s^o, rho_s^w */
+    double g[2];            /* body force used by lbm_batch_step */
+    const uint8_t *mask;    /* host [ny][nx], 1 = solid (same rules as lbm_create) */
+    const double *rho_init; /* host [2][ny][nx] initial densities */
+    double disp_threshold;  /* oil displacement over one probe window that means "moving" */
+} lbm_instance;
+
+/* Create n instances of uneven sizes that step together (one launch per step
+ * over all of them).  The library copies the instance data; the host arrays
+ * may be freed after the call.  Errors as lbm_create (per-instance text in
+ * lbm_batch_last_error(NULL)). */
+int lbm_batch_create(const lbm_instance *inst, int32_t n, int32_t precision, int32_t eq_order,
+                     void *cuda_stream, lbm_batch_t **out);
+
+/* Advance every active instance by nsteps (asynchronous). */
+int lbm_batch_step(lbm_batch_t *b, int64_t nsteps);
+
+/* Observables of every instance (out[n]); LBM_EUNSTABLE if any NaN flag. */
+int lbm_batch_observables(lbm_batch_t *b, lbm_obs *out);
+
+/* Set the x body force of every instance (gx[n]). */
+int lbm_batch_set_body_force(lbm_batch_t *b, const double *gx);
+
+/* Stored populations of instance i as lbm_save does for a single grid. */
+int lbm_batch_save(lbm_batch_t *b, int32_t i, double *f);
+
+typedef struct {
+    double rel_bracket;    /* stop when g_hi - g_lo <= rel_bracket * g_hi (e.g. 0.02) */
+    int64_t t_eq;          /* steps at g = 0 before the first probe */
+    int64_t t_obs;         /* steps per probe */
+    int32_t max_probes;    /* per instance, bracket checks included */
+    int32_t check_bracket; /* 1: first check that g_hi moves and g_lo does not,
+                              doubling g_hi / halving g_lo on failure; 0: trust the bracket */
+    double timeout_s;      /* host wall-clock limit (<= 0: none) */
+} lbm_bisect_opts;
+
+typedef struct {
+    double g_lo, g_hi;     /* final bracket: static at g_lo, moving at g_hi */
+    int32_t probes;        /* probe windows this instance took part in */
+    int32_t status;        /* 0 converged, 1 max_probes reached, 2 unstable, 3 timeout */
+} lbm_crit_result;
+
+/* Bisect every instance of b on its x body force, starting from the brackets
+ * [g_lo[i], g_hi[i]]; all instances probe in lockstep, finished ones drop
+ * out of the launches.  Classification and bracket updates run on the
+ * device in FP64.  Returns LBM_ETIMEOUT (results filled, status 3) when
+ * timeout_s ran out. */
+int lbm_critical_pressure_batch(lbm_batch_t *b, const double *g_lo, const double *g_hi,
+                                const lbm_bisect_opts *o, lbm_crit_result *out);
+
+void lbm_batch_destroy(lbm_batch_t *b);
+const char *lbm_batch_last_error(const lbm_batch_t *b);
+
+/* ---------------------------------------------------------------------------
+ * Surrogate of the critical body force (not in the paper)
+ *
+ * A small network that maps a channel description to a predicted log g_crit
+ * with an uncertainty; it only seeds the brackets of
+ * lbm_critical_pressure_batch, which stays the judge.  Network 5 -> 128 ->
+ * 128 -> 128 -> 2, SiLU hidden units, outputs (mu, s): mu the predicted
+ * log g_crit, s the log predicted variance; per-sample loss
+ * 0.5 (exp(-s) (y - mu)^2 + s).  34050 FP32 parameters, flat order
+ * W1 [128x5], b1 [128], W2 [128x128], b2, W3 [128x128], b3, W4 [2x128], b4 [2].
+ * Host arrays in, host arrays out; the network lives on the device.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm_mlp_t lbm_mlp_t;
+
+/* params: 34050 floats, or NULL for a seeded uniform(+-1/sqrt(fan_in)) init. */
+int lbm_mlp_create(const float *params, uint64_t seed, void *cuda_stream, lbm_mlp_t **out);
+/* Copy the parameters out (out_params may be NULL) and/or in (in_params may
+ * be NULL; loading resets the Adam moments). */
+int lbm_mlp_params(lbm_mlp_t *h, float *out_params, const float *in_params);
+/* out[B][2] = network(x[B][5]); 1 <= B <= 65536. */
+int lbm_mlp_forward(lbm_mlp_t *h, const float *x, int32_t B, float *out);
+/* Mean loss over the batch and its gradient (grad[34050], may be NULL). */
+int lbm_mlp_loss_grad(lbm_mlp_t *h, const float *x, const float *y, int32_t B, float *loss, float *grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with the last gradient. */
+int lbm_mlp_adam(lbm_mlp_t *h, float lr);
+/* epochs of minibatch Adam over (x[n][5], y[n]), shuffled with seed;
+ * *last_loss = loss of the last minibatch. */
+int lbm_mlp_train(lbm_mlp_t *h, const float *x, const float *y, int32_t n, int32_t epochs, int32_t batch,
+                  float lr, uint64_t seed, float *last_loss);
+void lbm_mlp_destroy(lbm_mlp_t *h);
+const char *lbm_mlp_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,7 @@
 #include "../../include/lbm.h"
 #include "lbm_step.cuh"
 #include "lbm_step_tma.cuh"
+#include "lbm_setup.cuh"
 
 using namespace gb300lbm;
 
@@ -148,65 +149,6 @@ bool layout_of(const lbm_params* p, Layout* L) {
     L->obs = align256(sizeof(ObsState));
     L->total = 2 * L->buf + L->links + L->rows + L->prm + 2 * L->acc + 2 * L->obs;
     return true;
-}
-
-// ---------------------------------------------------------------------------
-// set-up kernels
-// ---------------------------------------------------------------------------
-// Logical column of a storage column, or INT_MIN when it holds nothing
-// (padding, or a ghost of a non-periodic grid).
-__device__ __forceinline__ int logical_col(int sc, int nx, int periodic) {
-    const int x = sc - kGhost;
-    if (x >= 0 && x < nx) return x;
-    if (!periodic || x < -kGhost || x >= nx + kGhost) return INT_MIN;
-    int m = x % nx;
-    return m < 0 ? m + nx : m;
-}
-
-__global__ void links_kernel(const uint8_t* __restrict__ mask, uint16_t* __restrict__ links, int nx,
-                             int ny, int pitch, int periodic) {
-    const int sc = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (sc >= pitch || y >= ny) return;
-    const int x = logical_col(sc, nx, periodic);
-    if (x == INT_MIN) {
-        links[y * pitch + sc] = uint16_t(1u << kSolidBit);
-        return;
-    }
-    unsigned w = mask[y * nx + x] ? (1u << kSolidBit) : 0u;
-    for (int i = 1; i < 9; i++) {
-        int sx = x - d2q9_cx(i), sy = y - d2q9_cy(i);
-        sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-        if (mask[sy * nx + sx]) w |= 1u << i;
-    }
-    links[y * pitch + sc] = uint16_t(w);
-}
-
-template <typename S>
-__global__ void init_kernel(const double* __restrict__ rho, const uint16_t* __restrict__ links,
-                            S* __restrict__ f, int nx, int ny, int pitch, int periodic) {
-    using C = Codec<S>;
-    using R = typename C::R;
-    const int sc = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (sc >= pitch || y >= ny) return;
-    const int plane = ny * pitch;
-    const int x = logical_col(sc, nx, periodic);
-    const bool solid = x == INT_MIN || (links[y * pitch + sc] & (1u << kSolidBit));
-    S* node = f + y * pitch + sc;
-    for (int a = 0; a < 2; a++) {
-        const double r = solid ? 0.0 : rho[(size_t)a * nx * ny + (size_t)y * nx + x];
-        // solid nodes, padding and unused ghosts hold the stored value 0
-        R rh = R(0);
-        if (C::kNodeShift) {
-            const S q = C::rho_store(R(r));
-            node[(18 + a) * plane] = q;
-            rh = C::rho_value(q);
-        }
-        for (int i = 0; i < 9; i++)
-            node[(a * 9 + i) * plane] = C::encode(R(weight_of<double>(i) * r), wgt<R>(i), rh);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -449,7 +391,14 @@ int autotune(lbm_t* h) {
         // scratch accumulators: the stored state and the observables are untouched
         for (const Tuned& t : cand) {
             CUDA_TRY(nullptr, cudaMemsetAsync(h->tacc, 0, sizeof(ObsAccum), h->stream));
+            CUDA_TRY(nullptr, cudaMemsetAsync(h->tobs, 0, sizeof(ObsState), h->stream));
             CUDA_TRY(nullptr, launch_step(h, h->cur, t, h->tacc, h->tobs, h->stream));
+            // a candidate whose bounded waits gave up is not a candidate
+            int tflag = 0;
+            CUDA_TRY(nullptr, cudaMemcpyAsync(&tflag, &h->tobs->timeout_flag, sizeof(int), cudaMemcpyDeviceToHost,
+                                              h->stream));
+            CUDA_TRY(nullptr, cudaStreamSynchronize(h->stream));
+            if (tflag) continue;
             CUDA_TRY(nullptr, cudaEventRecord(e0, h->stream));
             for (int k = 0; k < 3; k++) CUDA_TRY(nullptr, launch_step(h, h->cur, t, h->tacc, h->tobs, h->stream));
             CUDA_TRY(nullptr, cudaEventRecord(e1, h->stream));

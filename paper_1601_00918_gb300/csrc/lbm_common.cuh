@@ -361,10 +361,12 @@ __device__ __forceinline__ void node_fields(const R (&f)[2][9], R rho0, R rho1, 
 }
 
 // Block reduction of the per-thread observables, FP64 atomics into `acc`, and
-// finalisation of the step by the last CTA to arrive.
+// finalisation of the step by the last of the `nblocks` CTAs that reduce into
+// the same accumulators (all CTAs of the grid by default).
 template <typename R, int NT>
 __device__ __forceinline__ void reduce_observables(ObsLocal<R> ob, ObsAccum* __restrict__ acc,
-                                                   ObsState* __restrict__ obs, bool timed_out) {
+                                                   ObsState* __restrict__ obs, bool timed_out,
+                                                   unsigned nblocks = 0u) {
     __shared__ R red[NT / 32][4];
     __shared__ unsigned red_bad;
     __shared__ bool is_last;
@@ -397,7 +399,7 @@ __device__ __forceinline__ void reduce_observables(ObsLocal<R> ob, ObsAccum* __r
         if (red_bad) atomicOr(&acc->bad, red_bad);
         __threadfence();
         const unsigned ticket = atomicAdd(&acc->blocks_done, 1u);
-        is_last = ticket == gridDim.x * gridDim.y - 1;
+        is_last = ticket == (nblocks ? nblocks : gridDim.x * gridDim.y) - 1;
     }
     __syncthreads();
     if (is_last && t == 0) {

@@ -31,34 +31,28 @@
 
 namespace gb300lbm {
 
-// FIELDS = false: one time step fin -> fout with observables.
+// The march of one CTA over rows [y0, y1) of columns [x0, x0 + BX).
+// FIELDS = false: one time step fin -> fout, observables into `ob`.
 // FIELDS = true : macroscopic fields of fin into `fields` (no fout write):
 //   fields[0..1][y][x] = rho^o, rho^w; [2..3] = u_x, u_y; [4] = pressure,
-//   rows [row_begin, row_end), planes of nx * (row_end - row_begin) doubles.
-// fin, fout and links point at logical column 0 of row 0.
+//   for rows [fr0, fr0 + frows), planes of nx * frows doubles.
+// fin, fout and links point at logical column 0 of row 0.  periodic_x only
+// controls the ghost images written for the staged kernel's row windows
+// (pass 0 for a layout without ghost columns); pulls wrap in x and y.
 template <typename S, int BX, bool FIELDS>
-__global__ void __launch_bounds__(BX) step_simple_kernel(const S* __restrict__ fin, S* __restrict__ fout,
-                                                         const uint16_t* __restrict__ links,
-                                                         const StepParams* __restrict__ prm,
-                                                         ObsAccum* __restrict__ acc,
-                                                         ObsState* __restrict__ obs,
-                                                         double* __restrict__ fields, Grid grid) {
+__device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __restrict__ fout,
+                                             const uint16_t* __restrict__ links,
+                                             const NodeParams<typename Codec<S>::R>& P,
+                                             double* __restrict__ fields, int nx, int ny, int pitch,
+                                             int periodic_x, int x0, int y0, int y1, int fr0, int frows,
+                                             ObsLocal<typename Codec<S>::R>& ob,
+                                             typename Codec<S>::R (*s_rho)[2][BX + 2]) {
     using C = Codec<S>;
     using R = typename C::R;
     constexpr unsigned kSolid = 1u << kSolidBit;
-
-    const int nx = grid.nx, ny = grid.ny, pitch = grid.pitch;
     const int plane = ny * pitch;
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
-    const int x0 = blockIdx.x * BX;
-    const int y0 = grid.row_begin + blockIdx.y * grid.rows_per_block;
-    const int y1 = min(y0 + grid.rows_per_block, grid.row_end);
-
-    __shared__ R s_rho[4][2][BX + 2];
-
-    NodeParams<R> P;
-    P.load(prm);
 
     // column owned by this thread; the first thread past the right edge of
     // the grid pulls the periodic image column 0 (its density only).
@@ -158,7 +152,6 @@ __global__ void __launch_bounds__(BX) step_simple_kernel(const S* __restrict__ f
     R cur[2][9], nxt[2][9];
     R rc0 = R(0), rc1 = R(0), rn0 = R(0), rn1 = R(0);
     bool solid_cur = true, solid_nxt = true;
-    ObsLocal<R> ob;
 
     // prologue: densities of rows y0 - 1 and y0
     {
@@ -193,8 +186,8 @@ __global__ void __launch_bounds__(BX) step_simple_kernel(const S* __restrict__ f
             const int s0 = slot(r), sm = slot(r - 1), sp = sn;
             if (solid_cur) {
                 if (FIELDS) {
-                    const size_t fp = (size_t)nx * (grid.row_end - grid.row_begin);
-                    double* o = fields + (size_t)(r - grid.row_begin) * nx + cx;
+                    const size_t fp = (size_t)nx * frows;
+                    double* o = fields + (size_t)(r - fr0) * nx + cx;
                     o[0] = double(P.rw0);
                     o[fp] = double(P.rw1);
                     o[2 * fp] = 0.0;
@@ -215,11 +208,11 @@ __global__ void __launch_bounds__(BX) step_simple_kernel(const S* __restrict__ f
                     nb[b][7] = s_rho[sm][b][t + 2];   // c_8 = ( 1,-1)
                 }
                 if (FIELDS) {
-                    const size_t fp = (size_t)nx * (grid.row_end - grid.row_begin);
-                    node_fields<R>(cur, rc0, rc1, nb, P, fields + (size_t)(r - grid.row_begin) * nx + cx, fp);
+                    node_fields<R>(cur, rc0, rc1, nb, P, fields + (size_t)(r - fr0) * nx + cx,
+                                   (size_t)nx * frows);
                 } else {
                     collide_store<S, R>(cur, rc0, rc1, nb, P, fout + r * pitch + cx, plane, cx, nx,
-                                        grid.periodic_x, ob);
+                                        periodic_x, ob);
                 }
             }
         }
@@ -233,7 +226,27 @@ __global__ void __launch_bounds__(BX) step_simple_kernel(const S* __restrict__ f
         rc1 = rn1;
         solid_cur = solid_nxt;
     }
+}
 
+// One time step (or the fields) of a single grid: CTA (bx, by) marches rows
+// [row_begin + by * rows_per_block, ...) of columns [bx * BX, bx * BX + BX).
+template <typename S, int BX, bool FIELDS>
+__global__ void __launch_bounds__(BX) step_simple_kernel(const S* __restrict__ fin, S* __restrict__ fout,
+                                                         const uint16_t* __restrict__ links,
+                                                         const StepParams* __restrict__ prm,
+                                                         ObsAccum* __restrict__ acc,
+                                                         ObsState* __restrict__ obs,
+                                                         double* __restrict__ fields, Grid grid) {
+    using R = typename Codec<S>::R;
+    __shared__ R s_rho[4][2][BX + 2];
+    NodeParams<R> P;
+    P.load(prm);
+    const int x0 = blockIdx.x * BX;
+    const int y0 = grid.row_begin + blockIdx.y * grid.rows_per_block;
+    const int y1 = min(y0 + grid.rows_per_block, grid.row_end);
+    ObsLocal<R> ob;
+    march_simple<S, BX, FIELDS>(fin, fout, links, P, fields, grid.nx, grid.ny, grid.pitch, grid.periodic_x,
+                                x0, y0, y1, grid.row_begin, grid.row_end - grid.row_begin, ob, s_rho);
     if (FIELDS) return;
     reduce_observables<R, BX>(ob, acc, obs, false);
 }

@@ -293,6 +293,13 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
             s_rho[slot(y0)][1][t + 1] = rc1;
         }
         halo(1, 2, 3, slot(y0));
+        // stages 0 and 1 are no longer needed: refill their slots now, so
+        // that stage 4 (the first one the loop waits for) is on its way even
+        // with a ring of only D + 3 = 4 slots
+        __syncthreads();
+        if (t == 0) {
+            while (next_issue <= 1 + NS && next_issue < n_stage) issue(next_issue++);
+        }
 
         for (int r = y0; r < y1; ++r) {
             const int j = r - y0 + 2;                 // stages j, j+1, j+2 hold rows r, r+1, r+2

@@ -26,7 +26,11 @@ PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": L
 # symbols declared in include/lbm.h
 EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "lbm_get_fields",
            "lbm_set_body_force", "lbm_save", "lbm_load", "lbm_kernel_info", "lbm_destroy",
-           "lbm_last_error")
+           "lbm_last_error", "lbm_batch_create", "lbm_batch_step", "lbm_batch_observables",
+           "lbm_batch_set_body_force", "lbm_batch_save", "lbm_critical_pressure_batch",
+           "lbm_batch_destroy", "lbm_batch_last_error", "lbm_mlp_create", "lbm_mlp_params",
+           "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam", "lbm_mlp_train", "lbm_mlp_destroy",
+           "lbm_mlp_last_error")
 
 
 class LbmError(RuntimeError):
@@ -58,6 +62,26 @@ class Obs(ctypes.Structure):
                 "nan_flag": self.nan_flag, "timeout_flag": self.timeout_flag}
 
 
+class Instance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+                ("tau", ctypes.c_double * 2), ("G", ctypes.c_double),
+                ("rho_wall", ctypes.c_double * 2), ("g", ctypes.c_double * 2),
+                ("mask", ctypes.POINTER(ctypes.c_uint8)), ("rho_init", ctypes.POINTER(ctypes.c_double)),
+                ("disp_threshold", ctypes.c_double)]
+
+
+class BisectOpts(ctypes.Structure):
+    _fields_ = [("rel_bracket", ctypes.c_double), ("t_eq", ctypes.c_int64), ("t_obs", ctypes.c_int64),
+                ("max_probes", ctypes.c_int32), ("check_bracket", ctypes.c_int32),
+                ("timeout_s", ctypes.c_double)]
+
+
+class CritResult(ctypes.Structure):
+    _fields_ = [("g_lo", ctypes.c_double), ("g_hi", ctypes.c_double), ("probes", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -82,12 +106,39 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_save.argtypes = [vp, dp]
     lib.lbm_load.argtypes = [vp, dp]
     lib.lbm_kernel_info.argtypes = [vp, P(ctypes.c_int32)]
+    lib.lbm_batch_create.argtypes = [P(Instance), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, P(vp)]
+    lib.lbm_batch_step.argtypes = [vp, ctypes.c_int64]
+    lib.lbm_batch_observables.argtypes = [vp, P(Obs)]
+    lib.lbm_batch_set_body_force.argtypes = [vp, dp]
+    lib.lbm_batch_save.argtypes = [vp, ctypes.c_int32, dp]
+    lib.lbm_critical_pressure_batch.argtypes = [vp, dp, dp, P(BisectOpts), P(CritResult)]
+    lib.lbm_batch_destroy.argtypes = [vp]
+    lib.lbm_batch_destroy.restype = None
+    lib.lbm_batch_last_error.argtypes = [vp]
+    lib.lbm_batch_last_error.restype = ctypes.c_char_p
+    fp = P(ctypes.c_float)
+    lib.lbm_mlp_create.argtypes = [fp, ctypes.c_uint64, vp, P(vp)]
+    lib.lbm_mlp_params.argtypes = [vp, fp, fp]
+    lib.lbm_mlp_forward.argtypes = [vp, fp, ctypes.c_int32, fp]
+    lib.lbm_mlp_loss_grad.argtypes = [vp, fp, fp, ctypes.c_int32, fp, fp]
+    lib.lbm_mlp_adam.argtypes = [vp, ctypes.c_float]
+    lib.lbm_mlp_train.argtypes = [vp, fp, fp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                  ctypes.c_uint64, fp]
+    lib.lbm_mlp_destroy.argtypes = [vp]
+    lib.lbm_mlp_destroy.restype = None
+    lib.lbm_mlp_last_error.argtypes = []
+    lib.lbm_mlp_last_error.restype = ctypes.c_char_p
+    for name in ("lbm_mlp_create", "lbm_mlp_params", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
+                 "lbm_mlp_train"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.lbm_destroy.argtypes = [vp]
     lib.lbm_destroy.restype = None
     lib.lbm_last_error.argtypes = [vp]
     lib.lbm_last_error.restype = ctypes.c_char_p
     for name in ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables",
-                 "lbm_get_fields", "lbm_set_body_force", "lbm_save", "lbm_load", "lbm_kernel_info"):
+                 "lbm_get_fields", "lbm_set_body_force", "lbm_save", "lbm_load", "lbm_kernel_info",
+                 "lbm_batch_create", "lbm_batch_step", "lbm_batch_observables",
+                 "lbm_batch_set_body_force", "lbm_batch_save", "lbm_critical_pressure_batch"):
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -244,6 +295,194 @@ class Simulation:
             lbm_destroy(self.h)
             self.h = None
         self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------
+# batches and the critical body force
+# ----------------------------------------------------------------------------
+def _bcheck(rc, b=None):
+    if rc != LBM_OK:
+        msg = library().lbm_batch_last_error(b)
+        raise LbmError(rc, (msg or b"").decode())
+    return rc
+
+
+def lbm_batch_create(instances, precision="fp32", eq_order=3, stream=None):
+    """instances: list of dicts with mask [ny, nx], rho_init [2, ny, nx], tau, G,
+    rho_wall, g, periodic, disp_threshold."""
+    keep = []
+    arr = (Instance * len(instances))()
+    for k, d in enumerate(instances):
+        mask = np.ascontiguousarray(d["mask"], dtype=np.uint8)
+        rho = np.ascontiguousarray(d["rho_init"], dtype=np.float64)
+        ny, nx = mask.shape
+        assert rho.shape == (2, ny, nx)
+        keep += [mask, rho]
+        per = d.get("periodic", (True, False))
+        arr[k] = Instance(nx, ny, int(per[0]), int(per[1]), (ctypes.c_double * 2)(*d.get("tau", (1.0, 1.0))),
+                          float(d.get("G", 0.0)), (ctypes.c_double * 2)(*d.get("rho_wall", (0.0, 0.0))),
+                          (ctypes.c_double * 2)(*d.get("g", (0.0, 0.0))),
+                          mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dptr(rho),
+                          float(d.get("disp_threshold", 0.0)))
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    h = ctypes.c_void_p()
+    _bcheck(library().lbm_batch_create(arr, len(instances), prec, int(eq_order),
+                                       ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+    return h.value
+
+
+def lbm_batch_step(b, nsteps):
+    _bcheck(library().lbm_batch_step(b, int(nsteps)), b)
+
+
+def lbm_batch_observables(b, n, check=True):
+    out = (Obs * n)()
+    rc = library().lbm_batch_observables(b, out)
+    if check:
+        _bcheck(rc, b)
+    return [o.as_dict() for o in out]
+
+
+def lbm_batch_set_body_force(b, gx):
+    gx = np.ascontiguousarray(gx, dtype=np.float64)
+    _bcheck(library().lbm_batch_set_body_force(b, _dptr(gx)), b)
+
+
+def lbm_batch_save(b, i, nx, ny):
+    f = np.empty((2, 9, ny, nx))
+    _bcheck(library().lbm_batch_save(b, int(i), _dptr(f)), b)
+    return f
+
+
+def lbm_critical_pressure_batch(b, g_lo, g_hi, rel_bracket=0.02, t_eq=1000, t_obs=2000, max_probes=24,
+                                check_bracket=True, timeout_s=0.0, check=True):
+    g_lo = np.ascontiguousarray(g_lo, dtype=np.float64)
+    g_hi = np.ascontiguousarray(g_hi, dtype=np.float64)
+    n = len(g_lo)
+    out = (CritResult * n)()
+    o = BisectOpts(float(rel_bracket), int(t_eq), int(t_obs), int(max_probes), int(bool(check_bracket)),
+                   float(timeout_s))
+    rc = library().lbm_critical_pressure_batch(b, _dptr(g_lo), _dptr(g_hi), ctypes.byref(o), out)
+    if check and rc not in (LBM_OK,):
+        _bcheck(rc, b)
+    return [{"g_lo": r.g_lo, "g_hi": r.g_hi, "probes": r.probes, "status": r.status} for r in out]
+
+
+def lbm_batch_destroy(b):
+    if b:
+        library().lbm_batch_destroy(b)
+
+
+class Batch:
+    """Owning wrapper of a batch; work on torch's current stream."""
+
+    def __init__(self, instances, precision="fp32", eq_order=3, device=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.n = len(instances)
+        self.shapes = [np.asarray(d["mask"]).shape for d in instances]
+        with torch.cuda.device(device):
+            stream = torch.cuda.current_stream().cuda_stream
+            self.h = lbm_batch_create(instances, precision, eq_order, stream)
+
+    def step(self, n=1):
+        lbm_batch_step(self.h, n)
+
+    def observables(self, check=True):
+        return lbm_batch_observables(self.h, self.n, check)
+
+    def set_body_force(self, gx):
+        lbm_batch_set_body_force(self.h, gx)
+
+    def save(self, i):
+        ny, nx = self.shapes[i]
+        return lbm_batch_save(self.h, i, nx, ny)
+
+    def critical_pressure(self, g_lo, g_hi, **opts):
+        return lbm_critical_pressure_batch(self.h, g_lo, g_hi, **opts)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------
+# surrogate network
+# ----------------------------------------------------------------------------
+MLP_PARAMS = 34050
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _mcheck(rc):
+    if rc != LBM_OK:
+        raise LbmError(rc, (library().lbm_mlp_last_error() or b"").decode())
+
+
+class Surrogate:
+    """The 5 -> 128 -> 128 -> 128 -> 2 network on the device (C ABI lbm_mlp_*)."""
+
+    def __init__(self, params=None, seed=0, stream=None):
+        h = ctypes.c_void_p()
+        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        _mcheck(library().lbm_mlp_create(_fptr(p) if p is not None else None, int(seed),
+                                         ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
+        self.h = h.value
+
+    def params(self):
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        _mcheck(library().lbm_mlp_params(self.h, _fptr(out), None))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _mcheck(library().lbm_mlp_params(self.h, None, _fptr(p)))
+
+    def forward(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        out = np.empty((x.shape[0], 2), dtype=np.float32)
+        _mcheck(library().lbm_mlp_forward(self.h, _fptr(x), x.shape[0], _fptr(out)))
+        return out
+
+    def loss_grad(self, x, y):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        _mcheck(library().lbm_mlp_loss_grad(self.h, _fptr(x), _fptr(y), x.shape[0], _fptr(loss), _fptr(g)))
+        return float(loss[0]), g
+
+    def adam(self, lr):
+        _mcheck(library().lbm_mlp_adam(self.h, float(lr)))
+
+    def train(self, x, y, epochs, batch=256, lr=1e-3, seed=0):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        _mcheck(library().lbm_mlp_train(self.h, _fptr(x), _fptr(y), x.shape[0], int(epochs), int(batch),
+                                        float(lr), int(seed), _fptr(loss)))
+        return float(loss[0])
+
+    def close(self):
+        if getattr(self, "h", None):
+            library().lbm_mlp_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -1,0 +1,119 @@
+"""Critical-body-force sweeps over many channels (Section 3.4 of the paper).
+
+The paper finds the body force at which a static oil slug in a sinusoidal
+channel starts to move.  Here every channel of a sweep is bisected on g by
+``lbm_critical_pressure_batch`` (all channels in one launch per step,
+decisions in FP64 on the device), optionally with brackets seeded by the
+surrogate network.
+
+Channel description (``workloads.ChannelSpec``): wavelength lambda, amplitude
+ratio A/h0, slug length / lambda, contact-angle parameter theta, viscosity
+ratio nu^o / nu^w; mean half-width h0 = 0.1875 lambda, n_periods periods.
+
+Readings (not fixed by the paper):
+* wettability: cos(theta) is mapped linearly onto the wall potentials,
+  rho_s^w = max(cos theta, 0) * RHO_S_MAX (water-wet) and
+  rho_s^o = max(-cos theta, 0) * RHO_S_MAX (oil-wet); the actual contact angle
+  of the model is not calibrated here;
+* viscosity ratio r: tau^w = 1 and tau^o = 3 r nu^w + 1/2, clipped so that
+  both relaxation times stay >= 0.85 (the plain BGK collision drives the
+  minority density negative below ~0.8 with the interaction strength used);
+* "moving": the oil centre of mass travels more than lambda / 2 within one
+  probe window.
+
+Surrogate features (all O(1)): amplitude ratio, slug length / lambda,
+cos(theta), log(viscosity ratio), 1 / resolution with the resolution the
+neck width 2 (h0 - A) in nodes.  Target: log g_crit, g_crit the geometric
+mean of the final bracket.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import workloads as wl
+
+G_INTERACTION = -1.79
+RHO_S_MAX = 0.5
+TAU_MIN = 0.85
+
+
+def relaxation_times(visc_ratio: float):
+    nu_w = (1.0 - 0.5) / 3.0
+    tau_o = 3.0 * visc_ratio * nu_w + 0.5
+    return (max(tau_o, TAU_MIN), 1.0)
+
+
+def wall_potentials(theta_deg: float):
+    c = math.cos(math.radians(theta_deg))
+    return (max(-c, 0.0) * RHO_S_MAX, max(c, 0.0) * RHO_S_MAX)
+
+
+def instance_of(spec: wl.ChannelSpec) -> dict:
+    w = wl.channel_instance(spec)
+    return dict(mask=w.mask, rho_init=w.rho, tau=relaxation_times(spec.visc_ratio), G=G_INTERACTION,
+                rho_wall=wall_potentials(spec.theta_deg), g=(0.0, 0.0), periodic=w.periodic,
+                disp_threshold=0.5 * spec.lam)
+
+
+def features(spec: wl.ChannelSpec) -> np.ndarray:
+    neck = 2.0 * (spec.h0 - spec.amp)
+    return np.array([spec.amp_ratio, spec.slug_len_over_lambda, math.cos(math.radians(spec.theta_deg)),
+                     math.log(spec.visc_ratio), 1.0 / neck], dtype=np.float64)
+
+
+def small_specs(n: int, seed: int, lambdas=(32, 48, 64)) -> list:
+    """Sweep instances scaled to a budget: lambda in `lambdas`, 4 periods,
+    A/h0 ~ U[0.2, 0.6], slug/lambda ~ U[1, 2], theta ~ U[20, 160] deg,
+    viscosity ratio log-U[0.5, 2]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        out.append(wl.ChannelSpec(
+            lam=int(rng.choice(np.asarray(lambdas))),
+            amp_ratio=float(rng.uniform(0.2, 0.6)),
+            slug_len_over_lambda=float(rng.uniform(1.0, 2.0)),
+            theta_deg=float(rng.uniform(20.0, 160.0)),
+            visc_ratio=float(np.exp(rng.uniform(np.log(0.5), np.log(2.0))))))
+    return out
+
+
+def run_sweep(lbm, specs, g_lo, g_hi, precision="fp32", rel_bracket=0.02, t_eq=1000, t_obs=2000,
+              max_probes=24, check_bracket=True, timeout_s=0.0):
+    """Batched bisection of every spec; returns (results, seconds)."""
+    insts = [instance_of(s) for s in specs]
+    t0 = time.perf_counter()
+    b = lbm.Batch(insts, precision=precision)
+    try:
+        res = b.critical_pressure(np.broadcast_to(np.asarray(g_lo, dtype=np.float64), (len(specs),)).copy(),
+                                  np.broadcast_to(np.asarray(g_hi, dtype=np.float64), (len(specs),)).copy(),
+                                  rel_bracket=rel_bracket, t_eq=t_eq, t_obs=t_obs, max_probes=max_probes,
+                                  check_bracket=check_bracket, timeout_s=timeout_s, check=False)
+    finally:
+        b.close()
+    return res, time.perf_counter() - t0
+
+
+def run_plain(lbm, specs, g_lo, g_hi, **kw):
+    """The same bisection one instance at a time (the baseline)."""
+    res, total = [], 0.0
+    for k, s in enumerate(specs):
+        lo = np.atleast_1d(g_lo)[k if np.ndim(g_lo) else 0]
+        hi = np.atleast_1d(g_hi)[k if np.ndim(g_hi) else 0]
+        r, dt = run_sweep(lbm, [s], lo, hi, **kw)
+        res += r
+        total += dt
+    return res, total
+
+
+def surrogate_brackets(net, specs, scale_x, k_sigma=2.0, floor=1.05):
+    """exp(mu -+ k sigma) from the surrogate; the bracket is at least a
+    factor `floor` wide."""
+    x = np.stack([features(s) for s in specs])
+    xs = ((x - scale_x[0]) / scale_x[1]).astype(np.float32)
+    out = net.forward(xs).astype(np.float64)
+    mu, s = out[:, 0], out[:, 1]
+    half = np.maximum(k_sigma * np.exp(0.5 * s), 0.5 * math.log(floor))
+    return np.exp(mu - half), np.exp(mu + half)

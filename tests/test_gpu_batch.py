@@ -1,0 +1,169 @@
+"""GPU tests of the batched path: many uneven channels in one launch per step,
+and the device-side bisection of the critical body force (Section 3.4)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.bisect import bisect_critical
+from paper_1601_00918_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+G = -1.79
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1601_00918_gb300 import build
+    build.build()
+    from paper_1601_00918_gb300 import lbm as mod
+    mod.library()
+    return mod
+
+
+def channel_instance(lam, periods, h0, amp, slug_len, tau=(1.0, 1.0), rho_wall=(0.3, 0.1), g=0.0):
+    nx = int(lam * periods)
+    ny = 2 * int(np.ceil(h0 + amp)) + 2
+    mask = wl.sinusoidal_channel(nx, ny, h0, amp, float(lam))
+    centre = lam * (periods // 2)
+    rho = wl.slug(nx, ny, centre - slug_len / 2, centre + slug_len / 2)
+    return dict(mask=mask, rho_init=rho, tau=tau, G=G, rho_wall=rho_wall, g=(g, 0.0), periodic=(True, False),
+                disp_threshold=lam / 2.0)
+
+
+def uneven_instances():
+    return [channel_instance(32, 3, 6.0, 2.0, 24.0, tau=(1.0, 0.9)),
+            channel_instance(48, 3, 9.0, 4.0, 40.0, rho_wall=(0.1, 0.4), g=2e-5),
+            channel_instance(100, 3, 12.0, 5.0, 90.0, tau=(0.9, 1.2), g=-1e-5),
+            channel_instance(20, 2, 4.0, 1.0, 12.0)]
+
+
+def test_batch_steps_match_single_grids(lbm):
+    """Four channels of different sizes (one narrower than a tile, one with
+    a ragged last tile) stepped together agree with each one stepped alone
+    through lbm_create / lbm_step (FP64: to rounding)."""
+    inst = uneven_instances()
+    b = lbm.Batch(inst, precision="fp64")
+    try:
+        b.step(40)
+        got = [b.save(i) for i in range(len(inst))]
+        obs = b.observables()
+    finally:
+        b.close()
+    for d, f_b, o in zip(inst, got, obs):
+        sim = lbm.Simulation(d["mask"], d["rho_init"], tau=d["tau"], G=d["G"], rho_wall=d["rho_wall"],
+                             g=d["g"], periodic=d["periodic"], precision="fp64", variant="simple")
+        try:
+            sim.step(40)
+            f_s = sim.save()
+            o_s = sim.observables()
+        finally:
+            sim.close()
+        np.testing.assert_allclose(f_b, f_s, rtol=0, atol=1e-13)
+        assert o["step"] == 40
+        np.testing.assert_allclose(o["mass"], o_s["mass"], rtol=1e-13)
+        np.testing.assert_allclose(o["oil_disp_x"], o_s["oil_disp_x"], rtol=1e-9, atol=1e-13)
+
+
+def test_batch_steps_fp32_match_oracle(lbm):
+    inst = uneven_instances()[:2]
+    b = lbm.Batch(inst, precision="fp32")
+    try:
+        b.step(30)
+        got = [b.save(i) for i in range(len(inst))]
+    finally:
+        b.close()
+    for d, f_b in zip(inst, got):
+        P = oracle.Problem(d["mask"], tau=d["tau"], G=d["G"], rho_wall=d["rho_wall"], g=d["g"],
+                           periodic=d["periodic"])
+        f_r = P.run(P.init(d["rho_init"]), 30)
+        np.testing.assert_allclose(f_b, f_r, rtol=0, atol=2e-5)
+
+
+def gpu_moving(lbm, d, f_eq, t_obs, precision="fp64"):
+    """One probe through the single-grid ABI: restart from f_eq at g."""
+    def moving(g):
+        sim = lbm.Simulation(d["mask"], d["rho_init"], tau=d["tau"], G=d["G"], rho_wall=d["rho_wall"],
+                             g=(g, 0.0), periodic=d["periodic"], precision=precision, variant="simple")
+        try:
+            sim.load(f_eq)
+            sim.step(t_obs)
+            o = sim.observables(check=False)
+        finally:
+            sim.close()
+        if o["nan_flag"]:
+            return None
+        return abs(o["oil_disp_x"]) > d["disp_threshold"]
+    return moving
+
+
+def test_device_bisection_follows_the_protocol(lbm):
+    """The device bisection (all instances in lockstep, decisions in FP64 on
+    the GPU) returns the same brackets as the host statement of the protocol
+    driving single-grid probes from the same equilibrated state."""
+    inst = [channel_instance(32, 2, 6.0, 3.0, 24.0), channel_instance(40, 2, 7.0, 2.0, 30.0, tau=(1.0, 0.9))]
+    t_eq, t_obs = 600, 1500
+    g_lo = np.array([2e-5, 2e-5])
+    g_hi = np.array([4e-4, 4e-4])
+    b = lbm.Batch(inst, precision="fp64")
+    try:
+        res = b.critical_pressure(g_lo, g_hi, rel_bracket=0.05, t_eq=t_eq, t_obs=t_obs, max_probes=16)
+    finally:
+        b.close()
+    for k, d in enumerate(inst):
+        sim = lbm.Simulation(d["mask"], d["rho_init"], tau=d["tau"], G=d["G"], rho_wall=d["rho_wall"],
+                             g=(0.0, 0.0), periodic=d["periodic"], precision="fp64", variant="simple")
+        try:
+            sim.step(t_eq)
+            f_eq = sim.save()
+        finally:
+            sim.close()
+        ref = bisect_critical(gpu_moving(lbm, d, f_eq, t_obs), g_lo[k], g_hi[k], rel=0.05, max_probes=16)
+        assert res[k]["status"] == ref["status"]
+        assert res[k]["probes"] == ref["probes"]
+        np.testing.assert_allclose([res[k]["g_lo"], res[k]["g_hi"]], [ref["g_lo"], ref["g_hi"]], rtol=1e-12)
+
+
+def test_bisection_matches_oracle_bracket(lbm):
+    """End to end on a small channel (64 x 20, lambda = 32): the GPU batch
+    bisection (FP32) and the FP64 oracle running the same protocol end with
+    brackets that overlap or touch (one 5 % bracket)."""
+    d = channel_instance(32, 2, 6.0, 3.0, 24.0)
+    t_eq, t_obs = 600, 1500
+    b = lbm.Batch([d], precision="fp32")
+    try:
+        res = b.critical_pressure([2e-5], [4e-4], rel_bracket=0.05, t_eq=t_eq, t_obs=t_obs, max_probes=16)[0]
+    finally:
+        b.close()
+    P = oracle.Problem(d["mask"], tau=d["tau"], G=d["G"], rho_wall=d["rho_wall"], g=(0.0, 0.0),
+                       periodic=d["periodic"])
+    f_eq = P.run(P.init(d["rho_init"]), t_eq)
+
+    def moving(g):
+        Pg = oracle.Problem(d["mask"], tau=d["tau"], G=d["G"], rho_wall=d["rho_wall"], g=(g, 0.0),
+                            periodic=d["periodic"])
+        _, hist = Pg.run(f_eq, t_obs, history=True)
+        if hist[:, 4].any():
+            return None
+        return abs(np.sum(hist[:, 2] / hist[:, 0])) > d["disp_threshold"]
+
+    ref = bisect_critical(moving, 2e-5, 4e-4, rel=0.05, max_probes=16)
+    assert res["status"] == 0 and ref["status"] == 0
+    assert res["g_lo"] <= ref["g_hi"] * (1 + 1e-12) and ref["g_lo"] <= res["g_hi"] * (1 + 1e-12)
+
+
+def test_bisection_status_paths(lbm):
+    """max_probes reached -> status 1; a bracket below the critical force is
+    expanded upwards until g_hi moves."""
+    d = channel_instance(32, 2, 6.0, 3.0, 24.0)
+    b = lbm.Batch([d, d], precision="fp32")
+    try:
+        res = b.critical_pressure([2e-5, 1e-6], [4e-4, 2e-6], rel_bracket=1e-6, t_eq=300, t_obs=800,
+                                  max_probes=6)
+    finally:
+        b.close()
+    assert res[0]["status"] == 1 and res[0]["probes"] == 6
+    assert res[1]["g_hi"] > 2e-6          # expanded

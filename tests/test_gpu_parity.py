@@ -224,6 +224,31 @@ def test_set_body_force_and_save_load_roundtrip(lbm):
     np.testing.assert_allclose(f10, P2.run(P.run(P.init(rho), 5), 5), rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("tune", ["staged,64,1,2", "staged,64,2,3", "staged,128,1,2", "staged,128,2,5",
+                                  "simple,7"])
+@pytest.mark.parametrize("precision", ["fp32", "fp16s"])
+def test_every_launch_configuration(lbm, tune, precision, monkeypatch):
+    """Each staged configuration (64 or 128 columns per CTA, 1 or 2 rows in
+    flight, several strips) and the simple kernel, pinned through the tuning
+    override, run 20 steps with no bounded wait giving up and agree with
+    the oracle."""
+    monkeypatch.setenv("GB300LBM_TUNE", tune)
+    mask, rho, kw = channel()
+    sim = lbm.Simulation(mask, rho, precision=precision, **kw)
+    try:
+        info = sim.kernel_info()
+        sim.step(20)
+        obs = sim.observables(check=False)
+        rho_g, _, _ = sim.fields()
+    finally:
+        sim.close()
+    assert info["variant"] == tune.split(",")[0]
+    assert obs["timeout_flag"] == 0 and obs["nan_flag"] == 0 and obs["step"] == 20
+    P = oracle.Problem(mask, **kw)
+    rho_r, _, _ = P.fields(P.run(P.init(rho), 20))
+    assert np.max(np.abs(rho_g - rho_r)) < (1e-5 if precision == "fp32" else 1e-3)
+
+
 @pytest.mark.parametrize("precision,atol", [("fp64", 1e-13), ("fp32", 5e-6), ("fp16s", 5e-4),
                                              ("bf16s", 4e-3)])
 def test_variants_agree(lbm, precision, atol):

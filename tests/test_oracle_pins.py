@@ -313,3 +313,90 @@ def test_oracle_rejects_open_boundary_without_walls():
     mask = np.zeros((6, 8), dtype=np.uint8)
     with pytest.raises(ValueError):
         oracle.Problem(mask, periodic=(True, False))
+
+
+# ----------------------------------------------------------------------------
+# bisection protocol of the critical body force
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("g_true,lo,hi", [(1.3e-4, 1e-4, 4e-4), (5e-4, 1e-4, 2e-4), (3e-5, 1e-4, 4e-4)])
+def test_bisection_brackets_a_sharp_threshold(g_true, lo, hi):
+    """With a sharp threshold (moving iff g > g_true) the final bracket
+    contains g_true and is at most rel wide, also when g_true lies above or
+    below the initial bracket (expansion), with the probe count the
+    geometric bisection needs."""
+    from oracle.bisect import bisect_critical
+    r = bisect_critical(lambda g: g > g_true, lo, hi, rel=0.02)
+    assert r["status"] == 0
+    assert r["g_lo"] <= g_true <= r["g_hi"]
+    assert r["g_hi"] - r["g_lo"] <= 0.02 * r["g_hi"]
+    if lo < g_true < hi:
+        # two checks + ceil(log2(ln(hi/lo)/ln(1/(1-0.02)))) halvings at most
+        assert r["probes"] <= 2 + math.ceil(math.log2(math.log(hi / lo) / -math.log(1 - 0.02))) + 1
+
+
+def test_bisection_status_codes():
+    from oracle.bisect import bisect_critical
+    assert bisect_critical(lambda g: None, 1.0, 2.0)["status"] == 2
+    r = bisect_critical(lambda g: g > 1.5, 1.0, 2.0, rel=1e-9, max_probes=5)
+    assert r["status"] == 1 and r["probes"] == 5
+    r = bisect_critical(lambda g: g > 1.5, 1.0, 2.0, check_bracket=False)
+    assert r["status"] == 0 and r["probes"] <= 6
+
+
+# ----------------------------------------------------------------------------
+# surrogate network (not in the paper; seeds the bisection brackets)
+# ----------------------------------------------------------------------------
+def test_mlp_parameter_count_and_layout():
+    from oracle import mlp
+    assert mlp.n_params() == 34050
+    th = np.arange(mlp.n_params(), dtype=np.float64)
+    (W1, b1), (W2, b2), (W3, b3), (W4, b4) = mlp.unpack(th)
+    assert W1.shape == (128, 5) and W4.shape == (2, 128) and b4.shape == (2,)
+    assert W1[0, 0] == 0 and b1[0] == 640 and W2[0, 0] == 768
+
+
+def test_mlp_gradient_matches_central_differences():
+    """The chain-rule gradient of the Gaussian NLL matches central finite
+    differences of the loss to 1e-6 relative on sampled coordinates
+    (including first-layer weights, hidden biases and the output layer)."""
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    th = mlp.init_params(1)
+    x = rng.normal(size=(16, 5))
+    y = rng.normal(size=16)
+    L, g = mlp.grad(th, x, y)
+    assert L == pytest.approx(mlp.loss(th, x, y), rel=1e-14)
+    idx = np.concatenate([rng.choice(640, 6, replace=False), [640, 700], rng.choice(np.arange(768, 33664), 8),
+                          np.arange(33794, 34050, 37), [34048, 34049]])
+    h = 1e-6
+    for k in idx:
+        e = np.zeros_like(th)
+        e[k] = h
+        fd = (mlp.loss(th + e, x, y) - mlp.loss(th - e, x, y)) / (2 * h)
+        assert g[k] == pytest.approx(fd, rel=1e-6, abs=1e-10), k
+
+
+def test_mlp_closed_forms():
+    """SiLU(0) = 0, SiLU'(0) = 1/2; with zero weights the network outputs
+    its output bias, and the NLL of (mu, s) is minimised at mu = y,
+    s = log((y - mu)^2): the gradient of the output bias is zero there."""
+    from oracle import mlp
+    assert mlp.silu(0.0) == 0.0 and mlp.dsilu(0.0) == 0.5
+    th = np.zeros(mlp.n_params())
+    th[-2:] = [0.3, np.log(0.25)]                # mu = 0.3, variance 0.25
+    x = np.ones((4, 5))
+    out, _, _ = mlp.forward(th, x)
+    np.testing.assert_allclose(out, np.tile([0.3, np.log(0.25)], (4, 1)))
+    y = np.array([0.8, -0.2, 0.8, -0.2])         # residuals +-0.5: mean square 0.25
+    _, g = mlp.grad(th, x, y)
+    np.testing.assert_allclose(g[-2:], 0.0, atol=1e-15)
+
+
+def test_adam_first_step_is_lr_times_sign():
+    """With bias correction the first Adam step moves every parameter by
+    lr * g / (|g| + eps), i.e. lr in the direction of -sign(g)."""
+    from oracle import mlp
+    th = np.zeros(5)
+    g = np.array([1.0, -2.0, 0.5, 1e-3, -7.0])
+    th1, m, v = mlp.adam_step(th, g, np.zeros(5), np.zeros(5), 1, lr=0.01, eps=0.0)
+    np.testing.assert_allclose(th1, -0.01 * np.sign(g), rtol=1e-12)
