@@ -1,0 +1,69 @@
+"""GPU tests of the critical-body-force sweep: batched vs one-at-a-time
+bisection, and what the surrogate-seeded brackets gain."""
+import numpy as np
+import pytest
+
+from paper_1601_00918_gb300 import sweep
+
+pytestmark = pytest.mark.gpu
+
+T_EQ, T_OBS = 800, 1600
+WIDE = (1e-6, 1e-3)
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1601_00918_gb300 import build
+    build.build()
+    from paper_1601_00918_gb300 import lbm as mod
+    mod.library()
+    return mod
+
+
+def test_batched_equals_one_at_a_time(lbm):
+    """Eight uneven channels bisected together end with the same brackets
+    as the same bisection run one channel at a time (the plain baseline)."""
+    specs = sweep.small_specs(8, seed=3)
+    kw = dict(t_eq=T_EQ, t_obs=T_OBS, rel_bracket=0.02, max_probes=24)
+    res_b, t_b = sweep.run_sweep(lbm, specs, *WIDE, **kw)
+    res_p, t_p = sweep.run_plain(lbm, specs, *WIDE, **kw)
+    for rb, rp in zip(res_b, res_p):
+        assert rb["status"] == rp["status"]
+        if rb["status"] == 0:
+            np.testing.assert_allclose([rb["g_lo"], rb["g_hi"]], [rp["g_lo"], rp["g_hi"]], rtol=1e-9)
+    assert sum(r["status"] == 0 for r in res_b) >= 6
+
+
+def test_surrogate_seeded_brackets_save_probes(lbm):
+    """Train the surrogate on the outcomes of a sweep (the LBM itself makes
+    the data), then bisect fresh channels from the surrogate's +-2 sigma
+    brackets: fewer probes per solve than from the wide bracket, and every
+    converged result overlaps the wide-bracket result (the LBM bisection
+    stays the judge; a failed surrogate bracket is expanded)."""
+    train_specs = sweep.small_specs(192, seed=1)
+    res, _ = sweep.run_sweep(lbm, train_specs, *WIDE, t_eq=T_EQ, t_obs=T_OBS, rel_bracket=0.02)
+    ok = [k for k, r in enumerate(res) if r["status"] == 0]
+    assert len(ok) > 120
+    x = np.stack([sweep.features(train_specs[k]) for k in ok])
+    y = np.array([0.5 * np.log(res[k]["g_lo"] * res[k]["g_hi"]) for k in ok])
+    scale = (x.mean(axis=0), x.std(axis=0) + 1e-12)
+    net = lbm.Surrogate(seed=0)
+    try:
+        net.train((x - scale[0]) / scale[1], y, epochs=400, batch=64, lr=2e-3, seed=0)
+        test_specs = sweep.small_specs(48, seed=2)
+        lo, hi = sweep.surrogate_brackets(net, test_specs, scale)
+    finally:
+        net.close()
+    res_s, _ = sweep.run_sweep(lbm, test_specs, lo, hi, t_eq=T_EQ, t_obs=T_OBS, rel_bracket=0.02)
+    res_w, _ = sweep.run_sweep(lbm, test_specs, *WIDE, t_eq=T_EQ, t_obs=T_OBS, rel_bracket=0.02)
+    both = [k for k in range(len(test_specs)) if res_s[k]["status"] == 0 and res_w[k]["status"] == 0]
+    assert len(both) > 30
+    probes_s = np.mean([res_s[k]["probes"] for k in both])
+    probes_w = np.mean([res_w[k]["probes"] for k in both])
+    assert probes_s < probes_w, (probes_s, probes_w)
+    for k in both:
+        a, b = res_s[k], res_w[k]
+        assert a["g_lo"] <= b["g_hi"] * 1.0001 and b["g_lo"] <= a["g_hi"] * 1.0001, (k, a, b)
