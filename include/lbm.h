@@ -142,6 +142,32 @@ int lbm_load(lbm_t *h, const double *f);
  * method: a report of this library's tuning. */
 int lbm_kernel_info(const lbm_t *h, int32_t info[4]);
 
+/* One FP32 time step that allocates nothing, for callers that cannot call
+ * cudaMalloc: code running while a CUDA graph is being captured, real-time
+ * loops that must not allocate, plug-ins whose device memory belongs to a
+ * host framework's allocator.  The paper has no counterpart; this is a
+ * calling convention of this library.
+ *   mask  device uint8 [ny][nx], 1 = solid (same rules as lbm_create)
+ *   f_in  device float [2][9][ny][nx] stored populations (the lbm_save layout,
+ *         dense, no padding)
+ *   f_out device float, same layout; receives the next stored state at fluid
+ *         nodes (solid nodes are not written)
+ *   obs   device lbm_obs receiving this step's observables (step = 1,
+ *         oil_disp_x = this step's displacement), or NULL
+ *   p     host parameters: precision must be LBM_FP32; nx * ny <= 2097152;
+ *         p->cuda_stream is the stream of all work; variant and workspace
+ *         fields are ignored
+ * The scratch is one static device array of 4 MiB + 1 KiB that every GPU
+ * which loads this library holds until the process exits.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.
+ * Every call shares the array: calls that may overlap on the GPU (on
+ * different streams, or from several threads) race; serialise them.  The
+ * call is asynchronous and returns LBM_EINVAL for sizes beyond the limit, a
+ * precision other than LBM_FP32 or NULL pointers. */
+int lbm_step_noalloc(const uint8_t *mask, const float *f_in, float *f_out, lbm_obs *obs,
+                     const lbm_params *p);
+
 /* Free the handle and the device memory it owns.  NULL is ignored. */
 void lbm_destroy(lbm_t *h);
 

@@ -832,3 +832,131 @@ void lbm_destroy(lbm_t* h) {
 const char* lbm_last_error(const lbm_t* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free step
+//
+// For callers that cannot allocate device memory: code running while a CUDA
+// graph is being captured (cudaMalloc is not allowed there), real-time loops
+// that must not allocate, or plug-ins whose device memory is owned by a host
+// framework's allocator.  The caller passes device inputs and outputs; the
+// step's scratch (link words, parameters, reduction accumulators) lives in
+// one fixed device array of this file.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Largest lattice the allocation-free entry point accepts (nx * ny).
+constexpr int kNoAllocMaxNodes = 1 << 21;
+// Scratch layout: [StepParams | ObsAccum | ObsState | link words (uint16)].
+constexpr size_t kNoAllocHead = 1024;
+constexpr size_t kNoAllocBytes = kNoAllocHead + sizeof(uint16_t) * (size_t)kNoAllocMaxNodes;
+
+// The scratch of lbm_step_noalloc: a fixed device array that every GPU which
+// loads the library holds until the process exits (4 MiB + 1 KiB).  In host
+// code this name is only a host-side stand-in; its device address is taken
+// with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kMaxDevices] = {};
+
+static_assert(sizeof(StepParams) + sizeof(ObsAccum) + sizeof(ObsState) <= kNoAllocHead, "scratch head");
+
+// Link words of a dense [ny][nx] lattice (no ghost columns), plus the
+// parameters and cleared accumulators, into the scratch.
+__global__ void noalloc_prepare_kernel(const uint8_t* __restrict__ mask, unsigned char* __restrict__ scratch, int nx,
+                                       int ny, StepParams prm) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x == 0 && y == 0) {
+        *(StepParams*)scratch = prm;
+        ObsAccum* acc = (ObsAccum*)(scratch + sizeof(StepParams));
+        ObsState* obs = (ObsState*)(scratch + sizeof(StepParams) + sizeof(ObsAccum));
+        memset(acc, 0, sizeof(ObsAccum));
+        memset(obs, 0, sizeof(ObsState));
+    }
+    if (x >= nx || y >= ny) return;
+    unsigned w = mask[y * nx + x] ? (1u << kSolidBit) : 0u;
+    for (int i = 1; i < 9; i++) {
+        int sx = x - d2q9_cx(i), sy = y - d2q9_cy(i);
+        sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+        if (mask[sy * nx + sx]) w |= 1u << i;
+    }
+    ((uint16_t*)(scratch + kNoAllocHead))[y * nx + x] = uint16_t(w);
+}
+
+__global__ void noalloc_obs_kernel(const unsigned char* __restrict__ scratch, lbm_obs* __restrict__ out) {
+    const ObsState* s = (const ObsState*)(scratch + sizeof(StepParams) + sizeof(ObsAccum));
+    out->mass[0] = s->mass[0];
+    out->mass[1] = s->mass[1];
+    out->oil_mom_x = s->px;
+    out->oil_disp_x = s->disp;
+    out->max_u = s->umax;
+    out->step = s->step;
+    out->nan_flag = s->nan_flag;
+    out->timeout_flag = s->timeout_flag;
+}
+
+}  // namespace
+
+extern "C" int lbm_step_noalloc(const uint8_t* mask, const float* f_in, float* f_out, lbm_obs* obs,
+                                const lbm_params* p) {
+    if (!mask || !f_in || !f_out || !p) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: NULL argument");
+    if (p->precision != LBM_FP32) return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: precision must be LBM_FP32");
+    if (p->nx < 1 || p->ny < 1 || (int64_t)p->nx * p->ny > kNoAllocMaxNodes)
+        return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: nx * ny must be in [1, %d] (got %d x %d)",
+                    kNoAllocMaxNodes, p->nx, p->ny);
+    if (p->eq_order != 2 && p->eq_order != 3) return fail(nullptr, LBM_EINVAL, "eq_order must be 2 or 3");
+    for (int a = 0; a < 2; a++)
+        if (!(p->tau[a] > 0.5)) return fail(nullptr, LBM_EINVAL, "tau[%d] must exceed 1/2", a);
+    int dev = 0;
+    CUDA_TRY(nullptr, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, LBM_EINVAL, "device %d out of range", dev);
+    unsigned char* scratch = nullptr;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess)
+                return fail(nullptr, LBM_ECUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = (unsigned char*)ptr;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    const int nx = p->nx, ny = p->ny;
+    cudaStream_t st = (cudaStream_t)p->cuda_stream;
+    StepParams prm{};
+    for (int a = 0; a < 2; a++) {
+        prm.nu[a] = (p->tau[a] - 0.5) / 3.0;
+        prm.rho_wall[a] = p->rho_wall[a];
+        prm.g[a] = p->g[a];
+    }
+    prm.G = p->G;
+    prm.k3 = p->eq_order >= 3 ? 4.5 : 0.0;
+    noalloc_prepare_kernel<<<dim3((nx + 127) / 128, ny), 128, 0, st>>>(mask, scratch, nx, ny, prm);
+    CUDA_TRY(nullptr, cudaGetLastError());
+    Grid g;
+    g.nx = nx;
+    g.ny = ny;
+    g.pitch = nx;            // dense rows, no ghost columns
+    g.periodic_x = 0;        // no ghost images to write (pulls still wrap)
+    g.rows_per_block = std::max(4, std::min(ny, 32));
+    g.row_begin = 0;
+    g.row_end = ny;
+    g.strips = 1;
+    dim3 grid((nx + kBX - 1) / kBX, (ny + g.rows_per_block - 1) / g.rows_per_block);
+    step_simple_kernel<float, kBX, false><<<grid, kBX, 0, st>>>(
+        f_in, f_out, (const uint16_t*)(scratch + kNoAllocHead), (const StepParams*)scratch,
+        (ObsAccum*)(scratch + sizeof(StepParams)), (ObsState*)(scratch + sizeof(StepParams) + sizeof(ObsAccum)),
+        nullptr, g);
+    CUDA_TRY(nullptr, cudaGetLastError());
+    if (obs) {
+        noalloc_obs_kernel<<<1, 1, 0, st>>>(scratch, obs);
+        CUDA_TRY(nullptr, cudaGetLastError());
+    }
+    return LBM_OK;
+}

@@ -30,7 +30,7 @@ EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "l
            "lbm_batch_set_body_force", "lbm_batch_save", "lbm_critical_pressure_batch",
            "lbm_batch_destroy", "lbm_batch_last_error", "lbm_mlp_create", "lbm_mlp_params",
            "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam", "lbm_mlp_train", "lbm_mlp_destroy",
-           "lbm_mlp_last_error")
+           "lbm_mlp_last_error", "lbm_step_noalloc")
 
 
 class LbmError(RuntimeError):
@@ -106,6 +106,8 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_save.argtypes = [vp, dp]
     lib.lbm_load.argtypes = [vp, dp]
     lib.lbm_kernel_info.argtypes = [vp, P(ctypes.c_int32)]
+    lib.lbm_step_noalloc.argtypes = [vp, vp, vp, vp, P(Params)]
+    lib.lbm_step_noalloc.restype = ctypes.c_int
     lib.lbm_batch_create.argtypes = [P(Instance), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, P(vp)]
     lib.lbm_batch_step.argtypes = [vp, ctypes.c_int64]
     lib.lbm_batch_observables.argtypes = [vp, P(Obs)]
