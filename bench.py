@@ -272,6 +272,7 @@ def native_arm(args):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_seconds)
+    crit = critical_pressure_arm(args) if rank == 0 and args.sweep_n > 0 else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -288,11 +289,60 @@ def native_arm(args):
                              "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                              "kernel": "step_%s_kernel" % kinfo["variant"],
                              "alg_bytes_per_launch": alg_bytes},
-                "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "cpu_baseline": cpu}
+                "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "cpu_baseline": cpu,
+                "critical_pressure": crit}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def critical_pressure_arm(args):
+    """Critical-pressure solves per hour on this GPU: the batched device
+    bisection of n channels vs the same bisection one channel at a time
+    (a subset, per-solve time extrapolated), and the batched bisection from
+    surrogate-seeded brackets (surrogate trained on a separate sweep)."""
+    import numpy as np
+    from paper_1601_00918_gb300 import lbm, sweep
+    kw = dict(t_eq=800, t_obs=1600, rel_bracket=0.02, max_probes=24)
+    wide = (1e-6, 1e-3)
+    specs = sweep.small_specs(args.sweep_n, seed=2)
+    res_b, t_b = sweep.run_sweep(lbm, specs, *wide, **kw)
+    ok_b = sum(r["status"] == 0 for r in res_b)
+    sub = specs[:args.sweep_plain]
+    res_p, t_p = sweep.run_plain(lbm, sub, *wide, **kw)
+    ok_p = sum(r["status"] == 0 for r in res_p)
+    # surrogate: trained on outcomes of another sweep
+    train = sweep.small_specs(args.sweep_train, seed=1)
+    t0 = time.perf_counter()
+    res_t, _ = sweep.run_sweep(lbm, train, *wide, **kw)
+    good = [k for k, r in enumerate(res_t) if r["status"] == 0]
+    x = np.stack([sweep.features(train[k]) for k in good])
+    y = np.array([0.5 * np.log(res_t[k]["g_lo"] * res_t[k]["g_hi"]) for k in good])
+    scale = (x.mean(axis=0), x.std(axis=0) + 1e-12)
+    net = lbm.Surrogate(seed=0)
+    net.train((x - scale[0]) / scale[1], y, epochs=400, batch=64, lr=2e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    lo, hi = sweep.surrogate_brackets(net, specs, scale)
+    net.close()
+    res_s, t_s = sweep.run_sweep(lbm, specs, lo, hi, **kw)
+    ok_s = sum(r["status"] == 0 for r in res_s)
+    agree = sum(1 for a, b in zip(res_s, res_b) if a["status"] == 0 and b["status"] == 0
+                and a["g_lo"] <= b["g_hi"] * 1.0001 and b["g_lo"] <= a["g_hi"] * 1.0001)
+    both = sum(1 for a, b in zip(res_s, res_b) if a["status"] == 0 and b["status"] == 0)
+    return {"instances": len(specs), "bracket": "2 % (relative), device FP64 decisions",
+            "t_eq": kw["t_eq"], "t_obs": kw["t_obs"], "wide_bracket": list(wide),
+            "batched": {"solved": ok_b, "seconds": t_b, "solves_per_hour": 3600.0 * ok_b / t_b,
+                        "mean_probes": float(np.mean([r["probes"] for r in res_b]))},
+            "plain_one_at_a_time": {"instances": len(sub), "solved": ok_p, "seconds": t_p,
+                                    "solves_per_hour": 3600.0 * ok_p / t_p},
+            "surrogate_seeded": {"solved": ok_s, "seconds": t_s, "solves_per_hour": 3600.0 * ok_s / t_s,
+                                 "mean_probes": float(np.mean([r["probes"] for r in res_s])),
+                                 "brackets_overlapping_wide_result": f"{agree}/{both}",
+                                 "training_sweep": len(train), "training_seconds": t_train},
+            "speedup_batched_vs_plain": (ok_b / t_b) / max(ok_p / t_p, 1e-30),
+            "speedup_seeded_vs_plain": (ok_s / t_s) / max(ok_p / t_p, 1e-30)}
 
 
 def e2e_arm(args, w, prec, device, n_fluid):
@@ -340,6 +390,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-n", type=int, default=64, help="channels of the solves/hour sweep (0: skip)")
+    ap.add_argument("--sweep-plain", type=int, default=8, help="channels bisected one at a time")
+    ap.add_argument("--sweep-train", type=int, default=192, help="channels of the surrogate's training sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kTileX) batch_step_kernel(BatchInst* __restric
                                                             S* __restrict__ fb, const uint16_t* __restrict__ links,
                                                             int parity) {
     using R = typename Codec<S>::R;
-    __shared__ R s_rho[4][2][kTileX + 2];
+    __shared__ pair_t<R> s_rho[4][kTileX + 2];
     const int ti = blockIdx.x;
     const int i = tile_inst[ti];
     BatchInst* I = inst + i;

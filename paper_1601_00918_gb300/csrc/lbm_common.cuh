@@ -196,6 +196,29 @@ __device__ __forceinline__ void equilibrium(R rho, R ux, R uy, R k3, R (&out)[9]
     }
 }
 
+// The density ring holds (rho^o, rho^w) pairs so one 8- or 16-byte access
+// moves both species.
+template <typename R>
+struct Pair;
+template <>
+struct Pair<float> {
+    using T = float2;
+};
+template <>
+struct Pair<double> {
+    using T = double2;
+};
+template <typename R>
+using pair_t = typename Pair<R>::T;
+
+template <typename R>
+__device__ __forceinline__ pair_t<R> make_pair_of(R a, R b) {
+    pair_t<R> v;
+    v.x = a;
+    v.y = b;
+    return v;
+}
+
 template <typename R>
 __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
@@ -277,12 +300,14 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
     const R nu_mix = (rho0 * P.nu0 + rho1 * P.nu1) * inv_rt;
     const R om1 = R(1) - R(1) / (R(3) * nu_mix + R(0.5));   // 1 - 1/tau_mix
     R out[2][9];
+    // f_i^eq(rho^a, u_mix) = rho^a e_i(u_mix) for both species: one evaluation
+    R eu[9];
+    equilibrium<R>(R(1), ux, uy, P.k3, eu);
 #pragma unroll
     for (int a = 0; a < 2; a++) {
         const R rho = a ? rho1 : rho0;
         const R ax = a ? ax1 : ax0, ay = a ? ay1 : ay0;
-        R fu[9], fs[9];
-        equilibrium<R>(rho, ux, uy, P.k3, fu);
+        R fs[9];
         equilibrium<R>(rho, ux + ax, uy + ay, P.k3, fs);
         S* d = dst + a * 9 * plane;
         R rh = R(0);
@@ -293,7 +318,7 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
         }
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            out[a][i] = fs[i] + om1 * (f[a][i] - fu[i]);
+            out[a][i] = fs[i] + om1 * (f[a][i] - rho * eu[i]);
             d[i * plane] = C::encode(out[a][i], wgt<R>(i), rh);
         }
     }

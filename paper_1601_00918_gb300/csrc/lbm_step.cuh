@@ -46,7 +46,7 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
                                              double* __restrict__ fields, int nx, int ny, int pitch,
                                              int periodic_x, int x0, int y0, int y1, int fr0, int frows,
                                              ObsLocal<typename Codec<S>::R>& ob,
-                                             typename Codec<S>::R (*s_rho)[2][BX + 2]) {
+                                             pair_t<typename Codec<S>::R> (*s_rho)[BX + 2]) {
     using C = Codec<S>;
     using R = typename C::R;
     constexpr unsigned kSolid = 1u << kSolidBit;
@@ -145,7 +145,7 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
         v += __shfl_xor_sync(0xffffffffu, v, 1);
         if ((lane & 15) == 0) {
             const R val = (lk & kSolid) ? (sp ? P.rw1 : P.rw0) : v;
-            s_rho[sl][sp][right ? BX + 1 : 0] = val;
+            reinterpret_cast<R*>(&s_rho[sl][right ? BX + 1 : 0])[sp] = val;
         }
     };
 
@@ -159,15 +159,13 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
         if (rho_col) {
             R tmp[2][9], a, b;
             pull(y, tmp, a, b);
-            s_rho[slot(y0 - 1)][0][t + 1] = a;
-            s_rho[slot(y0 - 1)][1][t + 1] = b;
+            s_rho[slot(y0 - 1)][t + 1] = make_pair_of<R>(a, b);
         }
         halo(y, slot(y0 - 1));
     }
     if (rho_col) {
         solid_cur = pull(y0, cur, rc0, rc1);
-        s_rho[slot(y0)][0][t + 1] = rc0;
-        s_rho[slot(y0)][1][t + 1] = rc1;
+        s_rho[slot(y0)][t + 1] = make_pair_of<R>(rc0, rc1);
     }
     halo(y0, slot(y0));
 
@@ -176,8 +174,7 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
         const int sn = slot(r + 1);
         if (rho_col) {
             solid_nxt = pull(yn, nxt, rn0, rn1);
-            s_rho[sn][0][t + 1] = rn0;
-            s_rho[sn][1][t + 1] = rn1;
+            s_rho[sn][t + 1] = make_pair_of<R>(rn0, rn1);
         }
         halo(yn, sn);
         __syncthreads();
@@ -196,16 +193,19 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
                 }
             } else {
                 R nb[2][8];
-#pragma unroll
-                for (int b = 0; b < 2; b++) {
-                    nb[b][0] = s_rho[s0][b][t + 2];   // c_1 = ( 1, 0)
-                    nb[b][1] = s_rho[sp][b][t + 1];   // c_2 = ( 0, 1)
-                    nb[b][2] = s_rho[s0][b][t];       // c_3 = (-1, 0)
-                    nb[b][3] = s_rho[sm][b][t + 1];   // c_4 = ( 0,-1)
-                    nb[b][4] = s_rho[sp][b][t + 2];   // c_5 = ( 1, 1)
-                    nb[b][5] = s_rho[sp][b][t];       // c_6 = (-1, 1)
-                    nb[b][6] = s_rho[sm][b][t];       // c_7 = (-1,-1)
-                    nb[b][7] = s_rho[sm][b][t + 2];   // c_8 = ( 1,-1)
+                {
+                    const pair_t<R> e = s_rho[s0][t + 2], n = s_rho[sp][t + 1], wv = s_rho[s0][t];
+                    const pair_t<R> so = s_rho[sm][t + 1], ne = s_rho[sp][t + 2], nw = s_rho[sp][t];
+                    const pair_t<R> sw = s_rho[sm][t], se = s_rho[sm][t + 2];
+                    // neighbours x + c_k in direction order k = 1..8
+                    nb[0][0] = e.x;  nb[1][0] = e.y;
+                    nb[0][1] = n.x;  nb[1][1] = n.y;
+                    nb[0][2] = wv.x; nb[1][2] = wv.y;
+                    nb[0][3] = so.x; nb[1][3] = so.y;
+                    nb[0][4] = ne.x; nb[1][4] = ne.y;
+                    nb[0][5] = nw.x; nb[1][5] = nw.y;
+                    nb[0][6] = sw.x; nb[1][6] = sw.y;
+                    nb[0][7] = se.x; nb[1][7] = se.y;
                 }
                 if (FIELDS) {
                     node_fields<R>(cur, rc0, rc1, nb, P, fields + (size_t)(r - fr0) * nx + cx,
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(BX) step_simple_kernel(const S* __restrict__ f
                                                          ObsState* __restrict__ obs,
                                                          double* __restrict__ fields, Grid grid) {
     using R = typename Codec<S>::R;
-    __shared__ R s_rho[4][2][BX + 2];
+    __shared__ pair_t<R> s_rho[4][BX + 2];
     NodeParams<R> P;
     P.load(prm);
     const int x0 = blockIdx.x * BX;

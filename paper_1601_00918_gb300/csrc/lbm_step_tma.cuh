@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     uint64_t* bars = (uint64_t*)(smem + Plan::kBarOffset);
-    R(*s_rho)[2][BX + 2] = (R(*)[2][BX + 2])(smem + Plan::kRhoOffset);
+    pair_t<R>(*s_rho)[BX + 2] = (pair_t<R>(*)[BX + 2])(smem + Plan::kRhoOffset);
     auto pops = [&](int stage) { return (const S*)(smem + (stage % NS) * Plan::kSlot); };
     auto lnks = [&](int stage) {
         return (const uint16_t*)(smem + (stage % NS) * Plan::kSlot + Plan::kPopSlot);
@@ -192,6 +192,21 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
         const S* pm = pops(jm);
         const S* pc = pops(jc);
         const S* pp = pops(jp);
+        if (lk == 0) {
+            // interior node: every population comes from its upwind neighbour
+            const S* q[9] = {pc + w, pc + w - 1, pm + w, pc + w + 1, pp + w, pm + w - 1, pm + w + 1, pp + w + 1,
+                             pp + w - 1};
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                R r0s = R(0), r1s = R(0);
+                if (C::kNodeShift) {
+                    r0s = C::rho_value(q[i][18 * W]);
+                    r1s = C::rho_value(q[i][19 * W]);
+                }
+                f[0][i] = C::decode(q[i][i * W], wgt<R>(i), r0s);
+                f[1][i] = C::decode(q[i][(9 + i) * W], wgt<R>(i), r1s);
+            }
+        } else {
         // (plane, stage, column) of each pulled population; bounced: own opp(i)
         const bool b1 = lk & (1u << 1), b2 = lk & (1u << 2), b3 = lk & (1u << 3), b4 = lk & (1u << 4);
         const bool b5 = lk & (1u << 5), b6 = lk & (1u << 6), b7 = lk & (1u << 7), b8 = lk & (1u << 8);
@@ -216,6 +231,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
             }
             f[0][i] = C::decode(q[pl[i] * W], wgt<R>(i), r0s);
             f[1][i] = C::decode(q[(9 + pl[i]) * W], wgt<R>(i), r1s);
+        }
         }
         R a = R(0), bsum = R(0);
 #pragma unroll
@@ -257,7 +273,8 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
         v += __shfl_xor_sync(0xffffffffu, v, 4);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
         v += __shfl_xor_sync(0xffffffffu, v, 1);
-        if ((lane & 15) == 0) s_rho[sl][sp][right ? BX + 1 : 0] = (lk & kSolid) ? (sp ? P.rw1 : P.rw0) : v;
+        if ((lane & 15) == 0)
+            reinterpret_cast<R*>(&s_rho[sl][right ? BX + 1 : 0])[sp] = (lk & kSolid) ? (sp ? P.rw1 : P.rw0) : v;
     };
 
     if (t == 0) {
@@ -282,15 +299,13 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
         if (rho_col) {
             R tmp[2][9], a, b;
             pull(0, 1, 2, wi, tmp, a, b);
-            s_rho[slot(y0 - 1)][0][t + 1] = a;
-            s_rho[slot(y0 - 1)][1][t + 1] = b;
+            s_rho[slot(y0 - 1)][t + 1] = make_pair_of<R>(a, b);
         }
         halo(0, 1, 2, slot(y0 - 1));
         wait_stage(3);
         if (rho_col) {
             solid_cur = pull(1, 2, 3, wi, cur, rc0, rc1);
-            s_rho[slot(y0)][0][t + 1] = rc0;
-            s_rho[slot(y0)][1][t + 1] = rc1;
+            s_rho[slot(y0)][t + 1] = make_pair_of<R>(rc0, rc1);
         }
         halo(1, 2, 3, slot(y0));
         // stages 0 and 1 are no longer needed: refill their slots now, so
@@ -307,8 +322,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
             wait_stage(j + 2);
             if (rho_col) {
                 solid_nxt = pull(j, j + 1, j + 2, wi, nxt, rn0, rn1);
-                s_rho[sn][0][t + 1] = rn0;
-                s_rho[sn][1][t + 1] = rn1;
+                s_rho[sn][t + 1] = make_pair_of<R>(rn0, rn1);
             }
             halo(j, j + 1, j + 2, sn);
             __syncthreads();
@@ -319,16 +333,19 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
             if (active && !solid_cur) {
                 const int s0 = slot(r), sm = slot(r - 1), sp = sn;
                 R nb[2][8];
-#pragma unroll
-                for (int b = 0; b < 2; b++) {
-                    nb[b][0] = s_rho[s0][b][t + 2];   // c_1 = ( 1, 0)
-                    nb[b][1] = s_rho[sp][b][t + 1];   // c_2 = ( 0, 1)
-                    nb[b][2] = s_rho[s0][b][t];       // c_3 = (-1, 0)
-                    nb[b][3] = s_rho[sm][b][t + 1];   // c_4 = ( 0,-1)
-                    nb[b][4] = s_rho[sp][b][t + 2];   // c_5 = ( 1, 1)
-                    nb[b][5] = s_rho[sp][b][t];       // c_6 = (-1, 1)
-                    nb[b][6] = s_rho[sm][b][t];       // c_7 = (-1,-1)
-                    nb[b][7] = s_rho[sm][b][t + 2];   // c_8 = ( 1,-1)
+                {
+                    const pair_t<R> e = s_rho[s0][t + 2], n = s_rho[sp][t + 1], wv = s_rho[s0][t];
+                    const pair_t<R> so = s_rho[sm][t + 1], ne = s_rho[sp][t + 2], nw = s_rho[sp][t];
+                    const pair_t<R> sw = s_rho[sm][t], se = s_rho[sm][t + 2];
+                    // neighbours x + c_k in direction order k = 1..8
+                    nb[0][0] = e.x;  nb[1][0] = e.y;
+                    nb[0][1] = n.x;  nb[1][1] = n.y;
+                    nb[0][2] = wv.x; nb[1][2] = wv.y;
+                    nb[0][3] = so.x; nb[1][3] = so.y;
+                    nb[0][4] = ne.x; nb[1][4] = ne.y;
+                    nb[0][5] = nw.x; nb[1][5] = nw.y;
+                    nb[0][6] = sw.x; nb[1][6] = sw.y;
+                    nb[0][7] = se.x; nb[1][7] = se.y;
                 }
                 collide_store<S, R>(cur, rc0, rc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx,
                                     grid.periodic_x, ob);
