@@ -35,6 +35,7 @@
 #include "../../include/lbm.h"
 #include "lbm_step.cuh"
 #include "lbm_step_tma.cuh"
+#include "lbm_step_warp.cuh"
 #include "lbm_setup.cuh"
 
 using namespace gb300lbm;
@@ -46,7 +47,7 @@ constexpr int kRowBlock = 64;    // column granularity of the fluid-row table
 constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity is kept)
 
 struct Tuned {
-    int variant = 1;   // 1 simple, 2 staged
+    int variant = 1;   // 1 simple, 2 staged, 3 pipelined
     int depth = 2;     // staged: rows in flight
     int rpb = 16;      // simple: rows per CTA strip
     int strips = 1;    // staged: strips per column block
@@ -192,8 +193,36 @@ cudaError_t launch_staged(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, Obs
     return cudaGetLastError();
 }
 
+template <typename S, int BX, int D>
+cudaError_t launch_pipelined(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs,
+                             cudaStream_t st) {
+    using Plan = WarpPlan<S, BX, D>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(step_warp_kernel<S, BX, D>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Plan::kBytes);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    Grid g = make_grid(h, 0, h->p.ny);
+    g.strips = tn.strips;
+    dim3 grid((h->p.nx + BX - 1) / BX, tn.strips);
+    step_warp_kernel<S, BX, D><<<grid, BX, Plan::kBytes, st>>>(
+        h->fmap[src][BX == 64 ? 0 : 1], h->lmap[BX == 64 ? 0 : 1], at_col0<S>(h->fbase[1 - src]), h->rows,
+        h->dprm, acc, obs, g);
+    return cudaGetLastError();
+}
+
 template <typename S>
 cudaError_t launch_one(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs, cudaStream_t st) {
+    if (tn.variant == 3) {
+        if (tn.bx == 64) {
+            if (tn.depth >= 2) return launch_pipelined<S, 64, 2>(h, src, tn, acc, obs, st);
+            return launch_pipelined<S, 64, 1>(h, src, tn, acc, obs, st);
+        }
+        if (tn.depth >= 2) return launch_pipelined<S, 128, 2>(h, src, tn, acc, obs, st);
+        return launch_pipelined<S, 128, 1>(h, src, tn, acc, obs, st);
+    }
     if (tn.variant == 2) {
         if (tn.bx == 64) {
             if (tn.depth >= 2) return launch_staged<S, 64, 2>(h, src, tn, acc, obs, st);
@@ -317,13 +346,14 @@ std::vector<Tuned> candidates(const lbm_t* h) {
             out.push_back(t);
         }
     }
-    if ((req == 0 || req == 2) && h->maps_ok) {
+    for (int var : {2, 3}) {
+        if (!((req == 0 || req == var) && h->maps_ok)) continue;
         for (int bx : {64, 128}) {
             const int ncols = (h->p.nx + bx - 1) / bx;
             for (int depth : {1, 2}) {
                 for (int waves : {1, 2, 4}) {
                     Tuned t;
-                    t.variant = 2;
+                    t.variant = var;
                     t.bx = bx;
                     t.depth = depth;
                     const int resident = sms * (bx == 64 ? 6 : 3);
@@ -344,17 +374,20 @@ std::vector<Tuned> candidates(const lbm_t* h) {
     return u;
 }
 
-// GB300LBM_TUNE="staged,<cols per CTA>,<rows in flight>,<strips>" or
-// "simple,<rows per strip>" pins the launch configuration (no timing); used
-// to profile one configuration.
+// GB300LBM_TUNE="staged,<cols per CTA>,<rows in flight>,<strips>",
+// "pipelined,<cols>,<rows in flight>,<strips>" or "simple,<rows per strip>"
+// pins the launch configuration (no timing); used to profile one
+// configuration.
 bool tune_from_env(lbm_t* h) {
     const char* e = getenv("GB300LBM_TUNE");
     if (!e || !*e) return false;
     Tuned t;
     int a = 0, b = 0, c = 0;
-    if (sscanf(e, "staged,%d,%d,%d", &a, &b, &c) == 3 && (a == 64 || a == 128) && (b == 1 || b == 2) && c >= 1 &&
-        h->maps_ok) {
-        t.variant = 2;
+    int v = 0;
+    if (sscanf(e, "staged,%d,%d,%d", &a, &b, &c) == 3) v = 2;
+    else if (sscanf(e, "pipelined,%d,%d,%d", &a, &b, &c) == 3) v = 3;
+    if (v && (a == 64 || a == 128) && (b == 1 || b == 2) && c >= 1 && h->maps_ok) {
+        t.variant = v;
         t.bx = a;
         t.depth = b;
         t.strips = std::min(c, h->p.ny);
@@ -456,7 +489,7 @@ int validate(const lbm_params* p, const uint8_t* mask) {
     if (p->nx < 1 || p->ny < 1) return fail(nullptr, LBM_EINVAL, "nx, ny must be >= 1");
     if (elem_size(p->precision) == 0) return fail(nullptr, LBM_EINVAL, "unknown precision %d", p->precision);
     if (p->eq_order != 2 && p->eq_order != 3) return fail(nullptr, LBM_EINVAL, "eq_order must be 2 or 3");
-    if (p->variant < 0 || p->variant > 2) return fail(nullptr, LBM_EINVAL, "variant must be 0, 1 or 2");
+    if (p->variant < 0 || p->variant > 3) return fail(nullptr, LBM_EINVAL, "variant must be 0, 1, 2 or 3");
     for (int a = 0; a < 2; a++)
         if (!(p->tau[a] > 0.5) || !std::isfinite(p->tau[a]))
             return fail(nullptr, LBM_EINVAL, "tau[%d] must be finite and exceed 1/2", a);
@@ -650,7 +683,7 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
 #undef CREATE_TRY
     h->maps_ok = make_maps(h);
     h->cur = 0;
-    if (p->variant == 2 && !h->maps_ok) {
+    if (p->variant >= 2 && !h->maps_ok) {
         fail(nullptr, LBM_ECUDA, "tensor-map encoding failed: the staged kernel is unavailable");
         return bail(LBM_ECUDA);
     }
@@ -813,9 +846,9 @@ int lbm_load(lbm_t* h, const double* f) {
 int lbm_kernel_info(const lbm_t* h, int32_t info[4]) {
     if (!h || !info) return fail(nullptr, LBM_EINVAL, "NULL argument");
     info[0] = h->tune.variant;
-    info[1] = h->tune.variant == 2 ? h->tune.depth : 0;
+    info[1] = h->tune.variant >= 2 ? h->tune.depth : 0;
     info[2] = h->tune.variant == 1 ? h->tune.rpb : h->tune.bx;
-    info[3] = h->tune.variant == 2 ? h->tune.strips : 0;
+    info[3] = h->tune.variant >= 2 ? h->tune.strips : 0;
     return LBM_OK;
 }
 

@@ -96,6 +96,18 @@ def run_sweep(lbm, specs, g_lo, g_hi, precision="fp32", rel_bracket=0.02, t_eq=1
     return res, time.perf_counter() - t0
 
 
+def run_sweep_sharded(lbm, specs, g_lo, g_hi, **kw):
+    """The sweep split across ranks (one GPU each, round-robin shares, no
+    collective while stepping); results gathered back in order on every rank."""
+    from . import dist as D
+    world, rank, _ = D.env()
+    lo = np.broadcast_to(np.asarray(g_lo, dtype=np.float64), (len(specs),))
+    hi = np.broadcast_to(np.asarray(g_hi, dtype=np.float64), (len(specs),))
+    mine = D.shard(range(len(specs)), rank, world)
+    res, dt = run_sweep(lbm, [specs[k] for k in mine], lo[mine], hi[mine], **kw) if mine else ([], 0.0)
+    return D.gather(res, len(specs)), D.max_over_ranks(dt)
+
+
 def run_plain(lbm, specs, g_lo, g_hi, **kw):
     """The same bisection one instance at a time (the baseline)."""
     res, total = [], 0.0

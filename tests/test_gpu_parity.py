@@ -39,7 +39,7 @@ def lbm():
     return mod
 
 
-VARIANTS = ["simple", "staged"]
+VARIANTS = ["simple", "staged", "pipelined"]
 
 
 def gpu_run(lbm, mask, rho, steps, precision="fp32", variant="auto", **kw):
@@ -225,7 +225,8 @@ def test_set_body_force_and_save_load_roundtrip(lbm):
 
 
 @pytest.mark.parametrize("tune", ["staged,64,1,2", "staged,64,2,3", "staged,128,1,2", "staged,128,2,5",
-                                  "simple,7"])
+                                  "pipelined,64,1,2", "pipelined,64,2,3", "pipelined,128,1,2",
+                                  "pipelined,128,2,5", "simple,7"])
 @pytest.mark.parametrize("precision", ["fp32", "fp16s"])
 def test_every_launch_configuration(lbm, tune, precision, monkeypatch):
     """Each staged configuration (64 or 128 columns per CTA, 1 or 2 rows in
@@ -262,8 +263,9 @@ def test_variants_agree(lbm, precision, atol):
     for v in VARIANTS:
         f, obs, _ = gpu_run(lbm, mask, rho, 64 + 3, precision, v, **kw)
         outs.append((f, obs))
-    np.testing.assert_allclose(outs[0][0], outs[1][0], rtol=0, atol=atol)
-    np.testing.assert_allclose(outs[0][1]["mass"], outs[1][1]["mass"], rtol=1e-6)
+    for other in outs[1:]:
+        np.testing.assert_allclose(outs[0][0], other[0], rtol=0, atol=atol)
+        np.testing.assert_allclose(outs[0][1]["mass"], other[1]["mass"], rtol=1e-6)
 
 
 # ----------------------------------------------------------------------------
@@ -287,7 +289,7 @@ def test_shifted_16bit_storage_error(lbm, precision, bound):
 # ----------------------------------------------------------------------------
 # full size: 8192 x 1170 sinusoidal channel, the benchmark's launch shape
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("variant", ["auto", "simple", "staged"])
+@pytest.mark.parametrize("variant", ["auto", "simple", "staged", "pipelined"])
 def test_full_size_sampled_nodes(lbm, variant):
     """At the benchmark workload (8192 x 1170, FP32), one step from a state
     reached on the GPU is checked node by node on a sample: every node of
