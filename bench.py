@@ -39,7 +39,6 @@ BYTES_PER_POP = {"fp64": 8, "fp32": 4, "fp16s": 2, "bf16s": 2}
 DTYPE_NAME = {"fp64": "f64", "fp32": "f32", "fp16s": "f16-shifted storage, f32 math",
               "bf16s": "bf16-shifted storage, f32 math"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SRC = os.path.join(ROOT, "paper_1601_00918_gb300", "csrc", "lbm_step.cuh")
 
 
 def workload():
@@ -57,19 +56,29 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_hash():
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+KERNEL_FILES = {"simple": ("lbm_common.cuh", "lbm_step.cuh"),
+                "staged": ("lbm_common.cuh", "lbm_step_tma.cuh"),
+                "pipelined": ("lbm_common.cuh", "lbm_step_tma.cuh", "lbm_step_warp.cuh")}
 
 
-def recorded_traffic(precision, wname):
+def kernel_hash(variant):
+    """sha256 prefix of the sources that define the step kernel `variant`."""
+    h = hashlib.sha256()
+    for f in KERNEL_FILES[variant]:
+        with open(os.path.join(ROOT, "paper_1601_00918_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(precision, wname, kinfo):
     """DRAM bytes per step-kernel launch from a committed ncu capture, or None
-    when it was taken on another kernel source, precision or workload."""
+    unless it was taken on this workload, precision, launch shape and kernel
+    source."""
     try:
         with open(TRAFFIC_FILE) as fh:
             d = json.load(fh)
         e = d.get(f"{wname}/{precision}")
-        if e and e.get("kernel_sha") == kernel_hash():
+        if e and e.get("kernel_info") == kinfo and e.get("kernel_sha") == kernel_hash(kinfo["variant"]):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -262,7 +271,7 @@ def native_arm(args):
     per_launch_s = ms * 1e-3 / args.steps
     achieved = alg_bytes / per_launch_s / 1e9
     peak, peak_src = peaks()
-    traffic = recorded_traffic(prec, w.name)
+    traffic = recorded_traffic(prec, w.name, kinfo)
 
     # end to end through the C ABI with host buffers
     e2e = e2e_arm(args, w, prec, local, n_fluid) if rank == 0 else None
@@ -384,7 +393,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_POP))
-    ap.add_argument("--variant", default="auto", choices=["auto", "simple", "staged"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "simple", "staged", "pipelined"])
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

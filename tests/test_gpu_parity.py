@@ -250,14 +250,15 @@ def test_every_launch_configuration(lbm, tune, precision, monkeypatch):
     assert np.max(np.abs(rho_g - rho_r)) < (1e-5 if precision == "fp32" else 1e-3)
 
 
-@pytest.mark.parametrize("precision,atol", [("fp64", 1e-13), ("fp32", 5e-6), ("fp16s", 5e-4),
-                                             ("bf16s", 4e-3)])
-def test_variants_agree(lbm, precision, atol):
+@pytest.mark.parametrize("precision,atol,mass_rtol", [("fp64", 1e-13, 1e-12), ("fp32", 5e-6, 1e-6),
+                                                       ("fp16s", 5e-4, 1e-5), ("bf16s", 4e-3, 1e-4)])
+def test_variants_agree(lbm, precision, atol, mass_rtol):
     """The simple and the staged kernel perform the same arithmetic; the
     compiler may fuse multiply-adds differently in the two, so after 67 steps
     (two captured graphs plus three single launches) they agree to a few
     rounding units of the arithmetic (FP64, FP32) or of the storage (16-bit
-    formats, 2^-11 and 2^-8 of the stored non-equilibrium part)."""
+    formats, 2^-11 and 2^-8 of the stored non-equilibrium part); the masses
+    to the drift each format shows against the oracle."""
     mask, rho, kw = channel()
     outs = []
     for v in VARIANTS:
@@ -265,7 +266,7 @@ def test_variants_agree(lbm, precision, atol):
         outs.append((f, obs))
     for other in outs[1:]:
         np.testing.assert_allclose(outs[0][0], other[0], rtol=0, atol=atol)
-        np.testing.assert_allclose(outs[0][1]["mass"], other[1]["mass"], rtol=1e-6)
+        np.testing.assert_allclose(outs[0][1]["mass"], other[1]["mass"], rtol=mass_rtol)
 
 
 # ----------------------------------------------------------------------------
