@@ -30,7 +30,11 @@
 
 namespace gb300lbm {
 
-constexpr unsigned kWaitLimit = 1u << 20;   // try_wait polls before a wait gives up
+// A waiting thread is suspended for up to kSuspendNs per poll (it resumes as
+// soon as the phase completes), so waits do not burn issue slots; after
+// kWaitLimit polls (about 2.6 s) the wait gives up.
+constexpr unsigned kSuspendNs = 20000;
+constexpr unsigned kWaitLimit = 1u << 17;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -53,10 +57,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
