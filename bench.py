@@ -58,7 +58,8 @@ def peaks():
 
 KERNEL_FILES = {"simple": ("lbm_common.cuh", "lbm_step.cuh"),
                 "staged": ("lbm_common.cuh", "lbm_step_tma.cuh"),
-                "pipelined": ("lbm_common.cuh", "lbm_step_tma.cuh", "lbm_step_warp.cuh")}
+                "pipelined": ("lbm_common.cuh", "lbm_step_tma.cuh", "lbm_step_warp.cuh"),
+                "private": ("lbm_common.cuh", "lbm_step_tma.cuh", "lbm_step_private.cuh")}
 
 
 def kernel_hash(variant):
@@ -393,7 +394,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_POP))
-    ap.add_argument("--variant", default="auto", choices=["auto", "simple", "staged", "pipelined"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "simple", "staged", "pipelined", "private"])
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -71,7 +71,9 @@ typedef struct {
     int32_t eq_order;               /* 3 = Eq. (feq) as printed, 2 = without cubic terms */
     int32_t variant;                /* step kernel: 0 = autotuned, 1 = simple (register pull),
                                        2 = staged (TMA row pipeline, CTA barrier per row),
-                                       3 = pipelined (TMA rows, warps march independently);
+                                       3 = pipelined (TMA rows, warps march independently),
+                                       4 = private (each warp stages its own row windows,
+                                       densities exchanged by shuffles, no CTA barrier);
                                        results agree to rounding */
     int32_t reserved;               /* must be 0 */
     void *cuda_stream;              /* cudaStream_t for all work, or NULL = legacy default */
@@ -138,9 +140,9 @@ int lbm_save(lbm_t *h, double *f);
 int lbm_load(lbm_t *h, const double *f);
 
 /* Launch configuration the autotuner chose for the step kernel:
- * info[0] = variant (1 simple, 2 staged, 3 pipelined); info[1] = rows in
- * flight (2, 3); info[2] = rows per CTA strip (1) or columns per CTA (2, 3);
- * info[3] = strips per column block (2, 3).  Not part of the paper's
+ * info[0] = variant (1 simple, 2 staged, 3 pipelined, 4 private); info[1] =
+ * rows in flight (2..4); info[2] = rows per CTA strip (1) or columns per CTA
+ * (2..4); info[3] = strips per column block (2..4).  Not part of the paper's
  * method: a report of this library's tuning. */
 int lbm_kernel_info(const lbm_t *h, int32_t info[4]);
 

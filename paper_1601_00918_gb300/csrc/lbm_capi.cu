@@ -36,6 +36,7 @@
 #include "lbm_step.cuh"
 #include "lbm_step_tma.cuh"
 #include "lbm_step_warp.cuh"
+#include "lbm_step_private.cuh"
 #include "lbm_setup.cuh"
 
 using namespace gb300lbm;
@@ -47,7 +48,7 @@ constexpr int kRowBlock = 64;    // column granularity of the fluid-row table
 constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity is kept)
 
 struct Tuned {
-    int variant = 1;   // 1 simple, 2 staged, 3 pipelined
+    int variant = 1;   // 1 simple, 2 staged, 3 pipelined, 4 private
     int depth = 2;     // staged: rows in flight
     int rpb = 16;      // simple: rows per CTA strip
     int strips = 1;    // staged: strips per column block
@@ -79,6 +80,8 @@ struct lbm_t {
     cudaStream_t capture = nullptr;       // private stream for graph capture
     CUtensorMap fmap[2][2];       // [buffer][box width 64 + 16 or 128 + 16]
     CUtensorMap lmap[2];
+    CUtensorMap pmap[2];          // [buffer] per-warp windows of the private kernel
+    CUtensorMap plmap;
     bool maps_ok = false;
     Tuned tune;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -213,8 +216,35 @@ cudaError_t launch_pipelined(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, 
     return cudaGetLastError();
 }
 
+template <typename S, int BX, int D>
+cudaError_t launch_private(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs,
+                           cudaStream_t st) {
+    using Plan = PrivatePlan<S, BX / 32, D>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(step_private_kernel<S, BX, D>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Plan::kBytes);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    Grid g = make_grid(h, 0, h->p.ny);
+    g.strips = tn.strips;
+    dim3 grid((h->p.nx + BX - 1) / BX, tn.strips);
+    step_private_kernel<S, BX, D><<<grid, BX, Plan::kBytes, st>>>(
+        h->pmap[src], h->plmap, at_col0<S>(h->fbase[1 - src]), h->rows, h->dprm, acc, obs, g);
+    return cudaGetLastError();
+}
+
 template <typename S>
 cudaError_t launch_one(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs, cudaStream_t st) {
+    if (tn.variant == 4) {
+        if (tn.bx == 64) {
+            if (tn.depth >= 2) return launch_private<S, 64, 2>(h, src, tn, acc, obs, st);
+            return launch_private<S, 64, 1>(h, src, tn, acc, obs, st);
+        }
+        if (tn.depth >= 2) return launch_private<S, 128, 2>(h, src, tn, acc, obs, st);
+        return launch_private<S, 128, 1>(h, src, tn, acc, obs, st);
+    }
     if (tn.variant == 3) {
         if (tn.bx == 64) {
             if (tn.depth >= 2) return launch_pipelined<S, 64, 2>(h, src, tn, acc, obs, st);
@@ -317,6 +347,34 @@ bool make_maps(lbm_t* h) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
     }
+    // per-warp windows of the private kernel (PrivatePlan: the width depends
+    // on the element size only)
+    {
+        cuuint32_t W = 0;
+        switch (h->p.precision) {
+            case LBM_FP64: W = PrivatePlan<double, 1, 1>::kW; break;
+            case LBM_FP32: W = PrivatePlan<float, 1, 1>::kW; break;
+            default: W = PrivatePlan<__half, 1, 1>::kW; break;
+        }
+        for (int b = 0; b < 2; b++) {
+            cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)h->p.ny, np};
+            cuuint64_t strides[2] = {(cuuint64_t)h->pitch * h->elem, (cuuint64_t)h->p.ny * h->pitch * h->elem};
+            cuuint32_t box[3] = {W, 1, np};
+            cuuint32_t es[3] = {1, 1, 1};
+            if (fn(&h->pmap[b], dt, 3, h->fbase[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
+        }
+        cuuint64_t dims[2] = {(cuuint64_t)h->pitch, (cuuint64_t)h->p.ny};
+        cuuint64_t strides[1] = {(cuuint64_t)h->pitch * 2};
+        cuuint32_t box[2] = {(cuuint32_t)PrivatePlan<float, 1, 1>::kLW, 1};
+        cuuint32_t es[2] = {1, 1};
+        if (fn(&h->plmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h->links, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
     return true;
 }
 
@@ -346,7 +404,7 @@ std::vector<Tuned> candidates(const lbm_t* h) {
             out.push_back(t);
         }
     }
-    for (int var : {2, 3}) {
+    for (int var : {2, 3, 4}) {
         if (!((req == 0 || req == var) && h->maps_ok)) continue;
         for (int bx : {64, 128}) {
             const int ncols = (h->p.nx + bx - 1) / bx;
@@ -374,8 +432,8 @@ std::vector<Tuned> candidates(const lbm_t* h) {
     return u;
 }
 
-// GB300LBM_TUNE="staged,<cols per CTA>,<rows in flight>,<strips>",
-// "pipelined,<cols>,<rows in flight>,<strips>" or "simple,<rows per strip>"
+// GB300LBM_TUNE="staged,<cols per CTA>,<rows in flight>,<strips>" (likewise
+// "pipelined,..." and "private,...") or "simple,<rows per strip>"
 // pins the launch configuration (no timing); used to profile one
 // configuration.
 bool tune_from_env(lbm_t* h) {
@@ -386,6 +444,7 @@ bool tune_from_env(lbm_t* h) {
     int v = 0;
     if (sscanf(e, "staged,%d,%d,%d", &a, &b, &c) == 3) v = 2;
     else if (sscanf(e, "pipelined,%d,%d,%d", &a, &b, &c) == 3) v = 3;
+    else if (sscanf(e, "private,%d,%d,%d", &a, &b, &c) == 3) v = 4;
     if (v && (a == 64 || a == 128) && (b == 1 || b == 2) && c >= 1 && h->maps_ok) {
         t.variant = v;
         t.bx = a;
@@ -489,7 +548,7 @@ int validate(const lbm_params* p, const uint8_t* mask) {
     if (p->nx < 1 || p->ny < 1) return fail(nullptr, LBM_EINVAL, "nx, ny must be >= 1");
     if (elem_size(p->precision) == 0) return fail(nullptr, LBM_EINVAL, "unknown precision %d", p->precision);
     if (p->eq_order != 2 && p->eq_order != 3) return fail(nullptr, LBM_EINVAL, "eq_order must be 2 or 3");
-    if (p->variant < 0 || p->variant > 3) return fail(nullptr, LBM_EINVAL, "variant must be 0, 1, 2 or 3");
+    if (p->variant < 0 || p->variant > 4) return fail(nullptr, LBM_EINVAL, "variant must be 0, 1, 2, 3 or 4");
     for (int a = 0; a < 2; a++)
         if (!(p->tau[a] > 0.5) || !std::isfinite(p->tau[a]))
             return fail(nullptr, LBM_EINVAL, "tau[%d] must be finite and exceed 1/2", a);

@@ -169,15 +169,16 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
     auto slot = [&](int r) { return (r - y0 + 1) & 3; };
 
     bool timed_out = false;
-    int next_issue = 0;                             // used by thread 0 only
-    auto issue = [&](int j) {
+    int next_issue = 0;                             // thread 0 only: next stage to issue
+    int next_row = (y0 - 2) % ny;                   // thread 0 only: its row (stage j holds row y0 - 2 + j mod ny)
+    next_row = next_row < 0 ? next_row + ny : next_row;
+    auto issue = [&]() {
+        const int j = next_issue++;
         uint64_t* bar = &bars[j % NS];
-        // full modulo: with ny < 3 the stage rows y0 - 2 .. y1 + 1 wrap more than once
-        int row = (y0 - 2 + j) % ny;
-        row = row < 0 ? row + ny : row;
         mbar_expect_tx(bar, Plan::kTxBytes);
-        tma_load_3d((void*)pops(j), &fmap, x0, row, 0, bar);
-        tma_load_2d((void*)lnks(j), &lmap, x0, row, bar);
+        tma_load_3d((void*)pops(j), &fmap, x0, next_row, 0, bar);
+        tma_load_2d((void*)lnks(j), &lmap, x0, next_row, bar);
+        next_row = next_row + 1 == ny ? 0 : next_row + 1;
     };
     // after one wait gave up the data is invalid anyway: skip the others
     auto wait_stage = [&](int j) {
@@ -290,25 +291,25 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
     ObsLocal<R> ob;
     if (!empty) {
         if (t == 0) {
-            while (next_issue < NS && next_issue < n_stage) issue(next_issue++);
+            while (next_issue < NS && next_issue < n_stage) issue();
         }
-        R cur[2][9], nxt[2][9];
+        R fa[2][9], fb[2][9];
         R rc0 = R(0), rc1 = R(0), rn0 = R(0), rn1 = R(0);
-        bool solid_cur = true, solid_nxt = true;
+        bool sa = true, sb = true;
 
         // prologue: densities of rows y0 - 1 (stages 0,1,2) and y0 (1,2,3)
         wait_stage(0);
         wait_stage(1);
         wait_stage(2);
         if (rho_col) {
-            R tmp[2][9], a, b;
-            pull(0, 1, 2, wi, tmp, a, b);
+            R a, b;
+            pull(0, 1, 2, wi, fb, a, b);
             s_rho[slot(y0 - 1)][t + 1] = make_pair_of<R>(a, b);
         }
         halo(0, 1, 2, slot(y0 - 1));
         wait_stage(3);
         if (rho_col) {
-            solid_cur = pull(1, 2, 3, wi, cur, rc0, rc1);
+            sa = pull(1, 2, 3, wi, fa, rc0, rc1);
             s_rho[slot(y0)][t + 1] = make_pair_of<R>(rc0, rc1);
         }
         halo(1, 2, 3, slot(y0));
@@ -316,25 +317,27 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
         // that stage 4 (the first one the loop waits for) is on its way even
         // with a ring of only D + 3 = 4 slots
         __syncthreads();
-        if (t == 0) {
-            while (next_issue <= 1 + NS && next_issue < n_stage) issue(next_issue++);
+        if (t == 0 && !timed_out) {
+            while (next_issue <= 1 + NS && next_issue < n_stage) issue();
         }
 
-        for (int r = y0; r < y1; ++r) {
+        // row r: pull row r + 1 into nxt, then collide row r from cur (the
+        // loop below alternates the two arrays instead of copying them)
+        auto row_step = [&](int r, R(&cur)[2][9], R(&nxt)[2][9], bool s_cur, bool& s_nxt) {
             const int j = r - y0 + 2;                 // stages j, j+1, j+2 hold rows r, r+1, r+2
             const int sn = slot(r + 1);
             wait_stage(j + 2);
             if (rho_col) {
-                solid_nxt = pull(j, j + 1, j + 2, wi, nxt, rn0, rn1);
+                s_nxt = pull(j, j + 1, j + 2, wi, nxt, rn0, rn1);
                 s_rho[sn][t + 1] = make_pair_of<R>(rn0, rn1);
             }
             halo(j, j + 1, j + 2, sn);
             __syncthreads();
             // every stage <= j is now free: refill the ring
-            if (t == 0) {
-                while (next_issue <= j + NS && next_issue < n_stage) issue(next_issue++);
+            if (t == 0 && !timed_out) {
+                while (next_issue <= j + NS && next_issue < n_stage) issue();
             }
-            if (active && !solid_cur) {
+            if (active && !s_cur) {
                 const int s0 = slot(r), sm = slot(r - 1), sp = sn;
                 R nb[2][8];
                 {
@@ -354,14 +357,16 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
                 collide_store<S, R>(cur, rc0, rc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx,
                                     grid.periodic_x, ob);
             }
-#pragma unroll
-            for (int a = 0; a < 2; a++)
-#pragma unroll
-                for (int i = 0; i < 9; i++) cur[a][i] = nxt[a][i];
             rc0 = rn0;
             rc1 = rn1;
-            solid_cur = solid_nxt;
+        };
+
+        int r = y0;
+        for (; r + 1 < y1; r += 2) {
+            row_step(r, fa, fb, sa, sb);
+            row_step(r + 1, fb, fa, sb, sa);
         }
+        if (r < y1) row_step(r, fa, fb, sa, sb);
     }
     const bool any_timeout = __syncthreads_or(timed_out) != 0;
     if (any_timeout && t == 0) {

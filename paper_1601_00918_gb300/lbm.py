@@ -158,7 +158,7 @@ def _check(rc, handle=None):
     return rc
 
 
-VARIANTS = {"auto": 0, "simple": 1, "staged": 2, "pipelined": 3}
+VARIANTS = {"auto": 0, "simple": 1, "staged": 2, "pipelined": 3, "private": 4}
 
 
 def make_params(nx, ny, tau=(1.0, 1.0), G=0.0, rho_wall=(0.0, 0.0), g=(0.0, 0.0),
@@ -232,7 +232,7 @@ def lbm_kernel_info(h) -> dict:
     _check(library().lbm_kernel_info(h, info), h)
     if info[0] == 1:
         return {"variant": "simple", "rows_per_cta": info[2]}
-    return {"variant": {2: "staged", 3: "pipelined"}[info[0]], "depth": info[1], "cols_per_cta": info[2],
+    return {"variant": {2: "staged", 3: "pipelined", 4: "private"}[info[0]], "depth": info[1], "cols_per_cta": info[2],
             "strips": info[3]}
 
 

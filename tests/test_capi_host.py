@@ -69,7 +69,7 @@ def test_too_large_grid_rejected(lib):
     dict(eq_order=4),
     dict(precision=9),
     dict(periodic=(True, False)),            # open in y without solid rows
-    dict(variant=4),
+    dict(variant=5),
 ])
 def test_create_rejects_bad_parameters(lib, bad):
     kw = dict(nx=16, ny=8)

@@ -39,7 +39,7 @@ def lbm():
     return mod
 
 
-VARIANTS = ["simple", "staged", "pipelined"]
+VARIANTS = ["simple", "staged", "pipelined", "private"]
 
 
 def gpu_run(lbm, mask, rho, steps, precision="fp32", variant="auto", **kw):
@@ -226,7 +226,8 @@ def test_set_body_force_and_save_load_roundtrip(lbm):
 
 @pytest.mark.parametrize("tune", ["staged,64,1,2", "staged,64,2,3", "staged,128,1,2", "staged,128,2,5",
                                   "pipelined,64,1,2", "pipelined,64,2,3", "pipelined,128,1,2",
-                                  "pipelined,128,2,5", "simple,7"])
+                                  "pipelined,128,2,5", "private,64,1,2", "private,64,2,3",
+                                  "private,128,1,2", "private,128,2,5", "simple,7"])
 @pytest.mark.parametrize("precision", ["fp32", "fp16s"])
 def test_every_launch_configuration(lbm, tune, precision, monkeypatch):
     """Each staged configuration (64 or 128 columns per CTA, 1 or 2 rows in
@@ -290,7 +291,7 @@ def test_shifted_16bit_storage_error(lbm, precision, bound):
 # ----------------------------------------------------------------------------
 # full size: 8192 x 1170 sinusoidal channel, the benchmark's launch shape
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("variant", ["auto", "simple", "staged", "pipelined"])
+@pytest.mark.parametrize("variant", ["auto", "simple", "staged", "pipelined", "private"])
 def test_full_size_sampled_nodes(lbm, variant):
     """At the benchmark workload (8192 x 1170, FP32), one step from a state
     reached on the GPU is checked node by node on a sample: every node of
