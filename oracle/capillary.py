@@ -27,8 +27,13 @@ from the same balance:
     two contact chords plus the circular segments beyond them (positive
     where an arc bulges into the water);
   * the rest position s0 is a zero of the capillary balance with positive
-    slope; loading g quasi-statically moves the slug forward until the
-    balance reaches its first maximum, so g_crit = that maximum / (rho L).
+    slope; loading g quasi-statically moves the slug forward along the
+    branch where the balance equals rho g L / sigma; past a local maximum
+    the slug jumps ahead to the next position where the balance is as large
+    again.  The slug counts as moving once such a jump is longer than
+    lam / 2, or no such position exists within the period ahead (the same
+    "displacement > lam / 2" reading the bisection uses); g_crit is the
+    balance at that local maximum, / (rho L).
 The formulas here are evaluated by direct sampling (no root finder on the
 balance) so they can be read against the statements above.
 """
@@ -118,15 +123,18 @@ def front_for(xr: float, area: float, theta: float, h0: float, amp: float, lam: 
 
 
 def critical_force(theta: float, area: float, h0: float, amp: float, lam: float, x_rest: float,
-                   n: int = 721):
+                   n: int = 1441, jump: float | None = None):
     """2-D critical body force of a static slug, in units of sigma / (rho L).
 
-    The rear chord position s is sampled over x_rest -+ lam / 2; the rest
-    position s0 is the zero of the balance with positive slope nearest to
-    x_rest (the rear contact position of the slug at rest); g_crit sigma /
-    (rho L) is the first maximum of the balance after s0.  A balance that
-    vanishes everywhere (a straight channel) gives 0.  Returns (balance_max,
-    s0, s_at_max, samples (s, xf, balance))."""
+    The rear chord position s is sampled from x_rest - lam / 2 over two
+    wavelengths; the rest position s0 is the zero of the balance with
+    positive slope nearest to x_rest (the rear contact position of the slug
+    at rest).  From s0 the loading path climbs to each local maximum in turn
+    and jumps to the next sample ahead whose balance is at least as large;
+    the first jump longer than `jump` (default lam / 2), or one that leaves
+    the period ahead of s0, ends it: g_crit sigma / (rho L) is the balance
+    there.  A balance that vanishes everywhere (a straight channel) gives 0.
+    Returns (balance_crit, s0, s_at_crit, samples (s, xf, balance))."""
     span = area / (2.0 * max(h0 - amp, 1e-9)) + 2.0 * lam     # any slug fits in this window
     ss = x_rest + np.linspace(-0.5 * lam, 1.5 * lam, n)
     xf = np.array([front_for(s, area, theta, h0, amp, lam, span) for s in ss])
@@ -139,11 +147,18 @@ def critical_force(theta: float, area: float, h0: float, amp: float, lam: float,
         raise ValueError("no stable rest position within half a wavelength")
     zs = ss[up] - bal[up] * (ss[up + 1] - ss[up]) / (bal[up + 1] - bal[up])
     k = int(np.argmin(np.abs(zs - x_rest)))
-    i0, s0 = int(up[k]), float(zs[k])
-    j = i0 + 1
-    while j + 1 < n and bal[j + 1] >= bal[j]:
-        j += 1
-    return float(bal[j]), s0, float(ss[j]), (ss, xf, bal)
+    s0 = float(zs[k])
+    jump = 0.5 * lam if jump is None else jump
+    j = int(up[k]) + 1
+    while True:
+        while j + 1 < n and bal[j + 1] >= bal[j]:
+            j += 1
+        nxt = j + 1
+        while nxt < n and bal[nxt] < bal[j]:
+            nxt += 1
+        if nxt >= n or ss[nxt] - ss[j] > jump or ss[nxt] >= s0 + lam:
+            return float(bal[j]), s0, float(ss[j]), (ss, xf, bal)
+        j = nxt
 
 
 # ----------------------------------------------------------------------------

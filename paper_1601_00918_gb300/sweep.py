@@ -11,10 +11,13 @@ ratio A/h0, slug length / lambda, contact-angle parameter theta, viscosity
 ratio nu^o / nu^w; mean half-width h0 = 0.1875 lambda, n_periods periods.
 
 Readings (not fixed by the paper):
-* wettability: cos(theta) is mapped linearly onto the wall potentials,
-  rho_s^w = max(cos theta, 0) * RHO_S_MAX (water-wet) and
-  rho_s^o = max(-cos theta, 0) * RHO_S_MAX (oil-wet); the actual contact angle
-  of the model is not calibrated here;
+* wettability: with a calibration table (wetting.calibrate, the Section 3.3
+  flat-plate procedure run on the GPU) the wall potentials are the ones
+  whose measured contact angle is theta; without one, cos(theta) is mapped
+  linearly onto them, rho_s^w = max(cos theta, 0) * RHO_S_MAX (water-wet)
+  and rho_s^o = max(-cos theta, 0) * RHO_S_MAX (oil-wet);
+* starting bracket of the plain bisection: 0.5 to 2 times the planar 2-D
+  critical force of the slug (wetting.analytic_g_crit);
 * viscosity ratio r: tau^w = 1 and tau^o = 3 r nu^w + 1/2, clipped so that
   both relaxation times stay >= 0.85 (the plain BGK collision drives the
   minority density negative below ~0.8 with the interaction strength used);
@@ -51,11 +54,20 @@ def wall_potentials(theta_deg: float):
     return (max(-c, 0.0) * RHO_S_MAX, max(c, 0.0) * RHO_S_MAX)
 
 
-def instance_of(spec: wl.ChannelSpec) -> dict:
+def instance_of(spec: wl.ChannelSpec, table=None) -> dict:
+    """Batch instance of a channel spec; `table` (wetting.WettingTable) gives
+    calibrated wall potentials."""
     w = wl.channel_instance(spec)
+    rw = table.potentials_for(spec.theta_deg) if table is not None else wall_potentials(spec.theta_deg)
     return dict(mask=w.mask, rho_init=w.rho, tau=relaxation_times(spec.visc_ratio), G=G_INTERACTION,
-                rho_wall=wall_potentials(spec.theta_deg), g=(0.0, 0.0), periodic=w.periodic,
-                disp_threshold=0.5 * spec.lam)
+                rho_wall=rw, g=(0.0, 0.0), periodic=w.periodic, disp_threshold=0.5 * spec.lam)
+
+
+def analytic_brackets(specs, lo: float = 0.5, hi: float = 2.0):
+    """(lo, hi) times the planar 2-D critical force of each slug."""
+    from . import wetting
+    g = np.array([wetting.analytic_g_crit(s, s.theta_deg) for s in specs])
+    return lo * g, hi * g
 
 
 def features(spec: wl.ChannelSpec) -> np.ndarray:
@@ -81,9 +93,9 @@ def small_specs(n: int, seed: int, lambdas=(32, 48, 64)) -> list:
 
 
 def run_sweep(lbm, specs, g_lo, g_hi, precision="fp32", rel_bracket=0.02, t_eq=1000, t_obs=2000,
-              max_probes=24, check_bracket=True, timeout_s=0.0):
+              max_probes=24, check_bracket=True, timeout_s=0.0, table=None):
     """Batched bisection of every spec; returns (results, seconds)."""
-    insts = [instance_of(s) for s in specs]
+    insts = [instance_of(s, table) for s in specs]
     t0 = time.perf_counter()
     b = lbm.Batch(insts, precision=precision)
     try:
