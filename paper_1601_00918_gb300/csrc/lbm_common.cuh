@@ -257,6 +257,12 @@ __device__ __forceinline__ R wgt(int i) {
 
 __host__ __device__ __forceinline__ int weight_class(int i) { return i == 0 ? 0 : (i <= 4 ? 1 : 2); }
 
+// 1/x in the arithmetic type: FP64 divides; FP32 uses the hardware
+// approximate reciprocal (__fdividef, a few ulp, no special-case branch),
+// since densities and relaxation times are O(1).
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+
 // Per-thread observables of one step.
 template <typename R>
 struct ObsLocal {
@@ -294,11 +300,11 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
         jy[a] = (f[a][2] - f[a][4]) + (f[a][5] - f[a][7]) + (f[a][6] - f[a][8]);
     }
     const R rt = rho0 + rho1;
-    const R inv_rt = R(1) / rt;
+    const R inv_rt = recip(rt);
     const R ux = (jx[0] + jx[1]) * inv_rt;
     const R uy = (jy[0] + jy[1]) * inv_rt;
     const R nu_mix = (rho0 * P.nu0 + rho1 * P.nu1) * inv_rt;
-    const R om1 = R(1) - R(1) / (R(3) * nu_mix + R(0.5));   // 1 - 1/tau_mix
+    const R om1 = R(1) - recip(R(3) * nu_mix + R(0.5));   // 1 - 1/tau_mix
     R out[2][9];
     // f_i^eq(rho^a, u_mix) = rho^a e_i(u_mix) for both species: one evaluation
     R eu[9];

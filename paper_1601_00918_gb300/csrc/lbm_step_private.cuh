@@ -74,8 +74,10 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
     constexpr unsigned kSolid = 1u << kSolidBit;
     constexpr unsigned kAll = 0xffffffffu;
 
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte aligned start, found in the shared window itself: pointer
+    // arithmetic on the __shared__ array keeps every access a shared one
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
     unsigned char* wbase = smem + warp * Plan::kWarpBytes;
@@ -88,7 +90,6 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
     const int x0w = blockIdx.x * BX + warp * 32;
     const int gxc = x0w + lane;
     const bool active = gxc < nx;
-    const bool rho_col = gxc <= nx;                 // the lane at column nx pulls the image column
     const bool warp_live = x0w < nx;
     const bool need_right = x0w + 32 <= nx;         // lane 31 collides: column x0w + 32 is needed
 
@@ -256,10 +257,10 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
         wait_full(0);
         wait_full(1);
         wait_full(2);
-        if (rho_col) pull_rho(0, 1, 2, wi, li, rm0, rm1);
+        pull_rho(0, 1, 2, wi, li, rm0, rm1);
         if (halo_lane) pull_rho(0, 1, 2, hw, hl, hm0, hm1);
         wait_full(3);
-        if (rho_col) sa = pull(1, 2, 3, wi, li, fa, rc0, rc1);
+        sa = pull(1, 2, 3, wi, li, fa, rc0, rc1);
         if (halo_lane) pull_rho(1, 2, 3, hw, hl, hc0, hc1);
         // stages 0 and 1 are done: refill their slots
         __syncwarp();
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
             rn0 = rn1 = R(0);
             hn0 = hn1 = R(0);
             s_nxt = true;
-            if (rho_col) s_nxt = pull(j, j + 1, j + 2, wi, li, nxt, rn0, rn1);
+            s_nxt = pull(j, j + 1, j + 2, wi, li, nxt, rn0, rn1);
             if (halo_lane) pull_rho(j, j + 1, j + 2, hw, hl, hn0, hn1);
             // stage j (row r) is no longer read: lane 0 refills its slot
             __syncwarp();

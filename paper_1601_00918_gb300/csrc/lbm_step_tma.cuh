@@ -125,8 +125,10 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
     constexpr int NS = Plan::kStages;
     constexpr unsigned kSolid = 1u << kSolidBit;
 
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte aligned start, found in the shared window itself: pointer
+    // arithmetic on the __shared__ array keeps every access a shared one
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     uint64_t* bars = (uint64_t*)(smem + Plan::kBarOffset);
     pair_t<R>(*s_rho)[BX + 2] = (pair_t<R>(*)[BX + 2])(smem + Plan::kRhoOffset);
     auto pops = [&](int stage) { return (const S*)(smem + (stage % NS) * Plan::kSlot); };
@@ -163,14 +165,23 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
 
     const int gxc = x0 + t;
     const bool active = gxc < nx;
-    const bool rho_col = gxc <= nx;                 // thread nx - x0 pulls the image column nx
     const int wi = t + kGhost;                      // this thread's column in the staged window
 
-    auto slot = [&](int r) { return (r - y0 + 1) & 3; };
+    // Odd strips march upwards: a boundary between two strips is then
+    // reached by both of them at the same time (both start there or both
+    // end there), so its rows are read from DRAM once and from L2 the
+    // second time.  Stage j holds the row first + dir (j - 2); the density
+    // ring is indexed by the (unwrapped) row.
+    const int dir = (blockIdx.y & 1) ? -1 : 1;
+    const int first = dir > 0 ? y0 : y1 - 1;
+    auto slot = [&](int r) { return r & 3; };
+    // stages of the rows below (y - 1) and above (y + 1) the row of stage j + 1
+    auto below = [&](int j) { return dir > 0 ? j : j + 2; };
+    auto above = [&](int j) { return dir > 0 ? j + 2 : j; };
 
     bool timed_out = false;
     int next_issue = 0;                             // thread 0 only: next stage to issue
-    int next_row = (y0 - 2) % ny;                   // thread 0 only: its row (stage j holds row y0 - 2 + j mod ny)
+    int next_row = (first - 2 * dir) % ny;          // thread 0 only: the row of stage next_issue
     next_row = next_row < 0 ? next_row + ny : next_row;
     auto issue = [&]() {
         const int j = next_issue++;
@@ -178,7 +189,8 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
         mbar_expect_tx(bar, Plan::kTxBytes);
         tma_load_3d((void*)pops(j), &fmap, x0, next_row, 0, bar);
         tma_load_2d((void*)lnks(j), &lmap, x0, next_row, bar);
-        next_row = next_row + 1 == ny ? 0 : next_row + 1;
+        next_row += dir;
+        next_row = next_row == ny ? 0 : (next_row < 0 ? ny - 1 : next_row);
     };
     // after one wait gave up the data is invalid anyway: skip the others
     auto wait_stage = [&](int j) {
@@ -252,8 +264,10 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
     // Densities of the halo columns x0 - 1 (warp 0) and x0 + BX (warp 1),
     // lanes 0..8 species o, lanes 16..24 species w, from the staged window.
     auto halo = [&](int jm, int jc, int jp, int sl) {
-        if (warp >= 2) return;
-        const bool right = warp == 1;
+        // the last two warps: warp 0 also issues the row copies, so the
+        // extra work of a row is spread over three warps
+        if (warp < BX / 32 - 2) return;
+        const bool right = warp == BX / 32 - 1;
         if (right && x0 + BX > nx) return;          // image column pulled by a thread instead
         const int w = right ? BX + kGhost : kGhost - 1;
         const unsigned lk = lnks(jc)[w];
@@ -297,22 +311,22 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
         R rc0 = R(0), rc1 = R(0), rn0 = R(0), rn1 = R(0);
         bool sa = true, sb = true;
 
-        // prologue: densities of rows y0 - 1 (stages 0,1,2) and y0 (1,2,3)
+        // prologue: densities of the rows first - dir (stage 1) and first (stage 2)
         wait_stage(0);
         wait_stage(1);
         wait_stage(2);
-        if (rho_col) {
+        // every thread pulls (its window column always exists); densities of
+        // columns beyond nx are read only by threads that do not collide
+        {
             R a, b;
-            pull(0, 1, 2, wi, fb, a, b);
-            s_rho[slot(y0 - 1)][t + 1] = make_pair_of<R>(a, b);
+            pull(below(0), 1, above(0), wi, fb, a, b);
+            s_rho[slot(first - dir)][t + 1] = make_pair_of<R>(a, b);
         }
-        halo(0, 1, 2, slot(y0 - 1));
+        halo(below(0), 1, above(0), slot(first - dir));
         wait_stage(3);
-        if (rho_col) {
-            sa = pull(1, 2, 3, wi, fa, rc0, rc1);
-            s_rho[slot(y0)][t + 1] = make_pair_of<R>(rc0, rc1);
-        }
-        halo(1, 2, 3, slot(y0));
+        sa = pull(below(1), 2, above(1), wi, fa, rc0, rc1);
+        s_rho[slot(first)][t + 1] = make_pair_of<R>(rc0, rc1);
+        halo(below(1), 2, above(1), slot(first));
         // stages 0 and 1 are no longer needed: refill their slots now, so
         // that stage 4 (the first one the loop waits for) is on its way even
         // with a ring of only D + 3 = 4 slots
@@ -321,24 +335,24 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
             while (next_issue <= 1 + NS && next_issue < n_stage) issue();
         }
 
-        // row r: pull row r + 1 into nxt, then collide row r from cur (the
-        // loop below alternates the two arrays instead of copying them)
-        auto row_step = [&](int r, R(&cur)[2][9], R(&nxt)[2][9], bool s_cur, bool& s_nxt) {
-            const int j = r - y0 + 2;                 // stages j, j+1, j+2 hold rows r, r+1, r+2
-            const int sn = slot(r + 1);
+        // k-th row of the march, r = first + dir k: pull row r + dir into nxt,
+        // then collide row r from cur (the loop below alternates the two
+        // arrays instead of copying them)
+        auto row_step = [&](int k, R(&cur)[2][9], R(&nxt)[2][9], bool s_cur, bool& s_nxt) {
+            const int r = first + dir * k;
+            const int j = k + 2;                      // stages j, j+1, j+2 hold rows r, r+dir, r+2dir
+            const int sn = slot(r + dir);
             wait_stage(j + 2);
-            if (rho_col) {
-                s_nxt = pull(j, j + 1, j + 2, wi, nxt, rn0, rn1);
-                s_rho[sn][t + 1] = make_pair_of<R>(rn0, rn1);
-            }
-            halo(j, j + 1, j + 2, sn);
+            s_nxt = pull(below(j), j + 1, above(j), wi, nxt, rn0, rn1);
+            s_rho[sn][t + 1] = make_pair_of<R>(rn0, rn1);
+            halo(below(j), j + 1, above(j), sn);
             __syncthreads();
             // every stage <= j is now free: refill the ring
             if (t == 0 && !timed_out) {
                 while (next_issue <= j + NS && next_issue < n_stage) issue();
             }
             if (active && !s_cur) {
-                const int s0 = slot(r), sm = slot(r - 1), sp = sn;
+                const int s0 = slot(r), sm = slot(r - 1), sp = slot(r + 1);
                 R nb[2][8];
                 {
                     const pair_t<R> e = s_rho[s0][t + 2], n = s_rho[sp][t + 1], wv = s_rho[s0][t];
@@ -361,12 +375,13 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
             rc1 = rn1;
         };
 
-        int r = y0;
-        for (; r + 1 < y1; r += 2) {
-            row_step(r, fa, fb, sa, sb);
-            row_step(r + 1, fb, fa, sb, sa);
+        const int nk = y1 - y0;
+        int k = 0;
+        for (; k + 1 < nk; k += 2) {
+            row_step(k, fa, fb, sa, sb);
+            row_step(k + 1, fb, fa, sb, sa);
         }
-        if (r < y1) row_step(r, fa, fb, sa, sb);
+        if (k < nk) row_step(k, fa, fb, sa, sb);
     }
     const bool any_timeout = __syncthreads_or(timed_out) != 0;
     if (any_timeout && t == 0) {

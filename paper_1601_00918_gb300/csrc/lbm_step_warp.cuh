@@ -57,8 +57,10 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
     constexpr int NW = Plan::kWarps;
     constexpr unsigned kSolid = 1u << kSolidBit;
 
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // 128-byte aligned start, found in the shared window itself: pointer
+    // arithmetic on the __shared__ array keeps every access a shared one
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     uint64_t* full = (uint64_t*)(smem + Plan::kBarOffset);
     uint64_t* empty = full + NS;
     auto pops = [&](int stage) { return (const S*)(smem + (stage % NS) * Plan::kSlot); };
