@@ -78,8 +78,9 @@ struct lbm_t {
     StepParams hprm{};
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;       // private stream for graph capture
-    CUtensorMap fmap[2][2];       // [buffer][box width 64 + 16 or 128 + 16]
-    CUtensorMap lmap[2];
+    CUtensorMap fmap[2][2];       // [buffer][box width 64 + 16 or 128 + 16] (pipelined kernel)
+    CUtensorMap lmap[2];          // link words, box width 64 + 16 or 128 + 16
+    CUtensorMap smap[2][2];       // [buffer][64 or 128 columns] windows of the staged kernel
     CUtensorMap pmap[2];          // [buffer] per-warp windows of the private kernel
     CUtensorMap plmap;
     bool maps_ok = false;
@@ -191,7 +192,7 @@ cudaError_t launch_staged(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, Obs
     g.strips = tn.strips;
     dim3 grid((h->p.nx + BX - 1) / BX, tn.strips);
     step_staged_kernel<S, BX, D><<<grid, BX, Plan::kBytes, st>>>(
-        h->fmap[src][BX == 64 ? 0 : 1], h->lmap[BX == 64 ? 0 : 1], at_col0<S>(h->fbase[1 - src]), h->rows,
+        h->smap[src][BX == 64 ? 0 : 1], h->lmap[BX == 64 ? 0 : 1], at_col0<S>(h->fbase[1 - src]), h->rows,
         h->dprm, acc, obs, g);
     return cudaGetLastError();
 }
@@ -346,6 +347,25 @@ bool make_maps(lbm_t* h) {
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
+    }
+    // windows of the staged kernel (StagedPlan: block width + twice the lead)
+    for (int k = 0; k < 2; k++) {
+        cuuint32_t W = 0;
+        switch (h->p.precision) {
+            case LBM_FP64: W = k ? StagedPlan<double, 128, 1>::kW : StagedPlan<double, 64, 1>::kW; break;
+            case LBM_FP32: W = k ? StagedPlan<float, 128, 1>::kW : StagedPlan<float, 64, 1>::kW; break;
+            default: W = k ? StagedPlan<__half, 128, 1>::kW : StagedPlan<__half, 64, 1>::kW; break;
+        }
+        for (int b = 0; b < 2; b++) {
+            cuuint64_t dims[3] = {(cuuint64_t)h->pitch, (cuuint64_t)h->p.ny, np};
+            cuuint64_t strides[2] = {(cuuint64_t)h->pitch * h->elem, (cuuint64_t)h->p.ny * h->pitch * h->elem};
+            cuuint32_t box[3] = {W, 1, np};
+            cuuint32_t es[3] = {1, 1, 1};
+            if (fn(&h->smap[b][k], dt, 3, h->fbase[b], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
+        }
     }
     // per-warp windows of the private kernel (PrivatePlan: the width depends
     // on the element size only)

@@ -90,24 +90,32 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 }
 
 // Shared-memory plan of the staged kernel (host and device agree on it).
+// Pulls and halo densities reach two columns beyond each side of the block.
+// The population window starts kLead columns before it, so that its first
+// element is 16-byte aligned (4 columns for 4- and 8-byte types, 8 for the
+// 2-byte ones); the link window (2-byte words) starts 8 columns before.
 template <typename S, int BX, int D>
 struct StagedPlan {
-    static constexpr int kW = BX + 2 * kGhost;            // staged columns per row
+    static constexpr int kLead = sizeof(S) == 2 ? 8 : 4;
+    static constexpr int kW = BX + 2 * kLead;             // staged population columns per row
+    static constexpr int kLinkLead = 8;
+    static constexpr int kLW = BX + 2 * kLinkLead;        // staged link-word columns per row
     static constexpr int kStages = D + 3;                 // ring: rows r..r+2 in use + D ahead
     static constexpr int kPlanes = Codec<S>::kPlanes;        // 18, or 20 with the density planes
     static constexpr int kPopBytes = kPlanes * kW * (int)sizeof(S);
     static constexpr int kPopSlot = (kPopBytes + 127) / 128 * 128;
-    static constexpr int kLinkSlot = (kW * 2 + 127) / 128 * 128;
+    static constexpr int kLinkSlot = (kLW * 2 + 127) / 128 * 128;
     static constexpr int kSlot = kPopSlot + kLinkSlot;
     static constexpr int kRhoBytes = 4 * 2 * (BX + 2) * (int)sizeof(typename Codec<S>::R);
     static constexpr int kBarOffset = kStages * kSlot;
     static constexpr int kRhoOffset = kBarOffset + ((kStages * 8 + 127) / 128) * 128;
     static constexpr int kBytes = kRhoOffset + kRhoBytes + 128;   // + alignment slack
-    static constexpr uint32_t kTxBytes = (uint32_t)(kPopBytes + kW * 2);
+    static constexpr uint32_t kTxBytes = (uint32_t)(kPopBytes + kLW * 2);
 };
 
-// One time step fin -> fout.  fmap views fin as [planes][ny][pitch],
-// lmap views the link words as [ny][pitch]; fout points at logical column 0
+// One time step fin -> fout.  fmap views fin as [planes][ny][pitch] (box
+// {kW, 1, planes}), lmap views the link words as [ny][pitch] (box {kLW, 1});
+// fout points at logical column 0
 // of row 0.  rows64[k] = (first, last) row with fluid in columns
 // [64 k, 64 k + 64); a CTA of BX columns merges BX / 64 of them.
 template <typename S, int BX, int D>
@@ -165,7 +173,8 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
 
     const int gxc = x0 + t;
     const bool active = gxc < nx;
-    const int wi = t + kGhost;                      // this thread's column in the staged window
+    const int wi = t + Plan::kLead;                 // this thread's column in the population window
+    const int li = t + Plan::kLinkLead;             // ... and in the link window
 
     // Odd strips march upwards: a boundary between two strips is then
     // reached by both of them at the same time (both start there or both
@@ -187,8 +196,8 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
         const int j = next_issue++;
         uint64_t* bar = &bars[j % NS];
         mbar_expect_tx(bar, Plan::kTxBytes);
-        tma_load_3d((void*)pops(j), &fmap, x0, next_row, 0, bar);
-        tma_load_2d((void*)lnks(j), &lmap, x0, next_row, bar);
+        tma_load_3d((void*)pops(j), &fmap, x0 + kGhost - Plan::kLead, next_row, 0, bar);
+        tma_load_2d((void*)lnks(j), &lmap, x0 + kGhost - Plan::kLinkLead, next_row, bar);
         next_row += dir;
         next_row = next_row == ny ? 0 : (next_row < 0 ? ny - 1 : next_row);
     };
@@ -198,9 +207,10 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
     };
 
     // Pull the populations of the row held by stage jc (rows above/below in
-    // jm/jp) at window column w.  Returns true at a solid node.
-    auto pull = [&](int jm, int jc, int jp, int w, R(&f)[2][9], R& r0, R& r1) -> bool {
-        const unsigned lk = lnks(jc)[w];
+    // jm/jp) at population window column w / link window column lw.  Returns
+    // true at a solid node.
+    auto pull = [&](int jm, int jc, int jp, int w, int lw, R(&f)[2][9], R& r0, R& r1) -> bool {
+        const unsigned lk = lnks(jc)[lw];
         if (lk & kSolid) {
             r0 = P.rw0;
             r1 = P.rw1;
@@ -269,8 +279,8 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
         if (warp < BX / 32 - 2) return;
         const bool right = warp == BX / 32 - 1;
         if (right && x0 + BX > nx) return;          // image column pulled by a thread instead
-        const int w = right ? BX + kGhost : kGhost - 1;
-        const unsigned lk = lnks(jc)[w];
+        const int w = right ? BX + Plan::kLead : Plan::kLead - 1;
+        const unsigned lk = lnks(jc)[right ? BX + Plan::kLinkLead : Plan::kLinkLead - 1];
         const int sp = lane >> 4, i = lane & 15;
         R v = R(0);
         if (!(lk & kSolid) && i < 9) {
@@ -319,12 +329,12 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
         // columns beyond nx are read only by threads that do not collide
         {
             R a, b;
-            pull(below(0), 1, above(0), wi, fb, a, b);
+            pull(below(0), 1, above(0), wi, li, fb, a, b);
             s_rho[slot(first - dir)][t + 1] = make_pair_of<R>(a, b);
         }
         halo(below(0), 1, above(0), slot(first - dir));
         wait_stage(3);
-        sa = pull(below(1), 2, above(1), wi, fa, rc0, rc1);
+        sa = pull(below(1), 2, above(1), wi, li, fa, rc0, rc1);
         s_rho[slot(first)][t + 1] = make_pair_of<R>(rc0, rc1);
         halo(below(1), 2, above(1), slot(first));
         // stages 0 and 1 are no longer needed: refill their slots now, so
@@ -343,7 +353,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) s
             const int j = k + 2;                      // stages j, j+1, j+2 hold rows r, r+dir, r+2dir
             const int sn = slot(r + dir);
             wait_stage(j + 2);
-            s_nxt = pull(below(j), j + 1, above(j), wi, nxt, rn0, rn1);
+            s_nxt = pull(below(j), j + 1, above(j), wi, li, nxt, rn0, rn1);
             s_rho[sn][t + 1] = make_pair_of<R>(rn0, rn1);
             halo(below(j), j + 1, above(j), sn);
             __syncthreads();
