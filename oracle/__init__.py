@@ -41,7 +41,7 @@ class OracleParams(ctypes.Structure):
                 ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
                 ("tau", ctypes.c_double * 2), ("G", ctypes.c_double),
                 ("rho_wall", ctypes.c_double * 2), ("g", ctypes.c_double * 2),
-                ("eq_order", ctypes.c_int32)]
+                ("eq_order", ctypes.c_int32), ("collision", ctypes.c_int32)]
 
 
 _lib = None
@@ -81,17 +81,18 @@ class Problem:
 
     mask: uint8 [ny, nx], 1 = solid.  tau = (tau^o, tau^w); G the interaction
     strength of Eq. comp_interaction (repulsive for G < 0); rho_wall =
-    (rho_s^o, rho_s^w); g = body-force acceleration (gx, gy)."""
+    (rho_s^o, rho_s^w); g = body-force acceleration (gx, gy); collision =
+    "bgk" (f' = f - f^eq) or "regularized" (Eq. Regualize)."""
 
     def __init__(self, mask, tau=(1.0, 1.0), G=0.0, rho_wall=(0.0, 0.0), g=(0.0, 0.0),
-                 periodic=(True, True), eq_order=3):
+                 periodic=(True, True), eq_order=3, collision="bgk"):
         self.mask = np.ascontiguousarray(mask, dtype=np.uint8)
         ny, nx = self.mask.shape
         self.nx, self.ny = nx, ny
         self.p = OracleParams(nx, ny, int(periodic[0]), int(periodic[1]),
                               (ctypes.c_double * 2)(*tau), float(G),
                               (ctypes.c_double * 2)(*rho_wall), (ctypes.c_double * 2)(*g),
-                              int(eq_order))
+                              int(eq_order), {"bgk": 0, "regularized": 1}[collision])
         if _load().oracle_check(ctypes.byref(self.p), _ptr(self.mask, ctypes.c_uint8)) != 0:
             raise ValueError("mask breaks the boundary rule: a non-periodic direction needs "
                              "solid nodes on both of its boundary lines")

@@ -14,7 +14,8 @@
  *     read with the force carried by the equilibrium velocity shift
  *     Eq. (collision_term), so the separate F_i term is zero and the
  *     non-equilibrium part is f'_i = f_i - f_i^eq(rho, u_mix) (plain BGK,
- *     the regularised projection Eq. (Regualize) is not used);
+ *     collision = 0) or its regularised projection Eq. (Regualize) onto the
+ *     second-order Hermite polynomials (collision = 1);
  *   - the mixture relaxation time tau_mix = nu_mix/T0 + 1/2 with
  *     nu_mix = (rho^o nu^o + rho^w nu^w)/(rho^o + rho^w) and T0 = 1/3;
  *   - the third-order equilibrium Eq. (feq) (second order as an option);
@@ -53,6 +54,7 @@ typedef struct {
     double rho_wall[2]; /* rho_s^o, rho_s^w */
     double g[2];        /* body-force acceleration (x, y) */
     int32_t eq_order;   /* 3: Eq. (feq) as printed; 2: drop the cubic terms */
+    int32_t collision;  /* 0: f' = f - f^eq (BGK); 1: f' regularised, Eq. (Regualize) */
 } oracle_params;
 
 static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -78,6 +80,7 @@ static int is_solid(const oracle_params *p, const uint8_t *solid, int x, int y) 
 /* 0 when the mask obeys the boundary rule above, -1 otherwise. */
 int oracle_check(const oracle_params *p, const uint8_t *solid) {
     if (p->nx < 1 || p->ny < 1) return -1;
+    if (p->collision != 0 && p->collision != 1) return -1;
     if (!p->periodic_x)
         for (int y = 0; y < p->ny; y++)
             if (!solid[(size_t)y * p->nx] || !solid[(size_t)y * p->nx + p->nx - 1]) return -1;
@@ -172,13 +175,30 @@ static void collide_node(const oracle_params *p, const double fl[2][9], const do
     double nu_mix = (rho[0] * nu0 + rho[1] * nu1) / rt;
     double tau_mix = nu_mix / T0 + 0.5;
     for (int a = 0; a < 2; a++) {
-        double feq_u[9], feq_s[9];
-        /* f' = f - f^eq(rho^a, u_mix): non-equilibrium part, plain BGK */
+        double feq_u[9], feq_s[9], fneq[9];
+        /* f' = f - f^eq(rho^a, u_mix): the non-equilibrium part */
         oracle_feq(p->eq_order, rho[a], ux, uy, feq_u);
+        for (int i = 0; i < 9; i++) fneq[i] = fl[a][i] - feq_u[i];
+        if (p->collision == 1) {
+            /* Eq. (Regualize): keep only the part of f' that carries the
+             * non-equilibrium momentum flux Pi = sum_j c_j c_j f'_j, through
+             * the second-order Hermite polynomial Q_i = c_i c_i - T0 I:
+             * f'_i = w_i / (2 T0^2) Q_i : Pi */
+            double pxx = 0.0, pyy = 0.0, pxy = 0.0;
+            for (int j = 0; j < 9; j++) {
+                pxx += CX[j] * CX[j] * fneq[j];
+                pyy += CY[j] * CY[j] * fneq[j];
+                pxy += CX[j] * CY[j] * fneq[j];
+            }
+            for (int i = 0; i < 9; i++) {
+                double qxx = CX[i] * CX[i] - T0, qyy = CY[i] * CY[i] - T0, qxy = CX[i] * CY[i];
+                fneq[i] = W[i] / (2.0 * T0 * T0) * (qxx * pxx + qyy * pyy + 2.0 * qxy * pxy);
+            }
+        }
         /* Eq. (collision_term): equilibrium at the force-shifted velocity */
         oracle_feq(p->eq_order, rho[a], ux + acc[a][0], uy + acc[a][1], feq_s);
         for (int i = 0; i < 9; i++)
-            out[a][i] = feq_s[i] + (1.0 - 1.0 / tau_mix) * (fl[a][i] - feq_u[i]);
+            out[a][i] = feq_s[i] + (1.0 - 1.0 / tau_mix) * fneq[i];
     }
     if (mac) {
         mac[0] = rho[0];
