@@ -75,7 +75,10 @@ typedef struct {
                                        4 = private (each warp stages its own row windows,
                                        densities exchanged by shuffles, no CTA barrier);
                                        results agree to rounding */
-    int32_t reserved;               /* must be 0 */
+    int32_t collision;              /* non-equilibrium part f' of Eq. (LBM_BGK): 0 = f - f^eq
+                                       (plain BGK); 1 = regularised, Eq. (Regualize): the
+                                       second-order Hermite projection w_i Q_i : Pi / (2 T0^2)
+                                       of the non-equilibrium momentum flux Pi */
     void *cuda_stream;              /* cudaStream_t for all work, or NULL = legacy default */
     void *workspace;                /* optional device arena (>= lbm_workspace_size bytes,
                                        256-byte aligned), or NULL: the library allocates */
@@ -202,6 +205,7 @@ typedef struct {
     const uint8_t *mask;    /* host [ny][nx], 1 = solid (same rules as lbm_create) */
     const double *rho_init; /* host [2][ny][nx] initial densities */
     double disp_threshold;  /* oil displacement over one probe window that means "moving" */
+    int32_t collision;      /* as lbm_params.collision */
 } lbm_instance;
 
 /* Create n instances of uneven sizes that step together (one launch per step

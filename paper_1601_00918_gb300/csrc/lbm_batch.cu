@@ -298,6 +298,10 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
             delete b;
             return batch_fail(nullptr, LBM_EINVAL, "instance %d: bad size or NULL mask/rho_init", i);
         }
+        if (in.collision != 0 && in.collision != 1) {
+            delete b;
+            return batch_fail(nullptr, LBM_EINVAL, "instance %d: collision must be 0 or 1", i);
+        }
         for (int a = 0; a < 2; a++)
             if (!(in.tau[a] > 0.5)) {
                 delete b;
@@ -346,6 +350,7 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
         I.prm.g[0] = in.g[0];
         I.prm.g[1] = in.g[1];
         I.prm.k3 = eq_order >= 3 ? 4.5 : 0.0;
+        I.prm.reg = in.collision == 1 ? 1.0 : 0.0;
         I.disp_thr = in.disp_threshold;
         I.status = -1;
     }

@@ -569,6 +569,7 @@ int validate(const lbm_params* p, const uint8_t* mask) {
     if (elem_size(p->precision) == 0) return fail(nullptr, LBM_EINVAL, "unknown precision %d", p->precision);
     if (p->eq_order != 2 && p->eq_order != 3) return fail(nullptr, LBM_EINVAL, "eq_order must be 2 or 3");
     if (p->variant < 0 || p->variant > 4) return fail(nullptr, LBM_EINVAL, "variant must be 0, 1, 2, 3 or 4");
+    if (p->collision != 0 && p->collision != 1) return fail(nullptr, LBM_EINVAL, "collision must be 0 or 1");
     for (int a = 0; a < 2; a++)
         if (!(p->tau[a] > 0.5) || !std::isfinite(p->tau[a]))
             return fail(nullptr, LBM_EINVAL, "tau[%d] must be finite and exceed 1/2", a);
@@ -600,6 +601,7 @@ void fill_params(lbm_t* h) {
     }
     s.G = h->p.G;
     s.k3 = h->p.eq_order >= 3 ? 4.5 : 0.0;
+    s.reg = h->p.collision == 1 ? 1.0 : 0.0;
 }
 
 void drop_graphs(lbm_t* h) {
@@ -1021,6 +1023,7 @@ extern "C" int lbm_step_noalloc(const uint8_t* mask, const float* f_in, float* f
         return fail(nullptr, LBM_EINVAL, "lbm_step_noalloc: nx * ny must be in [1, %d] (got %d x %d)",
                     kNoAllocMaxNodes, p->nx, p->ny);
     if (p->eq_order != 2 && p->eq_order != 3) return fail(nullptr, LBM_EINVAL, "eq_order must be 2 or 3");
+    if (p->collision != 0 && p->collision != 1) return fail(nullptr, LBM_EINVAL, "collision must be 0 or 1");
     for (int a = 0; a < 2; a++)
         if (!(p->tau[a] > 0.5)) return fail(nullptr, LBM_EINVAL, "tau[%d] must exceed 1/2", a);
     int dev = 0;
@@ -1049,6 +1052,7 @@ extern "C" int lbm_step_noalloc(const uint8_t* mask, const float* f_in, float* f
     }
     prm.G = p->G;
     prm.k3 = p->eq_order >= 3 ? 4.5 : 0.0;
+    prm.reg = p->collision == 1 ? 1.0 : 0.0;
     noalloc_prepare_kernel<<<dim3((nx + 127) / 128, ny), 128, 0, st>>>(mask, scratch, nx, ny, prm);
     CUDA_TRY(nullptr, cudaGetLastError());
     Grid g;

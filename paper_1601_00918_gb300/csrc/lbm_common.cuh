@@ -29,6 +29,7 @@ struct StepParams {
     double g[2];
     double rho_wall[2];
     double k3;           // 4.5 with the cubic terms of Eq. (feq), 0 without
+    double reg;          // 1: regularised non-equilibrium part (Eq. Regualize), 0: plain BGK
 };
 
 // Per-step reduction targets; reset by the last CTA of each step.
@@ -163,36 +164,39 @@ struct Weights<float> {
     static __device__ __forceinline__ float w5() { return __int_as_float(0x3CE38E38); }  // 1/36 - 1 ulp
 };
 
-// Eq. (feq) with T0 = 1/3, written by parity of c_i.u:
-//   f_i^eq = w_i rho [E + O],  E = 1 - 1.5 u^2 + 4.5 (c.u)^2,
-//                              O = (c.u) (3 - k3 u^2 + k3 (c.u)^2),
-// k3 = 4.5 for the cubic equilibrium; opposite directions share E and flip O.
+// Explicitly rounded arithmetic: the compiler neither fuses nor reorders
+// these operations, so every kernel that runs the collision below performs
+// the same operations in the same order and produces the same bits.
+__device__ __forceinline__ float xadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float xsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// Eq. (feq) with T0 = 1/3 as a deviation from rest,
+//   f_i^eq(rho, u) = w_i rho (1 + D_i),  D_i = E_i + O_i,
+//   E_i = -1.5 u^2 + 4.5 (c_i.u)^2,  O_i = (c_i.u) (3 - k3 u^2 + k3 (c_i.u)^2),
+// k3 = 4.5 for the cubic equilibrium; opposite directions share E and flip
+// O.  Keeping the 1 out of D keeps the small part at full relative
+// precision in FP32 (the collision adds w_i rho last).
 template <typename R>
-__device__ __forceinline__ void equilibrium(R rho, R ux, R uy, R k3, R (&out)[9]) {
-    const R uu = ux * ux + uy * uy;
-    const R A = R(1) - R(1.5) * uu;
-    const R B = R(3) - k3 * uu;
-    const R w0 = rho * Weights<R>::w0(), w1 = rho * Weights<R>::w1(), w5 = rho * Weights<R>::w5();
-    out[0] = w0 * A;
-    {
-        const R c = ux, c2 = c * c, e = A + R(4.5) * c2, o = c * (B + k3 * c2);
-        out[1] = w1 * (e + o);
-        out[3] = w1 * (e - o);
-    }
-    {
-        const R c = uy, c2 = c * c, e = A + R(4.5) * c2, o = c * (B + k3 * c2);
-        out[2] = w1 * (e + o);
-        out[4] = w1 * (e - o);
-    }
-    {
-        const R c = ux + uy, c2 = c * c, e = A + R(4.5) * c2, o = c * (B + k3 * c2);
-        out[5] = w5 * (e + o);
-        out[7] = w5 * (e - o);
-    }
-    {
-        const R c = uy - ux, c2 = c * c, e = A + R(4.5) * c2, o = c * (B + k3 * c2);
-        out[6] = w5 * (e + o);
-        out[8] = w5 * (e - o);
+__device__ __forceinline__ void eq_deviation(R ux, R uy, R k3, R (&D)[9]) {
+    const R uu = xfma(ux, ux, xmul(uy, uy));
+    const R m = xmul(R(-1.5), uu);
+    const R B = xfma(-k3, uu, R(3));
+    D[0] = m;
+    const R cs[4] = {ux, uy, xadd(ux, uy), xsub(uy, ux)};
+    const int ip[4] = {1, 2, 5, 6}, im[4] = {3, 4, 7, 8};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const R c = cs[k], c2 = xmul(c, c);
+        const R e = xfma(R(4.5), c2, m);
+        const R o = xmul(c, xfma(k3, c2, B));
+        D[ip[k]] = xadd(e, o);
+        D[im[k]] = xsub(e, o);
     }
 }
 
@@ -237,7 +241,9 @@ __device__ __forceinline__ R warp_max(R v) {
 template <typename R>
 struct NodeParams {
     R G, gx, gy, rw0, rw1, nu0, nu1, k3;
+    bool reg;
     __device__ __forceinline__ void load(const StepParams* __restrict__ p) {
+        reg = p->reg != 0.0;
         G = R(p->G);
         gx = R(p->g[0]);
         gy = R(p->g[1]);
@@ -287,34 +293,36 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
     for (int b = 0; b < 2; b++) {
         const R e = nb[b][0], n = nb[b][1], wv = nb[b][2], so = nb[b][3];
         const R ne = nb[b][4], nw = nb[b][5], sw = nb[b][6], se = nb[b][7];
-        sx[b] = (e - wv) * R(1.0 / 9.0) + (ne - nw - sw + se) * R(1.0 / 36.0);
-        sy[b] = (n - so) * R(1.0 / 9.0) + (ne + nw - sw - se) * R(1.0 / 36.0);
+        sx[b] = xfma(xsub(e, wv), R(1.0 / 9.0), xmul(xadd(xsub(xsub(ne, nw), sw), se), R(1.0 / 36.0)));
+        sy[b] = xfma(xsub(n, so), R(1.0 / 9.0), xmul(xsub(xsub(xadd(ne, nw), sw), se), R(1.0 / 36.0)));
     }
-    const R ax0 = P.G * sx[1] + P.gx, ay0 = P.G * sy[1] + P.gy;   // species o feels rho^w
-    const R ax1 = P.G * sx[0] + P.gx, ay1 = P.G * sy[0] + P.gy;   // species w feels rho^o
+    const R ax0 = xfma(P.G, sx[1], P.gx), ay0 = xfma(P.G, sy[1], P.gy);   // species o feels rho^w
+    const R ax1 = xfma(P.G, sx[0], P.gx), ay1 = xfma(P.G, sy[0], P.gy);   // species w feels rho^o
 
     R jx[2], jy[2];
 #pragma unroll
     for (int a = 0; a < 2; a++) {
-        jx[a] = (f[a][1] - f[a][3]) + (f[a][5] - f[a][7]) + (f[a][8] - f[a][6]);
-        jy[a] = (f[a][2] - f[a][4]) + (f[a][5] - f[a][7]) + (f[a][6] - f[a][8]);
+        jx[a] = xadd(xadd(xsub(f[a][1], f[a][3]), xsub(f[a][5], f[a][7])), xsub(f[a][8], f[a][6]));
+        jy[a] = xadd(xadd(xsub(f[a][2], f[a][4]), xsub(f[a][5], f[a][7])), xsub(f[a][6], f[a][8]));
     }
-    const R rt = rho0 + rho1;
+    const R rt = xadd(rho0, rho1);
     const R inv_rt = recip(rt);
-    const R ux = (jx[0] + jx[1]) * inv_rt;
-    const R uy = (jy[0] + jy[1]) * inv_rt;
-    const R nu_mix = (rho0 * P.nu0 + rho1 * P.nu1) * inv_rt;
-    const R om1 = R(1) - recip(R(3) * nu_mix + R(0.5));   // 1 - 1/tau_mix
+    const R ux = xmul(xadd(jx[0], jx[1]), inv_rt);
+    const R uy = xmul(xadd(jy[0], jy[1]), inv_rt);
+    const R nu_mix = xmul(xfma(rho0, P.nu0, xmul(rho1, P.nu1)), inv_rt);
+    const R om1 = xsub(R(1), recip(xfma(R(3), nu_mix, R(0.5))));   // 1 - 1/tau_mix
     R out[2][9];
-    // f_i^eq(rho^a, u_mix) = rho^a e_i(u_mix) for both species: one evaluation
-    R eu[9];
-    equilibrium<R>(R(1), ux, uy, P.k3, eu);
+    // deviation of f^eq(rho^a, u_mix) from rest: the same for both species
+    R Du[9];
+    eq_deviation<R>(ux, uy, P.k3, Du);
 #pragma unroll
     for (int a = 0; a < 2; a++) {
         const R rho = a ? rho1 : rho0;
         const R ax = a ? ax1 : ax0, ay = a ? ay1 : ay0;
-        R fs[9];
-        equilibrium<R>(rho, ux + ax, uy + ay, P.k3, fs);
+        // Eq. (collision_term): equilibrium at the force-shifted velocity
+        R Ds[9];
+        eq_deviation<R>(xadd(ux, ax), xadd(uy, ay), P.k3, Ds);
+        const R wr[3] = {xmul(Weights<R>::w0(), rho), xmul(Weights<R>::w1(), rho), xmul(Weights<R>::w5(), rho)};
         S* d = dst + a * 9 * plane;
         R rh = R(0);
         if (C::kNodeShift) {
@@ -322,11 +330,49 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
             dst[(18 + a) * plane] = q;
             rh = C::rho_value(q);
         }
+        // non-equilibrium part f' = f - f^eq(rho^a, u_mix) = (f - w rho) - w rho D(u_mix)
+        R fn[9];
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            out[a][i] = fs[i] + om1 * (f[a][i] - rho * eu[i]);
-            d[i * plane] = C::encode(out[a][i], wgt<R>(i), rh);
+            const R w = wr[weight_class(i)];
+            fn[i] = xfma(-w, Du[i], xsub(f[a][i], w));
         }
+        if (P.reg) {
+            // Eq. (Regualize): f'_i = w_i / (2 T0^2) Q_i : Pi with Q_i = c_i c_i - T0 I
+            // and Pi = sum_j c_j c_j f'_j; on D2Q9 with T0 = 1/3 the
+            // coefficients reduce to the combinations below (f'_0 is not
+            // needed: the rest population is set by mass below)
+            const R diag = xadd(xadd(fn[5], fn[6]), xadd(fn[7], fn[8]));
+            const R pxx = xadd(xadd(fn[1], fn[3]), diag);
+            const R pyy = xadd(xadd(fn[2], fn[4]), diag);
+            const R pxy = xsub(xadd(fn[5], fn[7]), xadd(fn[6], fn[8]));
+            const R s = xadd(pxx, pyy);
+            const R e1 = xfma(R(1.0 / 3.0), pxx, xmul(R(-1.0 / 6.0), pyy));
+            const R e2 = xfma(R(1.0 / 3.0), pyy, xmul(R(-1.0 / 6.0), pxx));
+            const R dp = xfma(R(1.0 / 12.0), s, xmul(R(0.25), pxy));
+            const R dm = xfma(R(1.0 / 12.0), s, xmul(R(-0.25), pxy));
+            fn[1] = e1;
+            fn[3] = e1;
+            fn[2] = e2;
+            fn[4] = e2;
+            fn[5] = dp;
+            fn[7] = dp;
+            fn[6] = dm;
+            fn[8] = dm;
+        }
+        // f*_i = f_i^eq(rho, u_mix + F/rho) + (1 - 1/tau_mix) f'_i, Eq. (LBM_BGK),
+        // summed as w rho + (w rho D_s + om1 f'); the rest population takes
+        // what the others leave of rho (the f*_i of a node sum to rho exactly
+        // for both forms of f', so this is the same value, rounded once)
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            const R w = wr[weight_class(i)];
+            out[a][i] = xadd(w, xfma(w, Ds[i], xmul(om1, fn[i])));
+        }
+        out[a][0] = xsub(rho, xadd(xadd(xadd(out[a][1], out[a][3]), xadd(out[a][2], out[a][4])),
+                                   xadd(xadd(out[a][5], out[a][7]), xadd(out[a][6], out[a][8]))));
+#pragma unroll
+        for (int i = 0; i < 9; i++) d[i * plane] = C::encode(out[a][i], wgt<R>(i), rh);
     }
     // periodic ghost images of columns 0, 1, nx - 2, nx - 1 (ghost columns
     // -2, -1, nx, nx + 1 hold columns (nx - 2, nx - 1, 0, 1) mod nx)

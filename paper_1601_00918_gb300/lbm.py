@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
                 ("tau", ctypes.c_double * 2), ("G", ctypes.c_double),
                 ("rho_wall", ctypes.c_double * 2), ("g", ctypes.c_double * 2),
                 ("precision", ctypes.c_int32), ("eq_order", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("collision", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
@@ -68,7 +68,7 @@ class Instance(ctypes.Structure):
                 ("tau", ctypes.c_double * 2), ("G", ctypes.c_double),
                 ("rho_wall", ctypes.c_double * 2), ("g", ctypes.c_double * 2),
                 ("mask", ctypes.POINTER(ctypes.c_uint8)), ("rho_init", ctypes.POINTER(ctypes.c_double)),
-                ("disp_threshold", ctypes.c_double)]
+                ("disp_threshold", ctypes.c_double), ("collision", ctypes.c_int32)]
 
 
 class BisectOpts(ctypes.Structure):
@@ -159,16 +159,18 @@ def _check(rc, handle=None):
 
 
 VARIANTS = {"auto": 0, "simple": 1, "staged": 2, "pipelined": 3, "private": 4}
+COLLISIONS = {"bgk": 0, "regularized": 1}
 
 
 def make_params(nx, ny, tau=(1.0, 1.0), G=0.0, rho_wall=(0.0, 0.0), g=(0.0, 0.0),
                 periodic=(True, True), precision="fp32", eq_order=3, stream=None,
-                workspace=None, workspace_bytes=0, variant="auto") -> Params:
+                workspace=None, workspace_bytes=0, variant="auto", collision="bgk") -> Params:
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     var = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    col = COLLISIONS[collision] if isinstance(collision, str) else int(collision)
     return Params(int(nx), int(ny), int(periodic[0]), int(periodic[1]),
                   (ctypes.c_double * 2)(*tau), float(G), (ctypes.c_double * 2)(*rho_wall),
-                  (ctypes.c_double * 2)(*g), prec, int(eq_order), var, 0,
+                  (ctypes.c_double * 2)(*g), prec, int(eq_order), var, col,
                   ctypes.c_void_p(stream) if stream else None,
                   ctypes.c_void_p(workspace) if workspace else None, int(workspace_bytes))
 
@@ -250,7 +252,7 @@ class Simulation:
 
     def __init__(self, mask, rho_init, tau=(1.0, 1.0), G=0.0, rho_wall=(0.0, 0.0),
                  g=(0.0, 0.0), periodic=(True, True), precision="fp32", eq_order=3,
-                 device=0, use_torch_arena=True, variant="auto"):
+                 device=0, use_torch_arena=True, variant="auto", collision="bgk"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -260,7 +262,7 @@ class Simulation:
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream
             p = make_params(self.nx, self.ny, tau, G, rho_wall, g, periodic, precision, eq_order,
-                            stream=stream, variant=variant)
+                            stream=stream, variant=variant, collision=collision)
             self._arena = None
             if use_torch_arena:
                 nbytes = lbm_workspace_size(p)
@@ -318,7 +320,7 @@ def _bcheck(rc, b=None):
 
 def lbm_batch_create(instances, precision="fp32", eq_order=3, stream=None):
     """instances: list of dicts with mask [ny, nx], rho_init [2, ny, nx], tau, G,
-    rho_wall, g, periodic, disp_threshold."""
+    rho_wall, g, periodic, disp_threshold, collision ("bgk" or "regularized")."""
     keep = []
     arr = (Instance * len(instances))()
     for k, d in enumerate(instances):
@@ -332,7 +334,7 @@ def lbm_batch_create(instances, precision="fp32", eq_order=3, stream=None):
                           float(d.get("G", 0.0)), (ctypes.c_double * 2)(*d.get("rho_wall", (0.0, 0.0))),
                           (ctypes.c_double * 2)(*d.get("g", (0.0, 0.0))),
                           mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dptr(rho),
-                          float(d.get("disp_threshold", 0.0)))
+                          float(d.get("disp_threshold", 0.0)), COLLISIONS[d.get("collision", "bgk")])
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     h = ctypes.c_void_p()
     _bcheck(library().lbm_batch_create(arr, len(instances), prec, int(eq_order),

@@ -70,6 +70,7 @@ def test_too_large_grid_rejected(lib):
     dict(precision=9),
     dict(periodic=(True, False)),            # open in y without solid rows
     dict(variant=5),
+    dict(collision=2),
 ])
 def test_create_rejects_bad_parameters(lib, bad):
     kw = dict(nx=16, ny=8)

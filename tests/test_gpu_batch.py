@@ -68,6 +68,24 @@ def test_batch_steps_match_single_grids(lbm):
         np.testing.assert_allclose(o["oil_disp_x"], o_s["oil_disp_x"], rtol=1e-9, atol=1e-13)
 
 
+def test_batch_regularized_matches_oracle(lbm):
+    """Instances may use the regularised collision (Eq. Regualize), each its
+    own choice: a mixed batch stepped together matches the FP64 oracle."""
+    inst = uneven_instances()[:2]
+    inst[0]["collision"] = "regularized"
+    inst[0]["tau"] = (1.0, 0.65)
+    b = lbm.Batch(inst, precision="fp64")
+    try:
+        b.step(40)
+        got = [b.save(i) for i in range(len(inst))]
+    finally:
+        b.close()
+    for d, f_b in zip(inst, got):
+        P = oracle.Problem(d["mask"], tau=d["tau"], G=d["G"], rho_wall=d["rho_wall"], g=d["g"],
+                           periodic=d["periodic"], collision=d.get("collision", "bgk"))
+        np.testing.assert_allclose(f_b, P.run(P.init(d["rho_init"]), 40), rtol=0, atol=1e-12)
+
+
 def test_batch_steps_fp32_match_oracle(lbm):
     inst = uneven_instances()[:2]
     b = lbm.Batch(inst, precision="fp32")

@@ -254,12 +254,13 @@ def test_every_launch_configuration(lbm, tune, precision, monkeypatch):
 @pytest.mark.parametrize("precision,atol,mass_rtol", [("fp64", 1e-13, 1e-12), ("fp32", 5e-6, 1e-6),
                                                        ("fp16s", 5e-4, 1e-5), ("bf16s", 4e-3, 1e-4)])
 def test_variants_agree(lbm, precision, atol, mass_rtol):
-    """The simple and the staged kernel perform the same arithmetic; the
-    compiler may fuse multiply-adds differently in the two, so after 67 steps
-    (two captured graphs plus three single launches) they agree to a few
-    rounding units of the arithmetic (FP64, FP32) or of the storage (16-bit
-    formats, 2^-11 and 2^-8 of the stored non-equilibrium part); the masses
-    to the drift each format shows against the oracle."""
+    """All step kernels run the same explicitly rounded collision; they
+    differ only in the order in which the densities of the halo columns at a
+    block's edges are summed, so after 67 steps (two captured graphs plus
+    three single launches) they agree to a few rounding units of the
+    arithmetic (FP64, FP32) or of the storage (16-bit formats, 2^-11 and
+    2^-8 of the stored non-equilibrium part); the masses to the drift each
+    format shows against the oracle."""
     mask, rho, kw = channel()
     outs = []
     for v in VARIANTS:
@@ -327,3 +328,37 @@ def test_full_size_sampled_nodes(lbm, variant):
     ref = P.step_nodes(f0, xs, ys)                       # [k, 2, 9]
     got = f1[:, :, ys, xs].transpose(2, 0, 1)
     np.testing.assert_allclose(got, ref, rtol=0, atol=5e-6)
+
+
+# ----------------------------------------------------------------------------
+# Eq. (Regualize): regularised collision
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_fp64_regularized_channel_matches_oracle(lbm, variant):
+    """The regularised non-equilibrium part in every step kernel against the
+    oracle, on the channel at tau_w = 0.7 (where plain BGK loses positivity)."""
+    mask, rho, kw = channel(tau=(1.0, 0.7), rho_wall=(0.6, 0.05))
+    f_gpu, obs, (rho_g, u_g, _) = gpu_run(lbm, mask, rho, 100, "fp64", variant, collision="regularized", **kw)
+    P = oracle.Problem(mask, collision="regularized", **kw)
+    f_ref, hist = P.run(P.init(rho), 100, history=True)
+    np.testing.assert_allclose(f_gpu, f_ref, rtol=0, atol=1e-12)
+    rho_r, u_r, _ = P.fields(f_ref)
+    np.testing.assert_allclose(rho_g, rho_r, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(u_g, u_r, rtol=0, atol=1e-13)
+    assert obs["nan_flag"] == 0 and not hist[:, 4].any()
+
+
+def test_fp32_regularized_channel_1000_steps(lbm):
+    """FP32 with the regularised collision after 1000 steps: relative
+    L-infinity on density within 1e-5 and on velocity within 3e-5 (the FP32
+    floor of this arithmetic, as for BGK), masses to 1e-6."""
+    mask, rho, kw = channel(tau=(1.0, 0.7), rho_wall=(0.6, 0.05))
+    _, obs, (rho_g, u_g, _) = gpu_run(lbm, mask, rho, 1000, "fp32", collision="regularized", **kw)
+    P = oracle.Problem(mask, collision="regularized", **kw)
+    f_ref, hist = P.run(P.init(rho), 1000, history=True)
+    rho_r, u_r, _ = P.fields(f_ref)
+    fluid = mask == 0
+    assert np.max(np.abs(rho_g - rho_r)[:, fluid]) / np.max(rho_r[:, fluid]) < 1e-5
+    assert np.max(np.abs(u_g - u_r)[:, fluid]) / np.max(np.abs(u_r[:, fluid])) < 3e-5
+    np.testing.assert_allclose(obs["mass"], hist[-1, :2], rtol=1e-6)
+
