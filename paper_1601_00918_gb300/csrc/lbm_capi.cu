@@ -411,6 +411,37 @@ int sms_of_device() {
     return n > 0 ? n : 152;
 }
 
+// Resident CTAs per SM of one launch configuration (0 if it cannot launch).
+template <typename K>
+int occupancy_of(K kernel, int threads, int smem) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+template <typename S, int BX, int D>
+int occupancy_tma(int var) {
+    if (var == 2) return occupancy_of(step_staged_kernel<S, BX, D>, BX, StagedPlan<S, BX, D>::kBytes);
+    if (var == 3) return occupancy_of(step_warp_kernel<S, BX, D>, BX, WarpPlan<S, BX, D>::kBytes);
+    return occupancy_of(step_private_kernel<S, BX, D>, BX, PrivatePlan<S, BX / 32, D>::kBytes);
+}
+
+template <typename S>
+int occupancy_prec(int var, int bx, int depth) {
+    if (bx == 64) return depth >= 2 ? occupancy_tma<S, 64, 2>(var) : occupancy_tma<S, 64, 1>(var);
+    return depth >= 2 ? occupancy_tma<S, 128, 2>(var) : occupancy_tma<S, 128, 1>(var);
+}
+
+int occupancy(const lbm_t* h, int var, int bx, int depth) {
+    switch (h->p.precision) {
+        case LBM_FP64: return occupancy_prec<double>(var, bx, depth);
+        case LBM_FP32: return occupancy_prec<float>(var, bx, depth);
+        case LBM_FP16S: return occupancy_prec<__half>(var, bx, depth);
+        default: return occupancy_prec<__nv_bfloat16>(var, bx, depth);
+    }
+}
+
 std::vector<Tuned> candidates(const lbm_t* h) {
     std::vector<Tuned> out;
     const int sms = sms_of_device();
@@ -429,12 +460,15 @@ std::vector<Tuned> candidates(const lbm_t* h) {
         for (int bx : {64, 128}) {
             const int ncols = (h->p.nx + bx - 1) / bx;
             for (int depth : {1, 2}) {
-                for (int waves : {1, 2, 4}) {
+                // strips for 1 to 4 full waves of the CTAs this configuration keeps resident
+                const int per_sm = occupancy(h, var, bx, depth);
+                if (per_sm < 1) continue;
+                for (int waves : {1, 2, 3, 4}) {
                     Tuned t;
                     t.variant = var;
                     t.bx = bx;
                     t.depth = depth;
-                    const int resident = sms * (bx == 64 ? 6 : 3);
+                    const int resident = sms * per_sm;
                     t.strips = std::max(1, std::min(ny, waves * resident / std::max(1, ncols)));
                     out.push_back(t);
                 }

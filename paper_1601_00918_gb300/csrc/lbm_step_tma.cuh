@@ -119,7 +119,10 @@ struct StagedPlan {
 // of row 0.  rows64[k] = (first, last) row with fluid in columns
 // [64 k, 64 k + 64); a CTA of BX columns merges BX / 64 of them.
 template <typename S, int BX, int D>
-__global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4)) step_staged_kernel(const __grid_constant__ CUtensorMap fmap,
+// FP32 at 128 columns and one row ahead fits five CTAs per SM (96 registers
+// without spills, 45.4 KB of shared memory each); the others four (or two).
+__global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((sizeof(S) == 4 && D == 1) ? 5 : 4)))
+    step_staged_kernel(const __grid_constant__ CUtensorMap fmap,
                                                          const __grid_constant__ CUtensorMap lmap,
                                                          S* __restrict__ fout,
                                                          const int2* __restrict__ rows64,
