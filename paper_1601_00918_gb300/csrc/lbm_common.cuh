@@ -164,17 +164,19 @@ struct Weights<float> {
     static __device__ __forceinline__ float w5() { return __int_as_float(0x3CE38E38); }  // 1/36 - 1 ulp
 };
 
-// Explicitly rounded arithmetic: the compiler neither fuses nor reorders
-// these operations, so every kernel that runs the collision below performs
-// the same operations in the same order and produces the same bits.
+// Explicitly rounded FP32 arithmetic: the compiler neither fuses nor
+// reorders these operations, so every kernel that runs the collision below
+// performs the same operations in the same order and produces the same
+// bits.  FP64 leaves the compiler free to fuse (its rounding is far below
+// any tolerance, and the FP64 pipe is the bottleneck there).
 __device__ __forceinline__ float xadd(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double xadd(double a, double b) { return a + b; }
 __device__ __forceinline__ float xsub(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double xsub(double a, double b) { return a - b; }
 __device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double xmul(double a, double b) { return a * b; }
 __device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return fma(a, b, c); }
 
 // Eq. (feq) with T0 = 1/3 as a deviation from rest,
 //   f_i^eq(rho, u) = w_i rho (1 + D_i),  D_i = E_i + O_i,
