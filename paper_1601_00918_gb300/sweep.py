@@ -27,6 +27,10 @@ Readings (not fixed by the paper):
 * "moving": the oil centre of mass travels more than lambda / 2 within one
   probe window.
 
+The paper's own protocol, a continuous ramp of g without restarts
+(ramp_critical), is here too; the bisection replaces it in the sweeps
+because it needs far fewer steps per solve.
+
 Surrogate features (all O(1)): amplitude ratio, slug length / lambda,
 cos(theta), log(viscosity ratio), 1 / resolution with the resolution the
 neck width 2 (h0 - A) in nodes.  Target: log g_crit, g_crit the geometric
@@ -123,6 +127,43 @@ def run_sweep_sharded(lbm, specs, g_lo, g_hi, **kw):
     mine = D.shard(range(len(specs)), rank, world)
     res, dt = run_sweep(lbm, [specs[k] for k in mine], lo[mine], hi[mine], **kw) if mine else ([], 0.0)
     return D.gather(res, len(specs)), D.max_over_ranks(dt)
+
+
+def ramp_critical(lbm, specs, g_start, ratio: float = 1.05, n_levels: int = 40, t_eq: int = 2000,
+                  t_level: int = 8000, precision: str = "fp32", table=None):
+    """The paper's own protocol (Section 3.4): after t_eq steps at g = 0, g
+    is raised level by level without restarting (level k of instance i is
+    g_start[i] ratio^k, t_level steps each), and a slug counts as moving at
+    the first level in which its oil centre of mass travels more than
+    lambda / 2.  Unlike the bisection, the slug carries its displacement
+    from level to level, as in the paper's ramp.  All instances step
+    together as one batch.  Returns (list of (g_static, g_moving) with the
+    last static and the first moving level, None where no level moved the
+    slug; seconds)."""
+    insts = [instance_of(s, table) for s in specs]
+    n = len(specs)
+    g0 = np.broadcast_to(np.asarray(g_start, dtype=np.float64), (n,)).copy()
+    thr = np.array([0.5 * s.lam for s in specs])
+    t0 = time.perf_counter()
+    b = lbm.Batch(insts, precision=precision)
+    out = [None] * n
+    try:
+        b.step(t_eq)
+        prev = np.array([o["oil_disp_x"] for o in b.observables(check=False)])
+        for k in range(n_levels):
+            g = g0 * ratio ** k
+            b.set_body_force(g)
+            b.step(t_level)
+            disp = np.array([o["oil_disp_x"] for o in b.observables(check=False)])
+            for i in range(n):
+                if out[i] is None and abs(disp[i] - prev[i]) > thr[i]:
+                    out[i] = (g[i] / ratio if k > 0 else 0.0, g[i])
+            prev = disp
+            if all(o is not None for o in out):
+                break
+    finally:
+        b.close()
+    return out, time.perf_counter() - t0
 
 
 def run_plain(lbm, specs, g_lo, g_hi, **kw):

@@ -67,3 +67,26 @@ def test_surrogate_seeded_brackets_save_probes(lbm):
     for k in both:
         a, b = res_s[k], res_w[k]
         assert a["g_lo"] <= b["g_hi"] * 1.0001 and b["g_lo"] <= a["g_hi"] * 1.0001, (k, a, b)
+
+
+def test_ramp_protocol_agrees_with_the_bisection(lbm):
+    """The paper's ramp (g raised by 5 % per 8000-step level without
+    restarting, Section 3.4) against the restart-per-probe bisection with the
+    same window, on eight channels stepped together: every channel moves in
+    both, and the two critical forces agree within a factor 1.5.  They are
+    not the same measurement: in the ramp the slug creeps towards its
+    critical position over the lower levels, while a restarted probe must
+    travel lambda / 2 from rest within one window, so with windows this short
+    the ramp usually moves the slug at a lower force (measured ratios 0.69 to
+    1.31, median 0.75)."""
+    specs = sweep.small_specs(8, seed=5)
+    lo, hi = sweep.analytic_brackets(specs)
+    kw = dict(t_eq=2000, t_obs=8000, rel_bracket=0.02, max_probes=24)
+    res, _ = sweep.run_sweep(lbm, specs, lo, hi, **kw)
+    ramp, _ = sweep.ramp_critical(lbm, specs, 0.4 * lo, ratio=1.05, n_levels=90, t_eq=2000, t_level=8000)
+    ratios = []
+    for r, rp in zip(res, ramp):
+        assert r["status"] == 0 and rp is not None, (r, rp)
+        assert rp[1] / rp[0] == pytest.approx(1.05) or rp[0] == 0.0
+        ratios.append(np.sqrt(rp[0] * rp[1]) / np.sqrt(r["g_lo"] * r["g_hi"]))
+    assert min(ratios) > 1.0 / 1.5 and max(ratios) < 1.5, ratios
