@@ -324,6 +324,13 @@ def critical_pressure_arm(args):
     lo_a, hi_a = sweep.analytic_brackets(specs)
     res_b, t_b = sweep.run_sweep(lbm, specs, lo_a, hi_a, table=table, **kw)
     ok_b = sum(r["status"] == 0 for r in res_b)
+    # the same batched sweep with FP16-shifted populations (FP32 arithmetic,
+    # FP64 decisions): solves/hour and whether the brackets move
+    res_h, t_h = sweep.run_sweep(lbm, specs, lo_a, hi_a, table=table, precision="fp16s", **kw)
+    ok_h = sum(r["status"] == 0 for r in res_h)
+    both_h = [(a, b) for a, b in zip(res_h, res_b) if a["status"] == 0 and b["status"] == 0]
+    over_h = sum(1 for a, b in both_h if a["g_lo"] <= b["g_hi"] * 1.0001 and b["g_lo"] <= a["g_hi"] * 1.0001)
+    dev_h = [abs(math.log(math.sqrt(a["g_lo"] * a["g_hi"]) / math.sqrt(b["g_lo"] * b["g_hi"]))) for a, b in both_h]
     n_p = min(args.sweep_plain, len(specs))
     res_p, t_p = sweep.run_plain(lbm, specs[:n_p], lo_a[:n_p], hi_a[:n_p], table=table, **kw)
     ok_p = sum(r["status"] == 0 for r in res_p)
@@ -355,6 +362,9 @@ def critical_pressure_arm(args):
             "lbm_over_analytic_median": float(np.median(g_b / g_a)) if g_b.size else None,
             "batched": {"solved": ok_b, "seconds": t_b, "solves_per_hour": 3600.0 * ok_b / t_b,
                         "mean_probes": float(np.mean([r["probes"] for r in res_b]))},
+            "batched_fp16s": {"solved": ok_h, "seconds": t_h, "solves_per_hour": 3600.0 * ok_h / t_h,
+                              "brackets_overlapping_fp32": f"{over_h}/{len(both_h)}",
+                              "max_relative_shift": float(math.expm1(max(dev_h))) if dev_h else None},
             "plain_one_at_a_time": {"instances": n_p, "solved": ok_p, "seconds": t_p,
                                     "solves_per_hour": 3600.0 * ok_p / t_p,
                                     "mean_probes": float(np.mean([r["probes"] for r in res_p]))},
