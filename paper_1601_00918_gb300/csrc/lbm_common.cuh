@@ -380,7 +380,9 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
     // -2, -1, nx, nx + 1 hold columns (nx - 2, nx - 1, 0, 1) mod nx)
     if (periodic && (x < 2 || x >= nx - 2)) {
         const int gcols[4] = {-2, -1, nx, nx + 1};
-#pragma unroll
+        // not unrolled: only four columns of the grid run this, and one copy
+        // of the 18 stores keeps the step kernels' code small
+#pragma unroll 1
         for (int k = 0; k < 4; k++) {
             int m = gcols[k] % nx;
             if (m < 0) m += nx;

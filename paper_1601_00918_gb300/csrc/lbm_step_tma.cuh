@@ -349,8 +349,9 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((siz
         }
 
         // k-th row of the march, r = first + dir k: pull row r + dir into nxt,
-        // then collide row r from cur (the loop below alternates the two
-        // arrays instead of copying them)
+        // then collide row r from cur.  The loop below is not unrolled: the
+        // copy of nxt into cur costs less than the instruction-cache misses
+        // of a loop body twice the size, with five CTAs per SM.
         auto row_step = [&](int k, R(&cur)[2][9], R(&nxt)[2][9], bool s_cur, bool& s_nxt) {
             const int r = first + dir * k;
             const int j = k + 2;                      // stages j, j+1, j+2 hold rows r, r+dir, r+2dir
@@ -390,11 +391,15 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((siz
 
         const int nk = y1 - y0;
         int k = 0;
-        for (; k + 1 < nk; k += 2) {
+#pragma unroll 1
+        for (; k < nk; ++k) {
             row_step(k, fa, fb, sa, sb);
-            row_step(k + 1, fb, fa, sb, sa);
+#pragma unroll
+            for (int a = 0; a < 2; a++)
+#pragma unroll
+                for (int i = 0; i < 9; i++) fa[a][i] = fb[a][i];
+            sa = sb;
         }
-        if (k < nk) row_step(k, fa, fb, sa, sb);
     }
     const bool any_timeout = __syncthreads_or(timed_out) != 0;
     if (any_timeout && t == 0) {
