@@ -149,6 +149,18 @@ int lbm_load(lbm_t *h, const double *f);
  * method: a report of this library's tuning. */
 int lbm_kernel_info(const lbm_t *h, int32_t info[4]);
 
+/* Self-test of the device-side wait limit.  Every wait of the step kernels
+ * (for a row copy to land, for a ring slot) is bounded: after about 0.5 s
+ * (measured on GB300) the kernel gives up, marks the step (LBM_ETIMEOUT from lbm_observables)
+ * and returns, so a lost copy cannot hang the GPU.  This call runs that same
+ * bounded wait on a barrier that nothing ever completes, on cuda_stream
+ * (NULL = legacy default), and returns LBM_ETIMEOUT when the wait gave up as
+ * it must (any other status is a failure); *seconds (may be NULL) receives
+ * how long the wait took.  The CUDA context stays usable afterwards.
+ * Allocates 4 bytes of device memory for the duration of the call.  Not part
+ * of the paper's method: a check of this library's failure handling. */
+int lbm_wait_selftest(void *cuda_stream, double *seconds);
+
 /* One FP32 time step that allocates nothing, for callers that cannot call
  * cudaMalloc: code running while a CUDA graph is being captured, real-time
  * loops that must not allocate, plug-ins whose device memory belongs to a

@@ -671,6 +671,16 @@ int build_graph(lbm_t* h, int src) {
 
 }  // namespace
 
+// Wait self-test: one thread waits, through the same bounded mbarrier wait
+// the step kernels use, on a barrier that nothing ever arrives at, and
+// records whether the wait gave up (it must).
+__global__ void wait_selftest_kernel(int* out) {
+    __shared__ __align__(8) uint64_t bar;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    out[0] = mbar_wait(&bar, 0u) ? 0 : 1;
+}
+
 extern "C" {
 
 int lbm_workspace_size(const lbm_params* p, size_t* bytes) {
@@ -978,6 +988,31 @@ void lbm_destroy(lbm_t* h) {
 }
 
 const char* lbm_last_error(const lbm_t* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int lbm_wait_selftest(void* cuda_stream, double* seconds) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int* d = nullptr;
+    CUDA_TRY(nullptr, cudaMalloc(&d, sizeof(int)));
+    int flag = -1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    wait_selftest_kernel<<<1, 1, 0, st>>>(d);
+    cudaError_t e = cudaGetLastError();
+    cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ECUDA, "wait self-test: %s", cudaGetErrorString(e));
+    if (seconds) *seconds = ms * 1e-3;
+    if (flag == 1) return fail(nullptr, LBM_ETIMEOUT, "wait self-test: the bounded wait gave up (as it should)");
+    return fail(nullptr, LBM_ECUDA, "wait self-test: a wait on a barrier nothing arrives at completed");
+}
 
 }  // extern "C"
 

@@ -31,8 +31,10 @@
 namespace gb300lbm {
 
 // A waiting thread is suspended for up to kSuspendNs per poll (it resumes as
-// soon as the phase completes), so waits do not burn issue slots; after
-// kWaitLimit polls (about 2.6 s) the wait gives up.
+// soon as the phase completes, and the hardware may resume it earlier), so
+// waits do not burn issue slots; after kWaitLimit polls the wait gives up
+// (about 0.5 s on GB300, measured by lbm_wait_selftest; a row copy takes
+// microseconds).
 constexpr unsigned kSuspendNs = 20000;
 constexpr unsigned kWaitLimit = 1u << 17;
 

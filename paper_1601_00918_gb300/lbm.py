@@ -30,7 +30,7 @@ EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "l
            "lbm_batch_set_body_force", "lbm_batch_save", "lbm_critical_pressure_batch",
            "lbm_batch_destroy", "lbm_batch_last_error", "lbm_mlp_create", "lbm_mlp_params",
            "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam", "lbm_mlp_train", "lbm_mlp_destroy",
-           "lbm_mlp_last_error", "lbm_step_noalloc")
+           "lbm_mlp_last_error", "lbm_step_noalloc", "lbm_wait_selftest")
 
 
 class LbmError(RuntimeError):
@@ -108,6 +108,8 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_kernel_info.argtypes = [vp, P(ctypes.c_int32)]
     lib.lbm_step_noalloc.argtypes = [vp, vp, vp, vp, P(Params)]
     lib.lbm_step_noalloc.restype = ctypes.c_int
+    lib.lbm_wait_selftest.argtypes = [vp, dp]
+    lib.lbm_wait_selftest.restype = ctypes.c_int
     lib.lbm_batch_create.argtypes = [P(Instance), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, P(vp)]
     lib.lbm_batch_step.argtypes = [vp, ctypes.c_int64]
     lib.lbm_batch_observables.argtypes = [vp, P(Obs)]
@@ -227,6 +229,14 @@ def lbm_save(h, nx, ny):
 def lbm_load(h, f):
     f = np.ascontiguousarray(f, dtype=np.float64)
     _check(library().lbm_load(h, _dptr(f)), h)
+
+
+def lbm_wait_selftest(stream=None):
+    """Run the bounded device wait on a barrier nothing completes; returns
+    (status, seconds): LBM_ETIMEOUT when the wait gave up as it must."""
+    sec = ctypes.c_double(0.0)
+    rc = library().lbm_wait_selftest(ctypes.c_void_p(stream) if stream else None, ctypes.byref(sec))
+    return rc, sec.value
 
 
 def lbm_kernel_info(h) -> dict:

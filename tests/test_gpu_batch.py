@@ -185,3 +185,20 @@ def test_bisection_status_paths(lbm):
         b.close()
     assert res[0]["status"] == 1 and res[0]["probes"] == 6
     assert res[1]["g_hi"] > 2e-6          # expanded
+
+
+def test_device_wait_gives_up_and_the_context_stays_usable(lbm):
+    """Failure handling of the device waits: the bounded mbarrier wait of the
+    step kernels, run on a barrier nothing ever completes, gives up within a
+    few seconds and the host sees LBM_ETIMEOUT; the CUDA context still works
+    (a batch steps normally right after)."""
+    rc, sec = lbm.lbm_wait_selftest()
+    assert rc == lbm.LBM_ETIMEOUT, (rc, lbm.library().lbm_last_error(None))
+    assert 0.05 < sec < 10.0, sec
+    b = lbm.Batch([channel_instance(32, 2, 6.0, 3.0, 24.0)], precision="fp32")
+    try:
+        b.step(10)
+        obs = b.observables()
+    finally:
+        b.close()
+    assert obs[0]["step"] == 10 and obs[0]["nan_flag"] == 0 and obs[0]["timeout_flag"] == 0
