@@ -144,10 +144,13 @@ int lbm_load(lbm_t *h, const double *f);
 
 /* Launch configuration the autotuner chose for the step kernel:
  * info[0] = variant (1 simple, 2 staged, 3 pipelined, 4 private); info[1] =
- * rows in flight (2..4); info[2] = rows per CTA strip (1) or columns per CTA
- * (2..4); info[3] = strips per column block (2..4).  Not part of the paper's
+ * rows in flight (variants 2..4); info[2] = rows per CTA strip (variant 1)
+ * or columns per CTA (2..4); info[3] = strips per column block (2..4);
+ * info[4] = 1 when the staged kernel's strips sit at the same absolute rows
+ * in every column block, 0 when each block's fluid rows are split into
+ * equal strips (and for the other variants).  Not part of the paper's
  * method: a report of this library's tuning. */
-int lbm_kernel_info(const lbm_t *h, int32_t info[4]);
+int lbm_kernel_info(const lbm_t *h, int32_t info[5]);
 
 /* Self-test of the device-side wait limit.  Every wait of the step kernels
  * (for a row copy to land, for a ring slot) is bounded: after about 0.5 s

@@ -53,6 +53,7 @@ struct Tuned {
     int rpb = 16;      // simple: rows per CTA strip
     int strips = 1;    // staged: strips per column block
     int bx = 128;      // staged: columns per CTA (64 or 128)
+    int strip_abs = 0; // staged: strips at absolute rows (Grid::strip_rows)
 };
 
 }  // namespace
@@ -169,6 +170,7 @@ Grid make_grid(const lbm_t* h, int row_begin, int row_end) {
     g.row_begin = row_begin;
     g.row_end = row_end;
     g.strips = h->tune.strips;
+    g.strip_rows = 0;
     return g;
 }
 
@@ -190,6 +192,7 @@ cudaError_t launch_staged(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, Obs
     }
     Grid g = make_grid(h, 0, h->p.ny);
     g.strips = tn.strips;
+    g.strip_rows = tn.strip_abs ? (h->p.ny + tn.strips - 1) / tn.strips : 0;
     dim3 grid((h->p.nx + BX - 1) / BX, tn.strips);
     step_staged_kernel<S, BX, D><<<grid, BX, Plan::kBytes, st>>>(
         h->smap[src][BX == 64 ? 0 : 1], h->lmap[BX == 64 ? 0 : 1], at_col0<S>(h->fbase[1 - src]), h->rows,
@@ -463,14 +466,21 @@ std::vector<Tuned> candidates(const lbm_t* h) {
                 // strips for 1 to 4 full waves of the CTAs this configuration keeps resident
                 const int per_sm = occupancy(h, var, bx, depth);
                 if (per_sm < 1) continue;
-                for (int waves : {1, 2, 3, 4}) {
-                    Tuned t;
-                    t.variant = var;
-                    t.bx = bx;
-                    t.depth = depth;
-                    const int resident = sms * per_sm;
-                    t.strips = std::max(1, std::min(ny, waves * resident / std::max(1, ncols)));
-                    out.push_back(t);
+                // staged: also strips at absolute rows, up to 5 (their clipped
+                // strips are shorter, so more of them fit the same waves)
+                for (int waves : {1, 2, 3, 4, 5}) {
+                    for (int abs_rows : {0, 1}) {
+                        if (abs_rows && var != 2) continue;
+                        if (!abs_rows && waves > 4) continue;
+                        Tuned t;
+                        t.variant = var;
+                        t.bx = bx;
+                        t.depth = depth;
+                        t.strip_abs = abs_rows;
+                        const int resident = sms * per_sm;
+                        t.strips = std::max(1, std::min(ny, waves * resident / std::max(1, ncols)));
+                        out.push_back(t);
+                    }
                 }
             }
         }
@@ -480,14 +490,15 @@ std::vector<Tuned> candidates(const lbm_t* h) {
         bool dup = false;
         for (auto& v : u)
             dup |= v.variant == t.variant && v.depth == t.depth && v.rpb == t.rpb && v.strips == t.strips &&
-                   v.bx == t.bx;
+                   v.bx == t.bx && v.strip_abs == t.strip_abs;
         if (!dup) u.push_back(t);
     }
     return u;
 }
 
-// GB300LBM_TUNE="staged,<cols per CTA>,<rows in flight>,<strips>" (likewise
-// "pipelined,..." and "private,...") or "simple,<rows per strip>"
+// GB300LBM_TUNE="staged,<cols per CTA>,<rows in flight>,<strips>[,abs]"
+// (",abs": strips at absolute rows; likewise "pipelined,..." and
+// "private,..." without it) or "simple,<rows per strip>"
 // pins the launch configuration (no timing); used to profile one
 // configuration.
 bool tune_from_env(lbm_t* h) {
@@ -495,8 +506,11 @@ bool tune_from_env(lbm_t* h) {
     if (!e || !*e) return false;
     Tuned t;
     int a = 0, b = 0, c = 0;
-    int v = 0;
-    if (sscanf(e, "staged,%d,%d,%d", &a, &b, &c) == 3) v = 2;
+    int v = 0, n = 0;
+    if (sscanf(e, "staged,%d,%d,%d%n", &a, &b, &c, &n) == 3) {
+        v = 2;
+        t.strip_abs = strcmp(e + n, ",abs") == 0;
+    }
     else if (sscanf(e, "pipelined,%d,%d,%d", &a, &b, &c) == 3) v = 3;
     else if (sscanf(e, "private,%d,%d,%d", &a, &b, &c) == 3) v = 4;
     if (v && (a == 64 || a == 128) && (b == 1 || b == 2) && c >= 1 && h->maps_ok) {
@@ -968,12 +982,13 @@ int lbm_load(lbm_t* h, const double* f) {
     return LBM_OK;
 }
 
-int lbm_kernel_info(const lbm_t* h, int32_t info[4]) {
+int lbm_kernel_info(const lbm_t* h, int32_t info[5]) {
     if (!h || !info) return fail(nullptr, LBM_EINVAL, "NULL argument");
     info[0] = h->tune.variant;
     info[1] = h->tune.variant >= 2 ? h->tune.depth : 0;
     info[2] = h->tune.variant == 1 ? h->tune.rpb : h->tune.bx;
     info[3] = h->tune.variant >= 2 ? h->tune.strips : 0;
+    info[4] = h->tune.variant == 2 ? h->tune.strip_abs : 0;
     return LBM_OK;
 }
 

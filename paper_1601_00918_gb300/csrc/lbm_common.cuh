@@ -59,6 +59,9 @@ struct Grid {
     int row_begin;        // first row handled by blockIdx.y == 0 (fields windows)
     int row_end;          // one past the last row handled by this launch
     int strips;           // staged kernel: strips per column block (gridDim.y)
+    int strip_rows;       // staged kernel: > 0: strip s holds the block's fluid rows among the
+                          // absolute rows [s strip_rows, (s + 1) strip_rows); 0: the block's
+                          // fluid rows split into `strips` equal parts
 };
 
 // ---------------------------------------------------------------------------

@@ -167,9 +167,18 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((siz
         }
     }
     const int nrows = rr.y - rr.x + 1;
-    const int rpb = nrows > 0 ? (nrows + grid.strips - 1) / grid.strips : 0;
-    const int y0 = rr.x + blockIdx.y * rpb;
-    const int y1 = min(y0 + rpb, rr.y + 1);
+    int y0, y1;
+    if (grid.strip_rows > 0) {
+        // strips at the same absolute rows in every column block: neighbouring
+        // blocks (adjacent in launch order) march over the same rows at the
+        // same time, so the window columns they share come from L2
+        y0 = max(rr.x, (int)blockIdx.y * grid.strip_rows);
+        y1 = min(rr.y + 1, ((int)blockIdx.y + 1) * grid.strip_rows);
+    } else {
+        const int rpb = nrows > 0 ? (nrows + grid.strips - 1) / grid.strips : 0;
+        y0 = rr.x + blockIdx.y * rpb;
+        y1 = min(y0 + rpb, rr.y + 1);
+    }
     const bool empty = nrows <= 0 || y0 >= y1;
     const int n_stage = empty ? 0 : (y1 - y0) + 4;   // rows y0 - 2 .. y1 + 1
 

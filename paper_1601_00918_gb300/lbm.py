@@ -240,12 +240,15 @@ def lbm_wait_selftest(stream=None):
 
 
 def lbm_kernel_info(h) -> dict:
-    info = (ctypes.c_int32 * 4)()
+    info = (ctypes.c_int32 * 5)()
     _check(library().lbm_kernel_info(h, info), h)
     if info[0] == 1:
         return {"variant": "simple", "rows_per_cta": info[2]}
-    return {"variant": {2: "staged", 3: "pipelined", 4: "private"}[info[0]], "depth": info[1], "cols_per_cta": info[2],
-            "strips": info[3]}
+    d = {"variant": {2: "staged", 3: "pipelined", 4: "private"}[info[0]], "depth": info[1], "cols_per_cta": info[2],
+         "strips": info[3]}
+    if info[0] == 2:
+        d["strip_rows"] = "absolute" if info[4] else "per block"
+    return d
 
 
 def lbm_destroy(h):

@@ -225,13 +225,15 @@ def test_set_body_force_and_save_load_roundtrip(lbm):
 
 
 @pytest.mark.parametrize("tune", ["staged,64,1,2", "staged,64,2,3", "staged,128,1,2", "staged,128,2,5",
+                                  "staged,64,1,5,abs", "staged,128,2,7,abs", "staged,128,1,47,abs",
                                   "pipelined,64,1,2", "pipelined,64,2,3", "pipelined,128,1,2",
                                   "pipelined,128,2,5", "private,64,1,2", "private,64,2,3",
                                   "private,128,1,2", "private,128,2,5", "simple,7"])
 @pytest.mark.parametrize("precision", ["fp32", "fp16s"])
 def test_every_launch_configuration(lbm, tune, precision, monkeypatch):
     """Each staged configuration (64 or 128 columns per CTA, 1 or 2 rows in
-    flight, several strips) and the simple kernel, pinned through the tuning
+    flight, several strips, per block or at absolute rows, including strips
+    of one or two rows) and the simple kernel, pinned through the tuning
     override, run 20 steps with no bounded wait giving up and agree with
     the oracle."""
     monkeypatch.setenv("GB300LBM_TUNE", tune)
@@ -245,6 +247,8 @@ def test_every_launch_configuration(lbm, tune, precision, monkeypatch):
     finally:
         sim.close()
     assert info["variant"] == tune.split(",")[0]
+    if info["variant"] == "staged":
+        assert info["strip_rows"] == ("absolute" if tune.endswith(",abs") else "per block")
     assert obs["timeout_flag"] == 0 and obs["nan_flag"] == 0 and obs["step"] == 20
     P = oracle.Problem(mask, **kw)
     rho_r, _, _ = P.fields(P.run(P.init(rho), 20))
