@@ -282,6 +282,7 @@ def native_arm(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.cpu_seconds)
     crit = critical_pressure_arm(args) if rank == 0 and args.sweep_n > 0 else None
+    bstep = batched_step_arm(args, peak) if rank == 0 and args.batch_n > 0 else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -299,11 +300,57 @@ def native_arm(args):
                              "kernel": "step_%s_kernel" % kinfo["variant"],
                              "alg_bytes_per_launch": alg_bytes},
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "cpu_baseline": cpu,
-                "critical_pressure": crit}
+                "critical_pressure": crit, "batched_step": bstep}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def batched_step_arm(args, peak):
+    """Steps of the batch of sweep channels at their full sizes (lambda in
+    {128, 192, 256, 384, 512} nodes, 4 periods, A/h0 ~ U[0.2, 0.6], slug /
+    lambda ~ U[1, 2], theta ~ U[20, 160] deg, seed 0; 512 channels: 1.23e8
+    nodes, 8.6e7 fluid), one launch per step for all of them, in FP16-shifted
+    storage (the sweep's precision) and FP32: fluid-node updates per second
+    and the algorithmic bytes of a step (18 populations read and written per
+    fluid node) against the measured copy rate.  The channels start at rest
+    with the slug in place and g = 1e-5 (a moving state, no bisection)."""
+    import torch
+    from paper_1601_00918_gb300 import lbm, sweep
+    from paper_1601_00918_gb300 import workloads as wl
+    specs = wl.sweep_specs(args.batch_n, seed=0)
+    insts = [dict(sweep.instance_of(s), g=(1e-5, 0.0)) for s in specs]
+    n_fluid = sum(int(np.count_nonzero(d["mask"] == 0)) for d in insts)
+    n_nodes = sum(int(d["mask"].size) for d in insts)
+    out = {"channels": len(insts), "nodes": n_nodes, "fluid_nodes": n_fluid, "steps": args.batch_steps,
+           "warmup": 16, "l2": "state > 129 MB L2: no flush needed"}
+    stream = torch.cuda.current_stream()
+    for prec in ("fp16s", "fp32"):
+        b = lbm.Batch(insts, precision=prec)
+        try:
+            kinfo = b.kernel_info()
+            b.step(16)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(args.batch_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            obs = b.observables(check=False)
+        finally:
+            b.close()
+        assert all(o["nan_flag"] == 0 and o["step"] == 16 + args.batch_steps for o in obs)
+        alg = n_fluid * 18 * 2 * BYTES_PER_POP[prec]
+        gbs = alg / (ms * 1e-3 / args.batch_steps) / 1e9
+        out[prec] = {"value": n_fluid * args.batch_steps / (ms * 1e-3) / 1e9, "unit": UNIT,
+                     "ms_per_step": ms / args.batch_steps,
+                     "kernel": "batch_staged_kernel" if kinfo["variant"] == "staged" else "batch_step_kernel",
+                     "strip_rows": kinfo["strip_rows"], "ctas_per_step": kinfo["ctas_per_step"],
+                     "alg_bytes_per_launch": alg, "achieved_gbs": gbs, "frac": gbs / peak}
+    return out
 
 
 def critical_pressure_arm(args):
@@ -424,6 +471,8 @@ def main():
     ap.add_argument("--sweep-n", type=int, default=64, help="channels of the solves/hour sweep (0: skip)")
     ap.add_argument("--sweep-plain", type=int, default=8, help="channels bisected one at a time")
     ap.add_argument("--sweep-train", type=int, default=192, help="channels of the surrogate's training sweep")
+    ap.add_argument("--batch-n", type=int, default=512, help="channels of the batched-step measurement (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=160, help="timed steps of the batched-step measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

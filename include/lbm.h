@@ -226,15 +226,25 @@ typedef struct {
 /* Create n instances of uneven sizes that step together (one launch per step
  * over all of them).  The library copies the instance data; the host arrays
  * may be freed after the call.  Errors as lbm_create (per-instance text in
- * lbm_batch_last_error(NULL)). */
+ * lbm_batch_last_error(NULL)).  FP32 and the 16-bit formats step with the
+ * staged (TMA) march over tiles of 128 columns x R rows holding fluid, R
+ * chosen from the total size (8..64) or pinned by the environment variable
+ * GB300LBM_BATCH_ROWS; FP64 with the register-pull march. */
 int lbm_batch_create(const lbm_instance *inst, int32_t n, int32_t precision, int32_t eq_order,
                      void *cuda_stream, lbm_batch_t **out);
 
 /* Advance every active instance by nsteps (asynchronous). */
 int lbm_batch_step(lbm_batch_t *b, int64_t nsteps);
 
-/* Observables of every instance (out[n]); LBM_EUNSTABLE if any NaN flag. */
+/* Observables of every instance (out[n]); LBM_EUNSTABLE if any NaN flag,
+ * else LBM_ETIMEOUT if a bounded device wait gave up in some step. */
 int lbm_batch_observables(lbm_batch_t *b, lbm_obs *out);
+
+/* Step kernel of the batch: info[0] = 2 staged (TMA) march, 1 register-pull
+ * march; info[1] = rows per strip of the staged tiles (0 otherwise);
+ * info[2] = CTAs per step.  Not part of the paper's method: a report of this
+ * library's tiling. */
+int lbm_batch_kernel_info(const lbm_batch_t *b, int32_t info[3]);
 
 /* Set the x body force of every instance (gx[n]). */
 int lbm_batch_set_body_force(lbm_batch_t *b, const double *gx);
@@ -255,7 +265,8 @@ typedef struct {
 typedef struct {
     double g_lo, g_hi;     /* final bracket: static at g_lo, moving at g_hi */
     int32_t probes;        /* probe windows this instance took part in */
-    int32_t status;        /* 0 converged, 1 max_probes reached, 2 unstable, 3 timeout */
+    int32_t status;        /* 0 converged, 1 max_probes reached, 2 unstable, 3 timeout
+                              (timeout_s ran out, or a bounded device wait gave up) */
 } lbm_crit_result;
 
 /* Bisect every instance of b on its x body force, starting from the brackets

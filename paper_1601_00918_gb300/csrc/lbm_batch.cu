@@ -22,14 +22,25 @@
 // Layout: three regions (A, B, snapshot) of the arena, each holding every
 // instance's population buffer at the same offset; link words in a fourth
 // region.  Buffer layout per instance as in lbm_common.cuh.
+//
+// Step kernels: FP32 and the 16-bit formats run the staged march of the
+// single-grid library (lbm_step_tma.cuh: rows moved to shared memory by the
+// Tensor Memory Accelerator) over a list of (instance, 128-column block,
+// strip of rows) tiles that holds only the rows with fluid; each instance has
+// its own tensor maps in device memory.  FP64 (arithmetic-bound) runs the
+// register-pull march over 128 x ~32 tiles.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -37,6 +48,7 @@
 #include "../../include/lbm.h"
 #include "lbm_setup.cuh"
 #include "lbm_step.cuh"
+#include "lbm_step_tma.cuh"
 
 using namespace gb300lbm;
 
@@ -47,11 +59,17 @@ constexpr int kBatchGraphSteps = 16;   // even: the parity is kept across a repl
 
 enum : int { kCheckHi = 0, kCheckLo = 1, kBisect = 2, kDone = 3 };
 
+// One tile of the staged batch kernel: rows [y0, y1) of the 128 columns
+// starting at x0 of instance inst, marched in direction dir.
+struct BatchTile {
+    int inst, x0, y0, y1, dir, pad[3];
+};
+
 // Per-instance device record.
 struct BatchInst {
     int nx, ny, pitch, periodic_x;
-    int ncb, rpb, strips;         // tiles: ncb column blocks x strips of rpb rows
-    int tile0, ntiles;
+    int ncb, rpb, strips;         // register-pull tiles: ncb column blocks x strips of rpb rows
+    int tile0, ntiles;            // first tile and tile count (of the kernel in use)
     int active;                   // steps run only for active instances
     long long off;                // element offset of the instance buffer in each region
     long long loff;               // element offset of its link words
@@ -109,6 +127,34 @@ __global__ void __launch_bounds__(kTileX) batch_step_kernel(BatchInst* __restric
     reduce_observables<R, kTileX>(ob, &I->acc, &I->obs, false, (unsigned)I->ntiles);
 }
 
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+    // the maps were written by a copy from the host before the launch; make
+    // them visible to the tensor-map proxy before the first copy uses them
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m) : "memory");
+}
+
+// Staged step of the batch: one CTA per tile.  maps holds three tensor maps
+// per instance (populations of region A, of region B, link words).
+template <typename S>
+__global__ void __launch_bounds__(kTileX, sizeof(S) == 4 ? 5 : 4)
+    batch_staged_kernel(BatchInst* __restrict__ inst, const BatchTile* __restrict__ tiles, const CUtensorMap* maps,
+                        S* __restrict__ fa, S* __restrict__ fb, int parity) {
+    using R = typename Codec<S>::R;
+    const BatchTile tl = tiles[blockIdx.x];
+    BatchInst* I = inst + tl.inst;
+    if (!I->active) return;                          // uniform over the CTA
+    const CUtensorMap* m = maps + 3 * tl.inst;
+    if (threadIdx.x == 0) {
+        tensormap_acquire(m + parity);
+        tensormap_acquire(m + 2);
+    }
+    S* fout = (parity ? fa : fb) + I->off + kGhost;
+    ObsLocal<R> ob;
+    const bool timed_out = staged_march<S, kTileX, 1>(m + parity, m + 2, fout, &I->prm, I->nx, I->ny, I->pitch,
+                                                      I->periodic_x, tl.x0, tl.y0, tl.y1, tl.dir, ob);
+    reduce_observables<R, kTileX>(ob, &I->acc, &I->obs, timed_out, (unsigned)I->ntiles);
+}
+
 // Start of a probe window: probe value by state, reset the window's
 // displacement.  One thread per instance.
 __global__ void probe_begin_kernel(BatchInst* __restrict__ inst, int n) {
@@ -134,8 +180,8 @@ __global__ void probe_decide_kernel(BatchInst* __restrict__ inst, int n, double 
     BatchInst* I = inst + i;
     if (!I->active) return;
     I->probes += 1;
-    if (I->obs.nan_flag) {                            // the instance became unstable
-        I->status = 2;
+    if (I->obs.nan_flag || I->obs.timeout_flag) {     // unstable, or a bounded wait gave up
+        I->status = I->obs.nan_flag ? 2 : 3;
         I->state = kDone;
         I->active = 0;
         return;
@@ -182,6 +228,116 @@ cudaError_t launch_batch_step(S* fa, S* fb, BatchInst* inst, const int* tiles, c
     return cudaGetLastError();
 }
 
+// Shared-memory limit of the staged batch kernel, set once per format (at
+// create time, outside any stream capture).
+template <typename S>
+cudaError_t staged_attr() {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(batch_staged_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    StagedPlan<S, kTileX, 1>::kBytes);
+    });
+    return attr;
+}
+
+cudaError_t staged_attr_for(int prec) {
+    if (prec == LBM_FP32) return staged_attr<float>();
+    if (prec == LBM_FP16S) return staged_attr<__half>();
+    return staged_attr<__nv_bfloat16>();
+}
+
+template <typename S>
+cudaError_t launch_batch_staged(S* fa, S* fb, BatchInst* inst, const BatchTile* tiles, const CUtensorMap* maps,
+                                int ntiles, int parity, cudaStream_t st) {
+    batch_staged_kernel<S><<<ntiles, kTileX, StagedPlan<S, kTileX, 1>::kBytes, st>>>(inst, tiles, maps, fa, fb,
+                                                                                     parity);
+    return cudaGetLastError();
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+// Window width (columns) of the staged march for a storage format.
+int staged_window(int prec) {
+    switch (prec) {
+        case LBM_FP32: return StagedPlan<float, kTileX, 1>::kW;
+        default: return StagedPlan<__half, kTileX, 1>::kW;
+    }
+}
+
+// The three tensor maps of instance I (populations in regions A and B, link
+// words); false if the driver refuses one.
+bool encode_instance_maps(CUtensorMap* out, const BatchInst& I, int prec, size_t es, int np, char* fa, char* fb,
+                          uint16_t* links) {
+    auto fn = batch_encode_fn();
+    if (!fn) return false;
+    const CUtensorMapDataType dt = prec == LBM_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : prec == LBM_FP16S ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    char* base[2] = {fa + I.off * es, fb + I.off * es};
+    for (int r = 0; r < 2; r++) {
+        cuuint64_t dims[3] = {(cuuint64_t)I.pitch, (cuuint64_t)I.ny, (cuuint64_t)np};
+        cuuint64_t strides[2] = {(cuuint64_t)I.pitch * es, (cuuint64_t)I.ny * I.pitch * es};
+        cuuint32_t box[3] = {(cuuint32_t)staged_window(prec), 1, (cuuint32_t)np};
+        cuuint32_t el[3] = {1, 1, 1};
+        if (fn(&out[r], dt, 3, base[r], dims, strides, box, el, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)I.pitch, (cuuint64_t)I.ny};
+    cuuint64_t strides[1] = {(cuuint64_t)I.pitch * 2};
+    cuuint32_t box[2] = {(cuuint32_t)StagedPlan<float, kTileX, 1>::kLW, 1};
+    cuuint32_t el[2] = {1, 1};
+    return fn(&out[2], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, links + I.loff, dims, strides, box, el,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// First and last row with fluid in every 128-column block of a mask (lo =
+// ny, hi = -1 for a block without fluid).
+void block_rows(const uint8_t* mask, int nx, int ny, std::vector<int>& lo, std::vector<int>& hi) {
+    const int ncb = (nx + kTileX - 1) / kTileX;
+    lo.assign(ncb, ny);
+    hi.assign(ncb, -1);
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++)
+            if (!mask[(size_t)y * nx + x]) {
+                const int cb = x / kTileX;
+                lo[cb] = std::min(lo[cb], y);
+                hi[cb] = std::max(hi[cb], y);
+            }
+}
+
+// Staged tiles of one instance: for every 128-column block the rows with
+// fluid, cut into strips at the same absolute rows [s R, (s + 1) R) in every
+// block (neighbouring blocks, adjacent in launch order, then share their
+// window columns through L2); odd strips march upwards.  An instance with no
+// fluid still gets one empty tile, so that its observables are reduced.
+void staged_tiles(const std::vector<int>& lo, const std::vector<int>& hi, int ny, int inst, int R,
+                  std::vector<BatchTile>& out) {
+    const int ncb = (int)lo.size();
+    const size_t before = out.size();
+    for (int s = 0; s * R < ny; s++)
+        for (int cb = 0; cb < ncb; cb++) {
+            const int y0 = std::max(lo[cb], s * R), y1 = std::min(hi[cb] + 1, (s + 1) * R);
+            if (y0 < y1) out.push_back(BatchTile{inst, cb * kTileX, y0, y1, (s & 1) ? -1 : 1, {0, 0, 0}});
+        }
+    if (out.size() == before) out.push_back(BatchTile{inst, 0, 0, 0, 1, {0, 0, 0}});
+}
+
 }  // namespace
 
 struct lbm_batch_t {
@@ -195,7 +351,11 @@ struct lbm_batch_t {
     char* snap = nullptr;
     uint16_t* links = nullptr;
     BatchInst* dinst = nullptr;
-    int* dtiles = nullptr;
+    int* dtiles = nullptr;        // register-pull kernel: instance of each tile
+    BatchTile* dstiles = nullptr; // staged kernel: tiles
+    CUtensorMap* dmaps = nullptr; // staged kernel: three maps per instance
+    bool staged = false;
+    int strip_rows = 0;           // staged kernel: rows per strip
     int* dcount = nullptr;
     int* hcount = nullptr;        // pinned
     int ntiles = 0;
@@ -228,6 +388,16 @@ int batch_fail(lbm_batch_t* b, int code, const char* fmt, ...) {
     } while (0)
 
 cudaError_t step_once(lbm_batch_t* b, int parity, cudaStream_t st) {
+    if (b->staged) {
+        if (b->prec == LBM_FP32)
+            return launch_batch_staged<float>((float*)b->fa, (float*)b->fb, b->dinst, b->dstiles, b->dmaps,
+                                              b->ntiles, parity, st);
+        if (b->prec == LBM_FP16S)
+            return launch_batch_staged<__half>((__half*)b->fa, (__half*)b->fb, b->dinst, b->dstiles, b->dmaps,
+                                               b->ntiles, parity, st);
+        return launch_batch_staged<__nv_bfloat16>((__nv_bfloat16*)b->fa, (__nv_bfloat16*)b->fb, b->dinst,
+                                                  b->dstiles, b->dmaps, b->ntiles, parity, st);
+    }
     switch (b->prec) {
         case LBM_FP64: return launch_batch_step<double>((double*)b->fa, (double*)b->fb, b->dinst, b->dtiles, b->links, b->ntiles, parity, st);
         case LBM_FP32: return launch_batch_step<float>((float*)b->fa, (float*)b->fb, b->dinst, b->dtiles, b->links, b->ntiles, parity, st);
@@ -356,11 +526,48 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
     }
     b->region_elems = off;
     b->ntiles = tiles;
+
+    // staged tiles (FP32 and the 16-bit formats): strips of R rows, R chosen
+    // so that the tiles fill about four waves of resident CTAs (8 <= R <= 64),
+    // or pinned by GB300LBM_BATCH_ROWS
+    std::vector<BatchTile> stiles;
+    std::vector<int> stile0(n), sntiles(n);
+    if (precision != LBM_FP64) {
+        std::vector<std::vector<int>> lo(n), hi(n);
+        long long block_rows_total = 0;
+        for (int i = 0; i < n; i++) {
+            block_rows(inst[i].mask, inst[i].nx, inst[i].ny, lo[i], hi[i]);
+            for (size_t k = 0; k < lo[i].size(); k++) block_rows_total += std::max(0, hi[i][k] - lo[i][k] + 1);
+        }
+        int dev = 0, sms = 148, per_sm = 4;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (precision == LBM_FP32)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_staged_kernel<float>, kTileX,
+                                                          StagedPlan<float, kTileX, 1>::kBytes);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_staged_kernel<__half>, kTileX,
+                                                          StagedPlan<__half, kTileX, 1>::kBytes);
+        cudaGetLastError();
+        const long long waves4 = 4LL * sms * std::max(1, per_sm);
+        int R = (int)std::max(8LL, std::min(64LL, block_rows_total / std::max(1LL, waves4)));
+        if (const char* e = getenv("GB300LBM_BATCH_ROWS")) {
+            const int r = atoi(e);
+            if (r >= 1) R = r;
+        }
+        b->strip_rows = R;
+        for (int i = 0; i < n; i++) {
+            stile0[i] = (int)stiles.size();
+            staged_tiles(lo[i], hi[i], inst[i].ny, i, R, stiles);
+            sntiles[i] = (int)stiles.size() - stile0[i];
+        }
+    }
     const size_t region = off * es;
     const size_t lbytes = a256(loff * 2);
     const size_t ibytes = a256(sizeof(BatchInst) * n);
     const size_t tbytes = a256(sizeof(int) * tiles);
-    const size_t total = 3 * region + lbytes + ibytes + tbytes + 256;
+    const size_t stbytes = a256(sizeof(BatchTile) * stiles.size());
+    const size_t mbytes = precision != LBM_FP64 ? a256(sizeof(CUtensorMap) * 3 * n) : 0;
+    const size_t total = 3 * region + lbytes + ibytes + tbytes + 256 + stbytes + mbytes;
     cudaError_t e = cudaMalloc(&b->arena, total);
     if (e != cudaSuccess) {
         delete b;
@@ -374,6 +581,8 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
     b->dinst = (BatchInst*)(p + 3 * region + lbytes);
     b->dtiles = (int*)(p + 3 * region + lbytes + ibytes);
     b->dcount = (int*)(p + 3 * region + lbytes + ibytes + tbytes);
+    b->dstiles = stbytes ? (BatchTile*)(p + 3 * region + lbytes + ibytes + tbytes + 256) : nullptr;
+    b->dmaps = mbytes ? (CUtensorMap*)(p + 3 * region + lbytes + ibytes + tbytes + 256 + stbytes) : nullptr;
     auto bail = [&](int code) {
         std::string m = g_batch_err;
         lbm_batch_destroy(b);
@@ -395,6 +604,29 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
     for (int i = 0; i < n; i++)
         for (int k = 0; k < b->hinst[i].ntiles; k++) tile_inst[b->hinst[i].tile0 + k] = i;
     CTRY(cudaMemcpyAsync(b->dtiles, tile_inst.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice, b->stream));
+    // the staged kernel, unless the driver refuses a tensor map (then every
+    // format runs the register-pull kernel)
+    if (precision != LBM_FP64) {
+        std::vector<CUtensorMap> maps(3 * (size_t)n);
+        bool ok = true;
+        for (int i = 0; i < n && ok; i++)
+            ok = encode_instance_maps(&maps[3 * (size_t)i], b->hinst[i], precision, es, np, b->fa, b->fb, b->links);
+        if (ok) {
+            CTRY(staged_attr_for(precision));
+            CTRY(cudaMemcpyAsync(b->dmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                                 b->stream));
+            CTRY(cudaMemcpyAsync(b->dstiles, stiles.data(), sizeof(BatchTile) * stiles.size(),
+                                 cudaMemcpyHostToDevice, b->stream));
+            for (int i = 0; i < n; i++) {
+                b->hinst[i].tile0 = stile0[i];
+                b->hinst[i].ntiles = sntiles[i];
+            }
+            b->ntiles = (int)stiles.size();
+            b->staged = true;
+            // done with the host vectors before they go out of scope
+            CTRY(cudaStreamSynchronize(b->stream));
+        }
+    }
     CTRY(cudaMemcpyAsync(b->dinst, b->hinst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, b->stream));
     // per instance: stage mask + densities in the snapshot region, links, init A
     for (int i = 0; i < n; i++) {
@@ -467,9 +699,19 @@ int lbm_batch_observables(lbm_batch_t* b, lbm_obs* out) {
         out[i].nan_flag = s.nan_flag;
         out[i].timeout_flag = s.timeout_flag;
         if (s.nan_flag && rc == LBM_OK) rc = LBM_EUNSTABLE;
+        if (s.timeout_flag && rc == LBM_OK) rc = LBM_ETIMEOUT;
     }
-    if (rc) batch_fail(b, rc, "an instance reached a NaN or negative density");
+    if (rc == LBM_EUNSTABLE) batch_fail(b, rc, "an instance reached a NaN or negative density");
+    else if (rc) batch_fail(b, rc, "a bounded device wait gave up: the state of that step is invalid");
     return rc;
+}
+
+int lbm_batch_kernel_info(const lbm_batch_t* b, int32_t info[3]) {
+    if (!b || !info) return batch_fail(nullptr, LBM_EINVAL, "NULL argument");
+    info[0] = b->staged ? 2 : 1;
+    info[1] = b->staged ? b->strip_rows : 0;
+    info[2] = b->ntiles;
+    return LBM_OK;
 }
 
 int lbm_batch_set_body_force(lbm_batch_t* b, const double* gx) {

@@ -115,22 +115,19 @@ struct StagedPlan {
     static constexpr uint32_t kTxBytes = (uint32_t)(kPopBytes + kLW * 2);
 };
 
-// One time step fin -> fout.  fmap views fin as [planes][ny][pitch] (box
-// {kW, 1, planes}), lmap views the link words as [ny][pitch] (box {kLW, 1});
-// fout points at logical column 0
-// of row 0.  rows64[k] = (first, last) row with fluid in columns
-// [64 k, 64 k + 64); a CTA of BX columns merges BX / 64 of them.
+// One CTA's march over the rows [y0, y1) of the BX columns starting at x0,
+// in direction dir (+1: increasing y), for one time step fin -> fout.  fmap
+// views fin as [planes][ny][pitch] (box {kW, 1, planes}), lmap views the link
+// words as [ny][pitch] (box {kLW, 1}); either may live in kernel parameter
+// space or in global memory (written before the launch).  fout
+// points at logical column 0 of row 0.  y0 >= y1: nothing to do.  Returns
+// (uniformly over the CTA) whether a bounded wait gave up; the caller
+// reduces the observables gathered in ob.
 template <typename S, int BX, int D>
-// FP32 at 128 columns and one row ahead fits five CTAs per SM (96 registers
-// without spills, 45.4 KB of shared memory each); the others four (or two).
-__global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((sizeof(S) == 4 && D == 1) ? 5 : 4)))
-    step_staged_kernel(const __grid_constant__ CUtensorMap fmap,
-                                                         const __grid_constant__ CUtensorMap lmap,
-                                                         S* __restrict__ fout,
-                                                         const int2* __restrict__ rows64,
-                                                         const StepParams* __restrict__ prm,
-                                                         ObsAccum* __restrict__ acc,
-                                                         ObsState* __restrict__ obs, Grid grid) {
+__device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUtensorMap* lmap,
+                                             S* __restrict__ fout, const StepParams* __restrict__ prm, int nx,
+                                             int ny, int pitch, int periodic_x, int x0, int y0, int y1, int dir,
+                                             ObsLocal<typename Codec<S>::R>& ob) {
     using C = Codec<S>;
     using R = typename C::R;
     using Plan = StagedPlan<S, BX, D>;
@@ -149,37 +146,10 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((siz
         return (const uint16_t*)(smem + (stage % NS) * Plan::kSlot + Plan::kPopSlot);
     };
 
-    const int nx = grid.nx, ny = grid.ny, pitch = grid.pitch;
     const int plane = ny * pitch;
     const int t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
-    const int cb = blockIdx.x;
-    const int x0 = cb * BX;
-
-    // this CTA's strip of the block's fluid rows
-    int2 rr = make_int2(ny, -1);
-    {
-        const int k0 = x0 / 64, k1 = min((x0 + BX + 63) / 64, (nx + 63) / 64);
-        for (int k = k0; k < k1; k++) {
-            const int2 q = rows64[k];
-            rr.x = min(rr.x, q.x);
-            rr.y = max(rr.y, q.y);
-        }
-    }
-    const int nrows = rr.y - rr.x + 1;
-    int y0, y1;
-    if (grid.strip_rows > 0) {
-        // strips at the same absolute rows in every column block: neighbouring
-        // blocks (adjacent in launch order) march over the same rows at the
-        // same time, so the window columns they share come from L2
-        y0 = max(rr.x, (int)blockIdx.y * grid.strip_rows);
-        y1 = min(rr.y + 1, ((int)blockIdx.y + 1) * grid.strip_rows);
-    } else {
-        const int rpb = nrows > 0 ? (nrows + grid.strips - 1) / grid.strips : 0;
-        y0 = rr.x + blockIdx.y * rpb;
-        y1 = min(y0 + rpb, rr.y + 1);
-    }
-    const bool empty = nrows <= 0 || y0 >= y1;
+    const bool empty = y0 >= y1;
     const int n_stage = empty ? 0 : (y1 - y0) + 4;   // rows y0 - 2 .. y1 + 1
 
     NodeParams<R> P;
@@ -190,12 +160,8 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((siz
     const int wi = t + Plan::kLead;                 // this thread's column in the population window
     const int li = t + Plan::kLinkLead;             // ... and in the link window
 
-    // Odd strips march upwards: a boundary between two strips is then
-    // reached by both of them at the same time (both start there or both
-    // end there), so its rows are read from DRAM once and from L2 the
-    // second time.  Stage j holds the row first + dir (j - 2); the density
-    // ring is indexed by the (unwrapped) row.
-    const int dir = (blockIdx.y & 1) ? -1 : 1;
+    // Stage j holds the row first + dir (j - 2); the density ring is indexed
+    // by the (unwrapped) row.
     const int first = dir > 0 ? y0 : y1 - 1;
     auto slot = [&](int r) { return r & 3; };
     // stages of the rows below (y - 1) and above (y + 1) the row of stage j + 1
@@ -210,8 +176,8 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((siz
         const int j = next_issue++;
         uint64_t* bar = &bars[j % NS];
         mbar_expect_tx(bar, Plan::kTxBytes);
-        tma_load_3d((void*)pops(j), &fmap, x0 + kGhost - Plan::kLead, next_row, 0, bar);
-        tma_load_2d((void*)lnks(j), &lmap, x0 + kGhost - Plan::kLinkLead, next_row, bar);
+        tma_load_3d((void*)pops(j), fmap, x0 + kGhost - Plan::kLead, next_row, 0, bar);
+        tma_load_2d((void*)lnks(j), lmap, x0 + kGhost - Plan::kLinkLead, next_row, bar);
         next_row += dir;
         next_row = next_row == ny ? 0 : (next_row < 0 ? ny - 1 : next_row);
     };
@@ -326,7 +292,6 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((siz
     }
     __syncthreads();
 
-    ObsLocal<R> ob;
     if (!empty) {
         if (t == 0) {
             while (next_issue < NS && next_issue < n_stage) issue();
@@ -394,7 +359,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((siz
                     nb[0][7] = se.x; nb[1][7] = se.y;
                 }
                 collide_store<S, R>(cur, rc0, rc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx,
-                                    grid.periodic_x, ob);
+                                    periodic_x, ob);
             }
             rc0 = rn0;
             rc1 = rn1;
@@ -417,6 +382,55 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((siz
         // a wait gave up: let the copies still in flight land before exit
         for (int j = max(0, next_issue - NS); j < next_issue; j++) mbar_wait(&bars[j % NS], (uint32_t)((j / NS) & 1));
     }
+    return any_timeout;
+}
+
+// One time step fin -> fout of one grid: CTA (bx, by) marches over strip by
+// of column block bx.  fmap / lmap as in staged_march; rows64[k] = (first,
+// last) row with fluid in columns [64 k, 64 k + 64); a CTA of BX columns
+// merges BX / 64 of them.
+template <typename S, int BX, int D>
+// FP32 at 128 columns and one row ahead fits five CTAs per SM (96 registers
+// without spills, 45.4 KB of shared memory each); the others four (or two).
+__global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((sizeof(S) == 4 && D == 1) ? 5 : 4)))
+    step_staged_kernel(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap lmap,
+                       S* __restrict__ fout, const int2* __restrict__ rows64, const StepParams* __restrict__ prm,
+                       ObsAccum* __restrict__ acc, ObsState* __restrict__ obs, Grid grid) {
+    using R = typename Codec<S>::R;
+    const int nx = grid.nx, ny = grid.ny;
+    const int x0 = blockIdx.x * BX;
+
+    // this CTA's strip of the block's fluid rows
+    int2 rr = make_int2(ny, -1);
+    {
+        const int k0 = x0 / 64, k1 = min((x0 + BX + 63) / 64, (nx + 63) / 64);
+        for (int k = k0; k < k1; k++) {
+            const int2 q = rows64[k];
+            rr.x = min(rr.x, q.x);
+            rr.y = max(rr.y, q.y);
+        }
+    }
+    const int nrows = rr.y - rr.x + 1;
+    int y0, y1;
+    if (grid.strip_rows > 0) {
+        // strips at the same absolute rows in every column block: neighbouring
+        // blocks (adjacent in launch order) march over the same rows at the
+        // same time, so the window columns they share come from L2
+        y0 = max(rr.x, (int)blockIdx.y * grid.strip_rows);
+        y1 = min(rr.y + 1, ((int)blockIdx.y + 1) * grid.strip_rows);
+    } else {
+        const int rpb = nrows > 0 ? (nrows + grid.strips - 1) / grid.strips : 0;
+        y0 = rr.x + blockIdx.y * rpb;
+        y1 = min(y0 + rpb, rr.y + 1);
+    }
+    // Odd strips march upwards: a boundary between two strips is then
+    // reached by both of them at the same time (both start there or both
+    // end there), so its rows are read from DRAM once and from L2 the
+    // second time.
+    const int dir = (blockIdx.y & 1) ? -1 : 1;
+    ObsLocal<R> ob;
+    const bool any_timeout = staged_march<S, BX, D>(&fmap, &lmap, fout, prm, nx, ny, grid.pitch, grid.periodic_x,
+                                                    x0, y0, y1, dir, ob);
     reduce_observables<R, BX>(ob, acc, obs, any_timeout);
 }
 

@@ -30,7 +30,7 @@ EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "l
            "lbm_batch_set_body_force", "lbm_batch_save", "lbm_critical_pressure_batch",
            "lbm_batch_destroy", "lbm_batch_last_error", "lbm_mlp_create", "lbm_mlp_params",
            "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam", "lbm_mlp_train", "lbm_mlp_destroy",
-           "lbm_mlp_last_error", "lbm_step_noalloc", "lbm_wait_selftest")
+           "lbm_mlp_last_error", "lbm_step_noalloc", "lbm_wait_selftest", "lbm_batch_kernel_info")
 
 
 class LbmError(RuntimeError):
@@ -115,6 +115,7 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_batch_observables.argtypes = [vp, P(Obs)]
     lib.lbm_batch_set_body_force.argtypes = [vp, dp]
     lib.lbm_batch_save.argtypes = [vp, ctypes.c_int32, dp]
+    lib.lbm_batch_kernel_info.argtypes = [vp, P(ctypes.c_int32)]
     lib.lbm_critical_pressure_batch.argtypes = [vp, dp, dp, P(BisectOpts), P(CritResult)]
     lib.lbm_batch_destroy.argtypes = [vp]
     lib.lbm_batch_destroy.restype = None
@@ -142,7 +143,8 @@ def library(path: str | None = None) -> ctypes.CDLL:
     for name in ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables",
                  "lbm_get_fields", "lbm_set_body_force", "lbm_save", "lbm_load", "lbm_kernel_info",
                  "lbm_batch_create", "lbm_batch_step", "lbm_batch_observables",
-                 "lbm_batch_set_body_force", "lbm_batch_save", "lbm_critical_pressure_batch"):
+                 "lbm_batch_set_body_force", "lbm_batch_save", "lbm_critical_pressure_batch",
+                 "lbm_batch_kernel_info"):
         getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -378,6 +380,12 @@ def lbm_batch_save(b, i, nx, ny):
     return f
 
 
+def lbm_batch_kernel_info(b) -> dict:
+    info = (ctypes.c_int32 * 3)()
+    _bcheck(library().lbm_batch_kernel_info(b, info), b)
+    return {"variant": {1: "register-pull", 2: "staged"}[info[0]], "strip_rows": info[1], "ctas_per_step": info[2]}
+
+
 def lbm_critical_pressure_batch(b, g_lo, g_hi, rel_bracket=0.02, t_eq=1000, t_obs=2000, max_probes=24,
                                 check_bracket=True, timeout_s=0.0, check=True):
     g_lo = np.ascontiguousarray(g_lo, dtype=np.float64)
@@ -422,6 +430,9 @@ class Batch:
     def save(self, i):
         ny, nx = self.shapes[i]
         return lbm_batch_save(self.h, i, nx, ny)
+
+    def kernel_info(self):
+        return lbm_batch_kernel_info(self.h)
 
     def critical_pressure(self, g_lo, g_hi, **opts):
         return lbm_critical_pressure_batch(self.h, g_lo, g_hi, **opts)

@@ -101,6 +101,53 @@ def test_batch_steps_fp32_match_oracle(lbm):
         np.testing.assert_allclose(f_b, f_r, rtol=0, atol=2e-5)
 
 
+@pytest.mark.parametrize("rows", [None, 1, 3, 8, 64])
+@pytest.mark.parametrize("precision,atol", [("fp32", 2e-5), ("fp16s", 2e-3)])
+def test_staged_batch_tiles_match_oracle(lbm, rows, precision, atol, monkeypatch):
+    """FP32 and FP16-shifted batches step with the staged (TMA) march over
+    tiles of 128 columns x R rows holding fluid: with R chosen by the
+    library or pinned (strips of 1, 3, 8 and 64 rows), four uneven channels
+    and an all-solid one (a single empty tile) stepped together agree with
+    the FP64 oracle; every instance counts its steps."""
+    if rows is None:
+        monkeypatch.delenv("GB300LBM_BATCH_ROWS", raising=False)
+    else:
+        monkeypatch.setenv("GB300LBM_BATCH_ROWS", str(rows))
+    inst = uneven_instances()
+    solid = dict(inst[3], mask=np.ones_like(inst[3]["mask"]))
+    inst.append(solid)
+    b = lbm.Batch(inst, precision=precision)
+    try:
+        info = b.kernel_info()
+        b.step(30)
+        got = [b.save(i) for i in range(len(inst) - 1)]
+        obs = b.observables()
+    finally:
+        b.close()
+    assert info["variant"] == "staged"
+    if rows is not None:
+        assert info["strip_rows"] == rows
+    assert 8 <= info["strip_rows"] <= 64 or rows is not None
+    assert all(o["step"] == 30 and o["timeout_flag"] == 0 for o in obs)
+    assert tuple(obs[-1]["mass"]) == (0.0, 0.0)
+    for d, f_b in zip(inst, got):
+        P = oracle.Problem(d["mask"], tau=d["tau"], G=d["G"], rho_wall=d["rho_wall"], g=d["g"],
+                           periodic=d["periodic"])
+        np.testing.assert_allclose(f_b, P.run(P.init(d["rho_init"]), 30), rtol=0, atol=atol)
+
+
+def test_batch_kernel_choice(lbm):
+    """FP64 batches keep the register-pull march (their step is arithmetic-
+    bound); BF16-shifted ones run staged."""
+    inst = uneven_instances()[:1]
+    for precision, variant in (("fp64", "register-pull"), ("bf16s", "staged")):
+        b = lbm.Batch(inst, precision=precision)
+        try:
+            assert b.kernel_info()["variant"] == variant
+        finally:
+            b.close()
+
+
 def gpu_moving(lbm, d, f_eq, t_obs, precision="fp64"):
     """One probe through the single-grid ABI: restart from f_eq at g."""
     def moving(g):
