@@ -227,9 +227,12 @@ typedef struct {
  * over all of them).  The library copies the instance data; the host arrays
  * may be freed after the call.  Errors as lbm_create (per-instance text in
  * lbm_batch_last_error(NULL)).  FP32 and the 16-bit formats step with the
- * staged (TMA) march over tiles of 128 columns x R rows holding fluid, R
- * chosen from the total size (8..64) or pinned by the environment variable
- * GB300LBM_BATCH_ROWS; FP64 with the register-pull march. */
+ * staged (TMA) march over tiles of 128 columns x R rows holding fluid; R is
+ * timed among 8, 16, 32, 48, 64 and the size that fills four waves of
+ * resident CTAs (a few steps from the initial state into the second buffer,
+ * which leave the state and the observables as created), or pinned by the
+ * environment variable GB300LBM_BATCH_ROWS; FP64 steps with the
+ * register-pull march. */
 int lbm_batch_create(const lbm_instance *inst, int32_t n, int32_t precision, int32_t eq_order,
                      void *cuda_stream, lbm_batch_t **out);
 

@@ -65,6 +65,13 @@ struct BatchTile {
     int inst, x0, y0, y1, dir, pad[3];
 };
 
+// Staged tiles of a whole batch for one strip height R.
+struct TileSet {
+    int R = 0;
+    std::vector<BatchTile> tiles;
+    std::vector<int> t0, nt;      // first tile and tile count of every instance
+};
+
 // Per-instance device record.
 struct BatchInst {
     int nx, ny, pitch, periodic_x;
@@ -527,11 +534,11 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
     b->region_elems = off;
     b->ntiles = tiles;
 
-    // staged tiles (FP32 and the 16-bit formats): strips of R rows, R chosen
-    // so that the tiles fill about four waves of resident CTAs (8 <= R <= 64),
-    // or pinned by GB300LBM_BATCH_ROWS
-    std::vector<BatchTile> stiles;
-    std::vector<int> stile0(n), sntiles(n);
+    // staged tiles (FP32 and the 16-bit formats): strips of R rows.  The
+    // candidates are R = 8, 16, 32, 48, 64 and the R whose tiles fill about
+    // four waves of resident CTAs; they are timed on the batch itself once
+    // its state is set up (GB300LBM_BATCH_ROWS pins one R, no timing)
+    std::vector<TileSet> cands;
     if (precision != LBM_FP64) {
         std::vector<std::vector<int>> lo(n), hi(n);
         long long block_rows_total = 0;
@@ -549,23 +556,35 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
                                                           StagedPlan<__half, kTileX, 1>::kBytes);
         cudaGetLastError();
         const long long waves4 = 4LL * sms * std::max(1, per_sm);
-        int R = (int)std::max(8LL, std::min(64LL, block_rows_total / std::max(1LL, waves4)));
+        std::vector<int> rs = {(int)std::max(8LL, std::min(64LL, block_rows_total / std::max(1LL, waves4))), 8, 16,
+                               32, 48, 64};
         if (const char* e = getenv("GB300LBM_BATCH_ROWS")) {
             const int r = atoi(e);
-            if (r >= 1) R = r;
+            if (r >= 1) rs = {r};
         }
-        b->strip_rows = R;
-        for (int i = 0; i < n; i++) {
-            stile0[i] = (int)stiles.size();
-            staged_tiles(lo[i], hi[i], inst[i].ny, i, R, stiles);
-            sntiles[i] = (int)stiles.size() - stile0[i];
+        for (int R : rs) {
+            bool dup = false;
+            for (const TileSet& c : cands) dup |= c.R == R;
+            if (dup) continue;
+            TileSet c;
+            c.R = R;
+            c.t0.resize(n);
+            c.nt.resize(n);
+            for (int i = 0; i < n; i++) {
+                c.t0[i] = (int)c.tiles.size();
+                staged_tiles(lo[i], hi[i], inst[i].ny, i, R, c.tiles);
+                c.nt[i] = (int)c.tiles.size() - c.t0[i];
+            }
+            cands.push_back(std::move(c));
         }
     }
+    size_t max_stiles = 0;
+    for (const TileSet& c : cands) max_stiles = std::max(max_stiles, c.tiles.size());
     const size_t region = off * es;
     const size_t lbytes = a256(loff * 2);
     const size_t ibytes = a256(sizeof(BatchInst) * n);
     const size_t tbytes = a256(sizeof(int) * tiles);
-    const size_t stbytes = a256(sizeof(BatchTile) * stiles.size());
+    const size_t stbytes = a256(sizeof(BatchTile) * max_stiles);
     const size_t mbytes = precision != LBM_FP64 ? a256(sizeof(CUtensorMap) * 3 * n) : 0;
     const size_t total = 3 * region + lbytes + ibytes + tbytes + 256 + stbytes + mbytes;
     cudaError_t e = cudaMalloc(&b->arena, total);
@@ -615,16 +634,8 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
             CTRY(staged_attr_for(precision));
             CTRY(cudaMemcpyAsync(b->dmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                                  b->stream));
-            CTRY(cudaMemcpyAsync(b->dstiles, stiles.data(), sizeof(BatchTile) * stiles.size(),
-                                 cudaMemcpyHostToDevice, b->stream));
-            for (int i = 0; i < n; i++) {
-                b->hinst[i].tile0 = stile0[i];
-                b->hinst[i].ntiles = sntiles[i];
-            }
-            b->ntiles = (int)stiles.size();
-            b->staged = true;
-            // done with the host vectors before they go out of scope
             CTRY(cudaStreamSynchronize(b->stream));
+            b->staged = true;
         }
     }
     CTRY(cudaMemcpyAsync(b->dinst, b->hinst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, b->stream));
@@ -651,6 +662,58 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
         }
         CTRY(cudaGetLastError());
         CTRY(cudaStreamSynchronize(b->stream));   // the staging area is reused by the next instance
+    }
+    if (b->staged) {
+        // time the strip-row candidates: steps A -> B only (A keeps the
+        // initial state), then the pristine instance records go back up
+        auto use = [&](const TileSet& c, std::vector<BatchInst>& h) -> cudaError_t {
+            for (int i = 0; i < n; i++) {
+                h[i].tile0 = c.t0[i];
+                h[i].ntiles = c.nt[i];
+            }
+            b->ntiles = (int)c.tiles.size();
+            b->strip_rows = c.R;
+            cudaError_t e1 = cudaMemcpyAsync(b->dstiles, c.tiles.data(), sizeof(BatchTile) * c.tiles.size(),
+                                             cudaMemcpyHostToDevice, b->stream);
+            if (e1 == cudaSuccess)
+                e1 = cudaMemcpyAsync(b->dinst, h.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, b->stream);
+            if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(b->stream);
+            return e1;
+        };
+        size_t best = 0;
+        if (cands.size() > 1) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            CTRY(cudaEventCreate(&e0));
+            CTRY(cudaEventCreate(&e1));
+            float best_ms = 1e30f;
+            std::vector<BatchInst> h = b->hinst, back(n);
+            cudaError_t te = cudaSuccess;
+            for (size_t k = 0; k < cands.size() && te == cudaSuccess; k++) {
+                te = use(cands[k], h);
+                if (te == cudaSuccess) te = step_once(b, 0, b->stream);
+                if (te == cudaSuccess) te = cudaEventRecord(e0, b->stream);
+                for (int r = 0; r < 3 && te == cudaSuccess; r++) te = step_once(b, 0, b->stream);
+                if (te == cudaSuccess) te = cudaEventRecord(e1, b->stream);
+                if (te == cudaSuccess) te = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (te == cudaSuccess) te = cudaEventElapsedTime(&ms, e0, e1);
+                if (te == cudaSuccess)
+                    te = cudaMemcpyAsync(back.data(), b->dinst, sizeof(BatchInst) * n, cudaMemcpyDeviceToHost,
+                                         b->stream);
+                if (te == cudaSuccess) te = cudaStreamSynchronize(b->stream);
+                bool gave_up = false;
+                for (int i = 0; i < n; i++) gave_up |= back[i].obs.timeout_flag != 0;
+                // a candidate whose bounded waits gave up is not a candidate
+                if (te == cudaSuccess && !gave_up && ms < best_ms) {
+                    best_ms = ms;
+                    best = k;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            CTRY(te);
+        }
+        CTRY(use(cands[best], b->hinst));
     }
     CTRY(cudaMemcpyAsync(b->fb, b->fa, region, cudaMemcpyDeviceToDevice, b->stream));
     CTRY(cudaMemcpyAsync(b->snap, b->fa, region, cudaMemcpyDeviceToDevice, b->stream));

@@ -136,6 +136,41 @@ def test_staged_batch_tiles_match_oracle(lbm, rows, precision, atol, monkeypatch
         np.testing.assert_allclose(f_b, P.run(P.init(d["rho_init"]), 30), rtol=0, atol=atol)
 
 
+def test_batch_autotune_keeps_the_state_and_tiling_changes_no_bit(lbm, monkeypatch):
+    """The strip-row autotuner steps the batch at create time: afterwards
+    the state and the observables are those of creation (step 0, the
+    initial populations).  The tiling changes no population: every node's
+    density is pulled and summed in the same order in any tile, so 20 steps
+    with the timed choice and with strips of 3 rows agree bit for bit; the
+    observables are sums reduced tile by tile, so they agree to rounding
+    (the oil displacement of these near-static slugs is a difference of
+    opposite momenta, ~1e-8 lattice units)."""
+    inst = uneven_instances()
+    monkeypatch.delenv("GB300LBM_BATCH_ROWS", raising=False)
+    a = lbm.Batch(inst, precision="fp32")
+    monkeypatch.setenv("GB300LBM_BATCH_ROWS", "3")
+    b = lbm.Batch(inst, precision="fp32")
+    try:
+        assert a.kernel_info()["strip_rows"] != 3
+        assert all(o["step"] == 0 and o["oil_disp_x"] == 0.0 for o in a.observables())
+        for i, d in enumerate(inst):
+            P = oracle.Problem(d["mask"], tau=d["tau"], G=d["G"], rho_wall=d["rho_wall"], g=d["g"],
+                               periodic=d["periodic"])
+            np.testing.assert_allclose(a.save(i), P.init(d["rho_init"]), rtol=0, atol=1e-6)
+        a.step(20)
+        b.step(20)
+        for i in range(len(inst)):
+            np.testing.assert_array_equal(a.save(i), b.save(i))
+        oa, ob = a.observables(), b.observables()
+        for x, y in zip(oa, ob):
+            assert x["step"] == y["step"] == 20
+            np.testing.assert_allclose(x["mass"], y["mass"], rtol=1e-6)
+            assert abs(x["oil_disp_x"] - y["oil_disp_x"]) < 1e-6
+    finally:
+        a.close()
+        b.close()
+
+
 def test_batch_kernel_choice(lbm):
     """FP64 batches keep the register-pull march (their step is arithmetic-
     bound); BF16-shifted ones run staged."""
