@@ -88,9 +88,11 @@ def recorded_traffic(precision, wname, kinfo):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms; stop()
+    keeps the samples taken inside the timed region (all of them, marked,
+    if none fell inside)."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
@@ -111,27 +113,37 @@ class ClockSampler:
             self.proc = None
 
     def _read(self):
+        import datetime
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) == 7:
-                self.rows.append(parts)
+            if len(parts) == 8:
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    ts = None
+                self.rows.append([ts] + parts[1:])
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples between host times t0 and t1 (seconds)."""
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-        if not self.rows:
+        rows = [r for r in self.rows if t0 is not None and r[0] is not None and t0 <= r[0] <= t1]
+        inside = bool(rows)
+        if not inside:
+            rows = self.rows
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k] == "Active"})
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+                "samples": len(rows), "in_timed_region": inside}
 
 
 def dist_env():
@@ -179,7 +191,7 @@ def reference_arm(args):
         return 0
     w = workload()
     ny, nx = w.mask.shape
-    per_step = max(0.3, 150.0 / max(1, args.steps + args.warmup))
+    per_step = max(0.02, 150.0 / max(1, args.steps + args.warmup))
     s = oracle_sample_for(w, per_step)
     for _ in range(args.warmup):
         s.step()
@@ -250,14 +262,16 @@ def native_arm(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t_start = time.time()
     e0.record(stream)
     sim.step(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
+    t_end = time.time()
     ms = e0.elapsed_time(e1)
     if ws > 1:
         torch.distributed.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_start, t_end)
     obs1 = sim.observables()
     assert obs1["step"] == obs0["step"] + args.steps and obs1["nan_flag"] == 0
     sim.close()
@@ -460,8 +474,8 @@ def e2e_arm(args, w, prec, device, n_fluid):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=100)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32", choices=list(BYTES_PER_POP))
     ap.add_argument("--variant", default="auto", choices=["auto", "simple", "staged", "pipelined", "private"])
