@@ -108,12 +108,16 @@ def test_staged_batch_tiles_match_oracle(lbm, rows, precision, atol, monkeypatch
     tiles of 128 columns x R rows holding fluid: with R chosen by the
     library or pinned (strips of 1, 3, 8 and 64 rows), four uneven channels
     and an all-solid one (a single empty tile) stepped together agree with
-    the FP64 oracle; every instance counts its steps."""
+    the FP64 oracle; so does a droplet in a box periodic in both directions
+    (rows wrap in y inside the march); every instance counts its steps."""
     if rows is None:
         monkeypatch.delenv("GB300LBM_BATCH_ROWS", raising=False)
     else:
         monkeypatch.setenv("GB300LBM_BATCH_ROWS", str(rows))
     inst = uneven_instances()
+    inst.append(dict(mask=wl.periodic_box(150, 40), rho_init=wl.droplet(150, 40, 12.0, 70.0, 18.0),
+                     tau=(1.0, 1.0), G=G, rho_wall=(0.0, 0.0), g=(1e-5, 0.0), periodic=(True, True),
+                     disp_threshold=10.0))
     solid = dict(inst[3], mask=np.ones_like(inst[3]["mask"]))
     inst.append(solid)
     b = lbm.Batch(inst, precision=precision)

@@ -255,6 +255,29 @@ def test_every_launch_configuration(lbm, tune, precision, monkeypatch):
     assert np.max(np.abs(rho_g - rho_r)) < (1e-5 if precision == "fp32" else 1e-3)
 
 
+@pytest.mark.parametrize("tune", ["staged,128,1,5,abs", "staged,64,2,9,abs", "staged,128,1,7"])
+def test_periodic_box_with_pinned_strips(lbm, tune, monkeypatch):
+    """A droplet in a box periodic in x and y (rows wrap inside the staged
+    march, strips at absolute rows or per block, a 150-column box ragged for
+    both block widths): 50 FP32 steps agree with the oracle."""
+    monkeypatch.setenv("GB300LBM_TUNE", tune)
+    mask, rho = wl.periodic_box(150, 60), wl.droplet(150, 60, 14.0, 60.0, 25.0)
+    kw = dict(tau=(1.0, 0.8), G=G, g=(1e-5, -2e-6))
+    sim = lbm.Simulation(mask, rho, precision="fp32", periodic=(True, True), **kw)
+    try:
+        info = sim.kernel_info()
+        sim.step(50)
+        obs = sim.observables()
+        rho_g, _, _ = sim.fields()
+    finally:
+        sim.close()
+    assert info["variant"] == "staged" and info["strips"] == int(tune.split(",")[3])
+    assert obs["timeout_flag"] == 0 and obs["step"] == 50
+    P = oracle.Problem(mask, periodic=(True, True), **kw)
+    rho_r, _, _ = P.fields(P.run(P.init(rho), 50))
+    assert np.max(np.abs(rho_g - rho_r)) < 5e-6
+
+
 @pytest.mark.parametrize("precision,atol,mass_rtol", [("fp64", 1e-13, 1e-12), ("fp32", 5e-6, 1e-6),
                                                        ("fp16s", 5e-4, 1e-5), ("bf16s", 4e-3, 1e-4)])
 def test_variants_agree(lbm, precision, atol, mass_rtol):
