@@ -441,7 +441,8 @@ def e2e_arm(args, w, prec, device, n_fluid):
     """GLUPS through the C ABI with host buffers: lbm_create from pinned host
     arrays (H2D of mask and densities), then every step lbm_step(1) and
     lbm_observables (D2H of the observables), then lbm_get_fields (D2H of
-    rho, u, p) and lbm_destroy, all inside the timed region."""
+    rho, u, p into pinned arrays) and lbm_destroy, all inside the timed
+    region."""
     import torch
     from paper_1601_00918_gb300 import lbm
     ny, nx = w.mask.shape
@@ -449,6 +450,11 @@ def e2e_arm(args, w, prec, device, n_fluid):
     rho_h = torch.empty((2, ny, nx), dtype=torch.float64, pin_memory=True).numpy()
     mask_h[...] = w.mask
     rho_h[...] = w.rho
+    # the fields come back into pinned arrays too (allocated, like the inputs,
+    # before the timed region)
+    out_h = (torch.empty((2, ny, nx), dtype=torch.float64, pin_memory=True).numpy(),
+             torch.empty((2, ny, nx), dtype=torch.float64, pin_memory=True).numpy(),
+             torch.empty((ny, nx), dtype=torch.float64, pin_memory=True).numpy())
     steps = max(1, min(args.steps, args.e2e_steps))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -458,7 +464,7 @@ def e2e_arm(args, w, prec, device, n_fluid):
     for _ in range(steps):
         lbm.lbm_step(h, 1)
         lbm.lbm_observables(h)
-    lbm.lbm_get_fields(h, nx, ny)
+    lbm.lbm_get_fields(h, nx, ny, out=out_h)
     lbm.lbm_destroy(h)
     dt = time.perf_counter() - t0
     n = nx * ny

@@ -129,7 +129,9 @@ int lbm_observables(lbm_t *h, lbm_obs *out);
  *   rho [2][ny][nx]  species densities (rho_s^a at solid nodes)
  *   u   [2][ny][nx]  mixture velocity planes u_x then u_y,
  *                    u = (j^o + j^w + (F^o + F^w)/2)/(rho^o + rho^w), 0 at solid
- *   p   [ny][nx]     pressure T0 (rho^o + rho^w) - G T0 rho^o rho^w, 0 at solid */
+ *   p   [ny][nx]     pressure T0 (rho^o + rho^w) - G T0 rho^o rho^w, 0 at solid
+ * The arrays are written by device-to-host copies (at full speed when they
+ * are in pinned memory); the call returns when they are complete. */
 int lbm_get_fields(lbm_t *h, double *rho, double *u, double *p);
 
 /* Change the body-force acceleration used by the following steps. */

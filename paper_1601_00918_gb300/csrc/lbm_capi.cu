@@ -714,30 +714,16 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
     const int nx = p->nx, ny = p->ny;
     const size_t n = (size_t)nx * ny;
 
-    // host checks and the fluid row range of every column block
-    int64_t nfluid = 0;
+    // the fluid-node count, the fluid row range of every column block and
+    // the check of the initial densities come from one device pass below
     Layout L;
     layout_of(p, &L);
-    std::vector<int2> rows(L.nrb, int2{ny, -1});
-    for (int y = 0; y < ny; y++)
-        for (int x = 0; x < nx; x++) {
-            const size_t k = (size_t)y * nx + x;
-            if (mask[k]) continue;
-            const double a = rho_init[k], b = rho_init[n + k];
-            if (!(a >= 0.0) || !(b >= 0.0) || !(a + b > 0.0) || !std::isfinite(a + b))
-                return fail(nullptr, LBM_EINVAL,
-                            "rho_init must be finite, >= 0, with positive total at fluid nodes");
-            nfluid++;
-            int2& r = rows[x / kRowBlock];
-            r.x = std::min(r.x, y);
-            r.y = std::max(r.y, y);
-        }
+    const std::vector<int2> rows(L.nrb, int2{ny, -1});
 
     lbm_t* h = new (std::nothrow) lbm_t();
     if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
     h->p = *p;
     h->stream = (cudaStream_t)p->cuda_stream;
-    h->fluid_nodes = nfluid;
     h->pitch = L.pitch;
     h->ncb = L.ncb;
     h->nrb = L.nrb;
@@ -803,6 +789,23 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
     CREATE_TRY(cudaMemcpyAsync(d_rho, rho_init, rho_bytes, cudaMemcpyHostToDevice, h->stream));
     CREATE_TRY(cudaMemcpyAsync(d_mask, mask, n, cudaMemcpyHostToDevice, h->stream));
     CREATE_TRY(cudaMemcpyAsync(h->rows, rows.data(), rows.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream));
+    // scan counters after the staged mask (the staging area is free until B is filled)
+    unsigned long long* d_nfluid = (unsigned long long*)(stage + align256(rho_bytes) + align256(n));
+    int* d_bad = (int*)(d_nfluid + 1);
+    CREATE_TRY(cudaMemsetAsync(d_nfluid, 0, 16, h->stream));
+    scan_kernel<<<dim3((nx + 255) / 256, ny), 256, 0, h->stream>>>(d_mask, d_rho, nx, ny, h->rows, d_nfluid, d_bad);
+    CREATE_TRY(cudaGetLastError());
+    struct {
+        unsigned long long nfluid;
+        int bad, pad;
+    } scan{};
+    CREATE_TRY(cudaMemcpyAsync(&scan, d_nfluid, 16, cudaMemcpyDeviceToHost, h->stream));
+    CREATE_TRY(cudaStreamSynchronize(h->stream));
+    if (scan.bad) {
+        fail(nullptr, LBM_EINVAL, "rho_init must be finite, >= 0, with positive total at fluid nodes");
+        return bail(LBM_EINVAL);
+    }
+    h->fluid_nodes = (int64_t)scan.nfluid;
     CREATE_TRY(cudaMemsetAsync(h->dacc, 0, 2 * L.acc, h->stream));
     CREATE_TRY(cudaMemsetAsync(h->dobs, 0, 2 * L.obs, h->stream));
     CREATE_TRY(cudaMemcpyAsync(h->dprm, &h->hprm, sizeof(StepParams), cudaMemcpyHostToDevice, h->stream));
@@ -879,24 +882,28 @@ int lbm_get_fields(lbm_t* h, double* rho, double* u, double* pr) {
     const int max_rows = (int)std::min<size_t>(ny, h->buf_bytes / (5 * sizeof(double) * nx));
     if (max_rows < 1) return fail(h, LBM_EINVAL, "grid row too long for the staging buffer");
     double* stage = (double*)h->fbase[1 - h->cur];
-    std::vector<double> tmp;
+    // the window's five planes (rho^o, rho^w, u_x, u_y, p) go straight into
+    // the caller's arrays: a single window when the grid fits the buffer,
+    // then rho and u are one copy each (their two planes are adjacent)
     for (int y0 = 0; y0 < ny; y0 += max_rows) {
         const int y1 = std::min(ny, y0 + max_rows);
         const size_t cnt = (size_t)nx * (y1 - y0);
-        CUDA_TRY(h, launch_fields(h, stage, y0, y1));
-        tmp.resize(cnt * 5);
-        CUDA_TRY(h, cudaMemcpyAsync(tmp.data(), stage, cnt * 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         const size_t o = (size_t)y0 * nx;
-        if (rho) {
-            memcpy(rho + o, tmp.data(), cnt * sizeof(double));
-            memcpy(rho + n + o, tmp.data() + cnt, cnt * sizeof(double));
+        const size_t b = cnt * sizeof(double);
+        CUDA_TRY(h, launch_fields(h, stage, y0, y1));
+        double* dst[5] = {rho ? rho + o : nullptr, rho ? rho + n + o : nullptr, u ? u + o : nullptr,
+                          u ? u + n + o : nullptr, pr ? pr + o : nullptr};
+        for (int k = 0; k < 5; k++) {
+            if (!dst[k]) continue;
+            if (cnt == n && k % 2 == 0 && k < 4 && dst[k + 1]) {
+                CUDA_TRY(h, cudaMemcpyAsync(dst[k], stage + k * cnt, 2 * b, cudaMemcpyDeviceToHost, h->stream));
+                k++;
+                continue;
+            }
+            CUDA_TRY(h, cudaMemcpyAsync(dst[k], stage + k * cnt, b, cudaMemcpyDeviceToHost, h->stream));
         }
-        if (u) {
-            memcpy(u + o, tmp.data() + 2 * cnt, cnt * sizeof(double));
-            memcpy(u + n + o, tmp.data() + 3 * cnt, cnt * sizeof(double));
-        }
-        if (pr) memcpy(pr + o, tmp.data() + 4 * cnt, cnt * sizeof(double));
+        // the next window overwrites the staging planes
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     }
     return LBM_OK;
 }

@@ -64,5 +64,35 @@ static __global__ void init_kernel(const double* __restrict__ rho, const uint16_
     }
 }
 
+// One pass over the mask and the initial densities of a single grid: the
+// number of fluid nodes (*nfluid), the first and last fluid row of every
+// 64-column block (rows64, initialised to (ny, -1)), and *bad = 1 if a fluid
+// node's densities are not finite, not >= 0, or sum to 0.  A block of
+// blockDim.x (a multiple of 32) columns of one row per CTA; a warp spans 32
+// columns of one 64-column block.
+static __global__ void scan_kernel(const uint8_t* __restrict__ mask, const double* __restrict__ rho, int nx,
+                                   int ny, int2* __restrict__ rows64, unsigned long long* __restrict__ nfluid,
+                                   int* __restrict__ bad) {
+    __shared__ unsigned count;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (threadIdx.x == 0) count = 0;
+    __syncthreads();
+    const size_t k = (size_t)y * nx + x;
+    const bool fluid = x < nx && y < ny && !mask[k];
+    if (fluid) {
+        const double a = rho[k], b = rho[(size_t)nx * ny + k];
+        if (!(a >= 0.0) || !(b >= 0.0) || !(a + b > 0.0) || !isfinite(a + b)) atomicOr(bad, 1);
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, fluid);
+    if ((threadIdx.x & 31) == 0 && ballot) {
+        atomicAdd(&count, (unsigned)__popc(ballot));
+        int2* r = rows64 + x / 64;
+        atomicMin(&r->x, y);
+        atomicMax(&r->y, y);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && count) atomicAdd(nfluid, (unsigned long long)count);
+}
 
 }  // namespace gb300lbm

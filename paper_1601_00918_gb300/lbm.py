@@ -210,10 +210,15 @@ def lbm_observables(h, check=True) -> dict:
     return d
 
 
-def lbm_get_fields(h, nx, ny):
-    rho = np.empty((2, ny, nx))
-    u = np.empty((2, ny, nx))
-    p = np.empty((ny, nx))
+def lbm_get_fields(h, nx, ny, out=None):
+    """(rho [2, ny, nx], u [2, ny, nx], p [ny, nx]) as float64; `out` may
+    supply the three arrays (C-contiguous float64, e.g. in pinned memory)."""
+    if out is None:
+        out = (np.empty((2, ny, nx)), np.empty((2, ny, nx)), np.empty((ny, nx)))
+    rho, u, p = out
+    for a, shape in ((rho, (2, ny, nx)), (u, (2, ny, nx)), (p, (ny, nx))):
+        if a.shape != shape or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"lbm_get_fields: expected a C-contiguous float64 array of shape {shape}")
     _check(library().lbm_get_fields(h, _dptr(rho), _dptr(u), _dptr(p)), h)
     return rho, u, p
 

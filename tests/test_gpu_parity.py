@@ -255,6 +255,62 @@ def test_every_launch_configuration(lbm, tune, precision, monkeypatch):
     assert np.max(np.abs(rho_g - rho_r)) < (1e-5 if precision == "fp32" else 1e-3)
 
 
+def test_create_checks_the_initial_densities(lbm):
+    """lbm_create checks rho_init at every fluid node on the device (finite,
+    >= 0, positive total) and fails with LBM_EINVAL; values at solid nodes
+    are ignored; a failed create leaves the library usable."""
+    mask, rho, kw = channel()
+    fluid = np.argwhere(mask == 0)
+    y, x = fluid[len(fluid) // 2]
+    for a, value in ((0, -1e-3), (1, np.nan), (0, np.inf)):
+        bad = rho.copy()
+        bad[a, y, x] = value
+        with pytest.raises(lbm.LbmError) as err:
+            lbm.Simulation(mask, bad, **kw)
+        assert err.value.code == lbm.LBM_EINVAL and "rho_init" in str(err.value)
+    bad = rho.copy()
+    bad[:, y, x] = 0.0
+    with pytest.raises(lbm.LbmError):
+        lbm.Simulation(mask, bad, **kw)
+    ok = rho.copy()
+    sy, sx = np.argwhere(mask == 1)[0]
+    ok[:, sy, sx] = np.nan                       # solid: never read
+    f_gpu, obs, _ = gpu_run(lbm, mask, ok, 5, **kw)
+    assert obs["step"] == 5 and obs["nan_flag"] == 0
+    P = oracle.Problem(mask, **kw)
+    np.testing.assert_allclose(f_gpu, P.run(P.init(rho), 5), rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16s"])
+def test_fields_into_caller_arrays(lbm, precision):
+    """lbm_get_fields writes straight into the caller's arrays: pinned or
+    pageable arrays give the same fields, and a NULL pointer skips that
+    field without touching the others."""
+    import ctypes
+    import torch
+    mask, rho, kw = channel()
+    ny, nx = mask.shape
+    sim = lbm.Simulation(mask, rho, precision=precision, **kw)
+    try:
+        sim.step(7)
+        ref = sim.fields()
+        pinned = (torch.empty((2, ny, nx), dtype=torch.float64, pin_memory=True).numpy(),
+                  torch.empty((2, ny, nx), dtype=torch.float64, pin_memory=True).numpy(),
+                  torch.empty((ny, nx), dtype=torch.float64, pin_memory=True).numpy())
+        got = lbm.lbm_get_fields(sim.h, nx, ny, out=pinned)
+        for a, b in zip(ref, got):
+            np.testing.assert_array_equal(a, b)
+        u_only = np.full((2, ny, nx), -7.0)
+        dp = ctypes.POINTER(ctypes.c_double)
+        rc = lbm.library().lbm_get_fields(sim.h, None, u_only.ctypes.data_as(dp), None)
+        assert rc == 0
+        np.testing.assert_array_equal(u_only, ref[1])
+        with pytest.raises(ValueError):
+            lbm.lbm_get_fields(sim.h, nx, ny, out=(np.empty((2, ny, nx), dtype=np.float32),) + pinned[1:])
+    finally:
+        sim.close()
+
+
 @pytest.mark.parametrize("tune", ["staged,128,1,5,abs", "staged,64,2,9,abs", "staged,128,1,7"])
 def test_periodic_box_with_pinned_strips(lbm, tune, monkeypatch):
     """A droplet in a box periodic in x and y (rows wrap inside the staged
