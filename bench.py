@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "2-comp D2Q9 GLUPS (fluid-node updates/s)"
 UNIT = "GLUPS"
+HBM_NOMINAL_GBS = 7900.0        # GB300 HBM3e nominal, for context beside the measured copy rate
 G_INTERACTION = -1.79
 PHYS = dict(tau=(1.0, 1.0), G=G_INTERACTION, rho_wall=(0.5, 0.05), g=(1e-5, 0.0))
 BYTES_PER_POP = {"fp64": 8, "fp32": 4, "fp16s": 2, "bf16s": 2}
@@ -312,7 +313,10 @@ def native_arm(args):
                              "frac": achieved / peak, "traffic": traffic,
                              "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                              "kernel": "step_%s_kernel" % kinfo["variant"],
-                             "alg_bytes_per_launch": alg_bytes},
+                             "alg_bytes_per_launch": alg_bytes,
+                             "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
+                             "traffic_gbs": traffic / per_launch_s / 1e9 if traffic else None},
+                "all_nodes_value": value * nx * ny / n_fluid,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "cpu_baseline": cpu,
                 "critical_pressure": crit, "batched_step": bstep}
         print(json.dumps(line), flush=True)
