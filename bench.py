@@ -177,13 +177,14 @@ class OracleSample:
         return time.perf_counter() - t0
 
 
-def oracle_sample_for(w, seconds_per_step, min_cols=64):
-    """Crop width whose oracle step takes about seconds_per_step."""
+def oracle_sample_for(w, seconds_per_step, min_cols=64, max_cols=2048):
+    """Crop width whose oracle step takes about seconds_per_step (at most
+    max_cols columns: one wavelength of the channel, ~0.7 GB of oracle state)."""
     ny, nx = w.mask.shape
     probe = OracleSample(w, min_cols)
     dt = probe.step()
     per_col = dt / min_cols
-    cols = int(min(nx, max(min_cols, seconds_per_step / max(per_col, 1e-12))))
+    cols = int(min(nx, max_cols, max(min_cols, seconds_per_step / max(per_col, 1e-12))))
     return OracleSample(w, cols)
 
 
@@ -265,7 +266,7 @@ def reference_arm(args):
     # the memory system); at most one wavelength (2048 columns, ~0.7 GB of
     # oracle state) per process
     per_step = max(0.02, 100.0 / max(1, args.steps + args.warmup))
-    cols = min(2048, oracle_sample_for(w, per_step).cols)
+    cols = oracle_sample_for(w, per_step).cols
     procs, model = host_cores()
     value, slowest, n_fluid = oracle_all_cores(w, cols, args.warmup, args.steps, procs)
     sample = (f"FP64 oracle on {procs} host cores ({model or 'model unknown'}), one process per core, each "
