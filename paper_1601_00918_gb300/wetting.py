@@ -96,7 +96,8 @@ def contact_angle(rho_o, rho_w, y_lo: int, y_hi: int, side: str = "right", margi
     """Contact angle through water (degrees) of one end of a slug between
     flat plates with fluid rows y_lo..y_hi; rows within `margin` of a wall
     are left out of the fit."""
-    frac = rho_o / (rho_o + rho_w)
+    with np.errstate(invalid="ignore", divide="ignore"):    # wall rows may hold 0 / 0; only fluid rows are read
+        frac = rho_o / (rho_o + rho_w)
     ys, xs = [], []
     for y in range(y_lo + margin, y_hi - margin + 1):
         x = half_crossings(frac[y], side)
