@@ -374,6 +374,7 @@ def native_arm(args):
         cpu = cpu_baseline(w, args.cpu_seconds)
     crit = critical_pressure_arm(args) if rank == 0 and args.sweep_n > 0 else None
     bstep = batched_step_arm(args, peak) if rank == 0 and args.batch_n > 0 else None
+    small = small_grids_arm() if rank == 0 and not args.no_small else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -394,11 +395,54 @@ def native_arm(args):
                              "traffic_gbs": traffic / per_launch_s / 1e9 if traffic else None},
                 "all_nodes_value": value * nx * ny / n_fluid,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "cpu_baseline": cpu,
-                "critical_pressure": crit, "batched_step": bstep}
+                "critical_pressure": crit, "batched_step": bstep, "small_grids": small}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def small_grids_arm(steps=2000):
+    """The survey's small configurations, each 2000 steps (CUDA graphs of 32
+    steps) after 64 warm-up steps; their state fits in the 129 MB L2, so they
+    show launch and graph overhead, not the HBM roofline: the static droplet
+    (128 x 128 periodic, R = 20, FP64), the layered channel (256 x 66, FP32)
+    and the sinusoidal channel with a slug (1024 x 146) in FP32, FP16- and
+    BF16-shifted storage."""
+    import torch
+    from paper_1601_00918_gb300 import lbm
+    from paper_1601_00918_gb300 import workloads as wl
+    cases = [("droplet_128x128_R20", wl.droplet_box(20.0, 128), "fp64", dict(tau=(1.0, 1.0), G=G_INTERACTION)),
+             ("layered_256x66", wl.Workload("layered", wl.straight_channel(256, 64), wl.layered_channel(256, 64, 12),
+                                            (True, False)), "fp32",
+              dict(tau=(1.0, 1.0), G=G_INTERACTION, g=(1e-6, 0.0))),
+             ]
+    w3 = wl.sinusoidal_slug(1)
+    for prec in ("fp32", "fp16s", "bf16s"):
+        cases.append(("sinusoidal_slug_1024x146", w3, prec, PHYS))
+    stream = torch.cuda.current_stream()
+    out = []
+    for name, w, prec, kw in cases:
+        sim = lbm.Simulation(w.mask, w.rho, precision=prec, periodic=w.periodic, **kw)
+        try:
+            kinfo = sim.kernel_info()
+            sim.step(64)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            obs = sim.observables(check=False)
+        finally:
+            sim.close()
+        n_fluid = int(np.count_nonzero(w.mask == 0))
+        out.append({"workload": name, "precision": prec, "value": n_fluid * steps / (ms * 1e-3) / 1e9,
+                    "unit": UNIT, "us_per_step": 1e3 * ms / steps, "kernel": kinfo,
+                    "nan_flag": obs["nan_flag"]})
+    return out
 
 
 def batched_step_arm(args, peak):
@@ -573,6 +617,7 @@ def main():
     ap.add_argument("--sweep-train", type=int, default=192, help="channels of the surrogate's training sweep")
     ap.add_argument("--batch-n", type=int, default=512, help="channels of the batched-step measurement (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=160, help="timed steps of the batched-step measurement")
+    ap.add_argument("--no-small", action="store_true", help="skip the small-grid latency lines")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
