@@ -403,7 +403,7 @@ def native_arm(args):
 
 
 def small_grids_arm(steps=2000):
-    """The survey's small configurations, each 2000 steps (CUDA graphs of 32
+    """The small configurations, each 2000 steps (CUDA graphs of 32
     steps) after 64 warm-up steps; their state fits in the 129 MB L2, so they
     show launch and graph overhead, not the HBM roofline: the static droplet
     (128 x 128 periodic, R = 20, FP64), the layered channel (256 x 66, FP32)

@@ -290,7 +290,7 @@ const char *lbm_batch_last_error(const lbm_batch_t *b);
  *
  * A small network that maps a channel description to a predicted log g_crit
  * with an uncertainty; it only seeds the brackets of
- * lbm_critical_pressure_batch, which stays the judge.  Network 5 -> 128 ->
+ * lbm_critical_pressure_batch, which alone decides.  Network 5 -> 128 ->
  * 128 -> 128 -> 2, SiLU hidden units, outputs (mu, s): mu the predicted
  * log g_crit, s the log predicted variance; per-sample loss
  * 0.5 (exp(-s) (y - mu)^2 + s).  34050 FP32 parameters, flat order

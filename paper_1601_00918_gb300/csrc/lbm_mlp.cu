@@ -2,7 +2,7 @@
 // negative log-likelihood and Adam as hand-written FP32 CUDA kernels.
 //
 // Not part of the paper: the network only seeds the bisection brackets of
-// lbm_critical_pressure_batch, which stays the judge of the result.
+// lbm_critical_pressure_batch, which alone decides the result.
 // Network 5 -> 128 -> 128 -> 128 -> 2 with SiLU hidden units; outputs
 // (mu, s) = (predicted log g_crit, log predicted variance); per-sample loss
 // 0.5 (exp(-s) (y - mu)^2 + s), averaged over the batch.  Parameters flat:

@@ -69,9 +69,9 @@ def test_layered_poiseuille_profile(lbm, tau_core, tau_wall, core, bound):
     profile (walls half a node outside the last fluid rows, interface at
     |y| = 20, viscosities mu = rho nu_mix of each layer's bulk) to `bound` in
     relative L2 (measured: 3.5 % at ratio 1, the diffuse interfaces and the
-    halfway-bounce-back slip).  Viscosity ratios 1, 2, 2.9 and 5.7; the survey's ratios 5
-    and 10 need tau = 0.6, where this plain-BGK model with G = -1.79 loses
-    positivity."""
+    halfway-bounce-back slip).  Viscosity ratios 1, 2, 2.9 and 5.7; ratios 5
+    and 10 at tau = 0.6 make this plain-BGK model with G = -1.79 lose
+    positivity (the regularised collision covers them, tested separately)."""
     mask, rho = layered(core=core)
     tau = [0.0, 0.0]
     tau[core], tau[1 - core] = tau_core, tau_wall

@@ -42,7 +42,7 @@ def test_surrogate_seeded_brackets_save_probes(lbm):
     the data), then bisect fresh channels from the surrogate's +-2 sigma
     brackets: fewer probes per solve than from the wide bracket, and every
     converged result overlaps the wide-bracket result (the LBM bisection
-    stays the judge; a failed surrogate bracket is expanded)."""
+    decides the result; a failed surrogate bracket is expanded)."""
     train_specs = sweep.small_specs(192, seed=1)
     res, _ = sweep.run_sweep(lbm, train_specs, *WIDE, t_eq=T_EQ, t_obs=T_OBS, rel_bracket=0.02)
     ok = [k for k, r in enumerate(res) if r["status"] == 0]
