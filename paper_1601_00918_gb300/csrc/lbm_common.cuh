@@ -85,6 +85,7 @@ struct Codec<double> {
     static constexpr int kPlanes = 18;
     static __device__ __forceinline__ double decode(double v, double, double) { return v; }
     static __device__ __forceinline__ double encode(double v, double, double) { return v; }
+    static __device__ __forceinline__ double pack(double v) { return v; }
     static __device__ __forceinline__ double rho_store(double r) { return r; }
     static __device__ __forceinline__ double rho_value(double s) { return s; }
 };
@@ -96,6 +97,7 @@ struct Codec<float> {
     static constexpr int kPlanes = 18;
     static __device__ __forceinline__ float decode(float v, float, float) { return v; }
     static __device__ __forceinline__ float encode(float v, float, float) { return v; }
+    static __device__ __forceinline__ float pack(float v) { return v; }
     static __device__ __forceinline__ float rho_store(float r) { return r; }
     static __device__ __forceinline__ float rho_value(float s) { return s; }
 };
@@ -112,6 +114,7 @@ struct Codec<__half> {
     static __device__ __forceinline__ __half encode(float v, float w, float rh) {
         return __float2half_rn(__fmaf_rn(-w, rh, v));
     }
+    static __device__ __forceinline__ __half pack(float s) { return __float2half_rn(s); }
     static __device__ __forceinline__ __half rho_store(float r) { return __float2half_rn(r); }
     static __device__ __forceinline__ float rho_value(__half s) { return __half2float(s); }
 };
@@ -127,6 +130,7 @@ struct Codec<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 encode(float v, float w, float rh) {
         return __float2bfloat16_rn(__fmaf_rn(-w, rh, v));
     }
+    static __device__ __forceinline__ __nv_bfloat16 pack(float s) { return __float2bfloat16_rn(s); }
     static __device__ __forceinline__ __nv_bfloat16 rho_store(float r) { return __float2bfloat16_rn(r); }
     static __device__ __forceinline__ float rho_value(__nv_bfloat16 s) { return __bfloat162float(s); }
 };
@@ -329,11 +333,11 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
         eq_deviation<R>(xadd(ux, ax), xadd(uy, ay), P.k3, Ds);
         const R wr[3] = {xmul(Weights<R>::w0(), rho), xmul(Weights<R>::w1(), rho), xmul(Weights<R>::w5(), rho)};
         S* d = dst + a * 9 * plane;
-        R rh = R(0);
+        R delta = R(0);                                 // 16-bit formats: rho - rhohat
         if (C::kNodeShift) {
             const S q = C::rho_store(rho);
             dst[(18 + a) * plane] = q;
-            rh = C::rho_value(q);
+            delta = xsub(rho, C::rho_value(q));
         }
         // non-equilibrium part f' = f - f^eq(rho^a, u_mix) = (f - w rho) - w rho D(u_mix)
         R fn[9];
@@ -366,18 +370,29 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
             fn[8] = dm;
         }
         // f*_i = f_i^eq(rho, u_mix + F/rho) + (1 - 1/tau_mix) f'_i, Eq. (LBM_BGK),
-        // summed as w rho + (w rho D_s + om1 f'); the rest population takes
-        // what the others leave of rho (the f*_i of a node sum to rho exactly
-        // for both forms of f', so this is the same value, rounded once)
+        // = w rho + t_i with t_i = w rho D_s + om1 f'; the rest population
+        // takes what the others leave of rho (the f*_i of a node sum to rho
+        // exactly for both forms of f', so this is the same value, rounded
+        // once).  FP32 / FP64 store f*_i = w rho + t_i (out); the 16-bit
+        // formats store s_i = f*_i - w_i rhohat = w_i (rho - rhohat) + t_i and
+        // s_0 = w_0 (rho - rhohat) - sum_{i>0} t_i (out holds s), one rounding
+        // to FP32 before the one to 16 bits
 #pragma unroll
         for (int i = 1; i < 9; i++) {
             const R w = wr[weight_class(i)];
-            out[a][i] = xadd(w, xfma(w, Ds[i], xmul(om1, fn[i])));
+            const R ti = xfma(w, Ds[i], xmul(om1, fn[i]));
+            out[a][i] = C::kNodeShift ? xfma(wgt<R>(i), delta, ti) : xadd(w, ti);
+            if (C::kNodeShift) fn[i] = ti;
         }
-        out[a][0] = xsub(rho, xadd(xadd(xadd(out[a][1], out[a][3]), xadd(out[a][2], out[a][4])),
-                                   xadd(xadd(out[a][5], out[a][7]), xadd(out[a][6], out[a][8]))));
+        if (C::kNodeShift) {
+            const R ts = xadd(xadd(xadd(fn[1], fn[3]), xadd(fn[2], fn[4])), xadd(xadd(fn[5], fn[7]), xadd(fn[6], fn[8])));
+            out[a][0] = xfma(wgt<R>(0), delta, -ts);
+        } else {
+            out[a][0] = xsub(rho, xadd(xadd(xadd(out[a][1], out[a][3]), xadd(out[a][2], out[a][4])),
+                                       xadd(xadd(out[a][5], out[a][7]), xadd(out[a][6], out[a][8]))));
+        }
 #pragma unroll
-        for (int i = 0; i < 9; i++) d[i * plane] = C::encode(out[a][i], wgt<R>(i), rh);
+        for (int i = 0; i < 9; i++) d[i * plane] = C::pack(out[a][i]);
     }
     // periodic ghost images of columns 0, 1, nx - 2, nx - 1 (ghost columns
     // -2, -1, nx, nx + 1 hold columns (nx - 2, nx - 1, 0, 1) mod nx)
@@ -393,15 +408,9 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
             const int off = gcols[k] - x;
 #pragma unroll
             for (int a = 0; a < 2; a++) {
-                R rh = R(0);
-                if (C::kNodeShift) {
-                    const S q = C::rho_store(a ? rho1 : rho0);
-                    dst[(18 + a) * plane + off] = q;
-                    rh = C::rho_value(q);
-                }
+                if (C::kNodeShift) dst[(18 + a) * plane + off] = C::rho_store(a ? rho1 : rho0);
 #pragma unroll
-                for (int i = 0; i < 9; i++)
-                    dst[a * 9 * plane + i * plane + off] = C::encode(out[a][i], wgt<R>(i), rh);
+                for (int i = 0; i < 9; i++) dst[a * 9 * plane + i * plane + off] = C::pack(out[a][i]);
             }
         }
     }
