@@ -1,18 +1,21 @@
 """Host-side pieces of bench.py (no GPU): the clock summary keeps only the
-samples of the timed region, and a recorded ncu traffic figure is used only
-while the kernel's launch shape and source hash match."""
-import importlib.util
+samples of the timed region, a recorded ncu traffic figure is used only
+while the kernel's launch shape and source hash match, and the all-core
+oracle baseline runs one spawned process per core."""
+import importlib
 import json
 import os
+import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def load_bench():
-    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
-    mod = importlib.util.module_from_spec(spec)
-    spec.loader.exec_module(mod)
-    return mod
+    # imported by its own name, so that spawned worker processes can find
+    # the functions they run
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    return importlib.import_module("bench")
 
 
 def test_clock_summary_keeps_the_timed_region():
@@ -47,3 +50,16 @@ def test_recorded_traffic_needs_the_same_kernel(tmp_path, monkeypatch):
     f.write_text(json.dumps(rec))
     assert b.recorded_traffic("fp32", "w", kinfo) is None
 
+
+
+def test_oracle_on_several_host_cores():
+    """The all-core oracle baseline: spawned processes, one per core, each on
+    its own copy of the crop; the figure counts every process's updates over
+    the slowest one's time."""
+    b = load_bench()
+    w = b.workload()
+    value, slowest, n_fluid = b.oracle_all_cores(w, 16, 1, 2, 2)
+    assert n_fluid == int((w.mask[:, :16] == 0).sum())
+    assert slowest > 0 and value == 2 * n_fluid * 2 / slowest / 1e9
+    n, model = b.host_cores()
+    assert n >= 1 and isinstance(model, str)
