@@ -55,9 +55,11 @@ typedef enum {
 } lbm_status;
 
 /* Storage of the populations.  Arithmetic is FP64 for LBM_FP64 and FP32
- * otherwise.  The 16-bit formats store f_i - w_i rho_ref^a, the population
- * minus the rest equilibrium at the species' reference density rho_ref^a
- * (the mean initial density of the species over fluid nodes). */
+ * otherwise.  The 16-bit formats store s_i = f_i - w_i rhohat^a(x), the
+ * population minus the rest equilibrium at the writing node's own density
+ * rounded to the 16-bit format, rhohat^a(x), which is kept in two extra
+ * planes; a reader adds back w_i rhohat^a of the source node, so only the
+ * small non-equilibrium part is rounded to 16 bits. */
 typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_precision;
 
 typedef struct {
@@ -110,13 +112,15 @@ int lbm_workspace_size(const lbm_params *p, size_t *bytes);
  *   p        parameters; copied, so the caller may free it afterwards
  *   out      receives the handle
  * Errors: LBM_EINVAL (NULL pointer, size, tau <= 1/2, precision, eq_order,
- * open boundary without solid lines, non-positive total density at a fluid
- * node), LBM_ENOMEM, LBM_ECUDA. */
+ * open boundary without solid lines, a fluid node whose initial densities
+ * are not finite, negative, or sum to 0: checked on the device after the
+ * upload), LBM_ENOMEM, LBM_ECUDA. */
 int lbm_create(const uint8_t *mask, const double *rho_init, const lbm_params *p, lbm_t **out);
 
-/* Advance nsteps >= 0 time steps (Eq. basic_LBM_eq with the BGK collision of
- * Eq. LBM_BGK), asynchronously on the handle's stream.  Returns the launch
- * status; instability is reported by lbm_observables. */
+/* Advance nsteps >= 0 time steps (Eq. basic_LBM_eq with the collision of
+ * Eq. LBM_BGK, its non-equilibrium part as lbm_params.collision says),
+ * asynchronously on the handle's stream.  Returns the launch status;
+ * instability is reported by lbm_observables. */
 int lbm_step(lbm_t *h, int64_t nsteps);
 
 /* Synchronise the stream and copy the observables of the latest step.
