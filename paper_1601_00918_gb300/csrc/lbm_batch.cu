@@ -497,6 +497,19 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
                     delete b;
                     return batch_fail(nullptr, LBM_EINVAL, "instance %d: y not periodic but boundary fluid", i);
                 }
+        {
+            const size_t nn = (size_t)nx * ny;
+            for (size_t k = 0; k < nn; k++) {
+                if (in.mask[k]) continue;
+                const double a = in.rho_init[k], c = in.rho_init[nn + k];
+                if (!(a >= 0.0) || !(c >= 0.0) || !(a + c > 0.0) || !std::isfinite(a + c)) {
+                    delete b;
+                    return batch_fail(nullptr, LBM_EINVAL,
+                                      "instance %d: rho_init must be finite, >= 0, with positive total at fluid "
+                                      "nodes", i);
+                }
+            }
+        }
         I.nx = nx;
         I.ny = ny;
         I.pitch = (nx + 2 * kGhost + 31) / 32 * 32;

@@ -338,6 +338,10 @@ def _bcheck(rc, b=None):
     return rc
 
 
+def _collision_code(c):
+    return COLLISIONS[c] if isinstance(c, str) else int(c)
+
+
 def lbm_batch_create(instances, precision="fp32", eq_order=3, stream=None):
     """instances: list of dicts with mask [ny, nx], rho_init [2, ny, nx], tau, G,
     rho_wall, g, periodic, disp_threshold, collision ("bgk" or "regularized")."""
@@ -354,7 +358,7 @@ def lbm_batch_create(instances, precision="fp32", eq_order=3, stream=None):
                           float(d.get("G", 0.0)), (ctypes.c_double * 2)(*d.get("rho_wall", (0.0, 0.0))),
                           (ctypes.c_double * 2)(*d.get("g", (0.0, 0.0))),
                           mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dptr(rho),
-                          float(d.get("disp_threshold", 0.0)), COLLISIONS[d.get("collision", "bgk")])
+                          float(d.get("disp_threshold", 0.0)), _collision_code(d.get("collision", "bgk")))
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     h = ctypes.c_void_p()
     _bcheck(library().lbm_batch_create(arr, len(instances), prec, int(eq_order),

@@ -99,6 +99,34 @@ def test_create_with_bad_densities_fails_with_a_status(lib):
         assert lbm.lbm_last_error(None)
 
 
+@pytest.mark.parametrize("bad", ["negative", "nan", "empty", "tau", "collision", "open_y"])
+def test_batch_create_checks_every_instance_on_the_host(lib, bad):
+    """lbm_batch_create validates each instance before touching the device:
+    the densities at fluid nodes (finite, >= 0, positive total), tau > 1/2,
+    the collision option and solid boundary lines of an open direction."""
+    mask = wl.sinusoidal_channel(64, 24, 6.0, 2.0, 32.0)
+    good = dict(mask=mask, rho_init=wl.slug(64, 24, 16.0, 40.0), tau=(1.0, 1.0), G=-1.79,
+                periodic=(True, False), disp_threshold=16.0)
+    d = dict(good, rho_init=good["rho_init"].copy())
+    y, x = np.argwhere(mask == 0)[5]
+    if bad == "negative":
+        d["rho_init"][1, y, x] = -1e-3
+    elif bad == "nan":
+        d["rho_init"][0, y, x] = np.nan
+    elif bad == "empty":
+        d["rho_init"][:, y, x] = 0.0
+    elif bad == "tau":
+        d["tau"] = (0.5, 1.0)
+    elif bad == "collision":
+        d["collision"] = 2
+    else:
+        d["mask"] = np.zeros_like(mask)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_batch_create([good, d])
+    assert e.value.code == lbm.LBM_EINVAL
+    assert "instance 1" in str(e.value)
+
+
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbm_step(None, 1) == lbm.LBM_EINVAL
     assert lib.lbm_observables(None, None) == lbm.LBM_EINVAL
