@@ -253,6 +253,31 @@ def test_poiseuille_single_species():
     assert np.max(np.abs(u[1])) < 1e-6 * g
 
 
+@pytest.mark.parametrize("tau", [0.6, 0.8, 0.5 + (3.0 / 16.0) ** 0.5, 1.0, 1.5])
+def test_poiseuille_bounce_back_slip_closed_form(tau):
+    """The discrete steady state of force-driven BGK channel flow with
+    halfway bounce-back is known in closed form: the parabola of the walls
+    half a node outside the last fluid rows plus a uniform slip
+    u_s = g [(2 tau - 1)^2 - 3/4] / (6 nu), which vanishes at
+    tau = 1/2 + sqrt(3/16) (the published "exact" relaxation time).  The
+    oracle (G = 0, exact-difference forcing, physical velocity (j + F/2)/rho)
+    reproduces it to 1e-8 of the centre velocity at every tau: this pins the
+    wall position, the forcing, the half-force velocity correction and
+    nu = T0 (tau - 1/2) together."""
+    width, g = 16, 1e-6
+    mask = wl.straight_channel(4, width)
+    rho = wl.uniform(4, width + 2, 1.0, 0.0)
+    P = oracle.Problem(mask, tau=(tau, tau), G=0.0, g=(g, 0.0), periodic=(True, False))
+    _, u, _ = P.fields(P.run(P.init(rho), 40000))
+    prof = u[0, 1:-1, 0]
+    nu = (tau - 0.5) / 3.0
+    a = width / 2.0
+    yy = np.arange(1, width + 1) - (width + 1) / 2.0
+    slip = g * ((2.0 * tau - 1.0) ** 2 - 0.75) / (6.0 * nu)
+    ref = g * (a * a - yy * yy) / (2.0 * nu) + slip
+    assert np.max(np.abs(prof - ref)) < 1e-8 * ref.max()
+
+
 # ----------------------------------------------------------------------------
 # Section 3.1: Laplace law on static droplets
 # ----------------------------------------------------------------------------
