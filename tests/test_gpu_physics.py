@@ -34,6 +34,36 @@ def lbm():
     return mod
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 1e-2)])
+@pytest.mark.parametrize("tau", [0.6, 0.5 + (3.0 / 16.0) ** 0.5, 1.5])
+def test_poiseuille_slip_closed_form(lbm, precision, tol, tau):
+    """Force-driven single-species channel flow with halfway bounce-back on
+    the GPU: the steady profile is the parabola of walls half a node outside
+    the last fluid rows plus the published slip g[(2 tau - 1)^2 - 3/4]/(6 nu)
+    (zero at tau = 1/2 + sqrt(3/16)); FP64 to 1e-8 of the centre velocity.
+    FP32 to 1e-2 of it: populations of ~0.1 carry velocities of 1e-4 to 1e-3
+    here, and their rounding leaves ~3e-7 absolute (measured 3.5e-3 and
+    2.7e-3 relative at tau = 0.93 and 1.5, below 2e-4 at tau = 0.6)."""
+    width, g, nx = 16, 1e-6, 32
+    mask = wl.straight_channel(nx, width)
+    rho = wl.uniform(nx, width + 2, 1.0, 0.0)
+    sim = lbm.Simulation(mask, rho, tau=(tau, tau), G=0.0, g=(g, 0.0), periodic=(True, False),
+                         precision=precision)
+    try:
+        sim.step(40000)
+        obs = sim.observables()
+        _, u, _ = sim.fields()
+    finally:
+        sim.close()
+    assert obs["step"] == 40000
+    prof = u[0, 1:-1, :].mean(axis=1)
+    nu = (tau - 0.5) / 3.0
+    a = width / 2.0
+    yy = np.arange(1, width + 1) - (width + 1) / 2.0
+    ref = g * (a * a - yy * yy) / (2.0 * nu) + g * ((2.0 * tau - 1.0) ** 2 - 0.75) / (6.0 * nu)
+    assert np.max(np.abs(prof - ref)) < tol * ref.max()
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_laplace_surface_tension_matches_oracle(lbm, precision):
     with open(os.path.join(GOLDEN, "laplace_droplets_128.json")) as fh:
