@@ -38,9 +38,9 @@ UNIT = "GLUPS"
 HBM_NOMINAL_GBS = 7900.0        # GB300 HBM3e nominal, for context beside the measured copy rate
 G_INTERACTION = -1.79
 PHYS = dict(tau=(1.0, 1.0), G=G_INTERACTION, rho_wall=(0.5, 0.05), g=(1e-5, 0.0))
-BYTES_PER_POP = {"fp64": 8, "fp32": 4, "fp16s": 2, "bf16s": 2}
-DTYPE_NAME = {"fp64": "f64", "fp32": "f32", "fp16s": "f16-shifted storage, f32 math",
-              "bf16s": "bf16-shifted storage, f32 math"}
+BYTES_PER_POP = {"fp64": 8, "fp32": 4, "fp32c": 4, "fp16s": 2, "bf16s": 2}
+DTYPE_NAME = {"fp64": "f64", "fp32": "f32", "fp32c": "f32 storage, compensated f32 math",
+              "fp16s": "f16-shifted storage, f32 math", "bf16s": "bf16-shifted storage, f32 math"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 

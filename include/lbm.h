@@ -59,8 +59,17 @@ typedef enum {
  * population minus the rest equilibrium at the writing node's own density
  * rounded to the 16-bit format, rhohat^a(x), which is kept in two extra
  * planes; a reader adds back w_i rhohat^a of the source node, so only the
- * small non-equilibrium part is rounded to 16 bits. */
-typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3 } lbm_precision;
+ * small non-equilibrium part is rounded to 16 bits.
+ * LBM_FP32C stores FP32 like LBM_FP32 and compensates the two arithmetic
+ * stages whose FP32 rounding dominates the error against exact arithmetic:
+ * the density sums (rho carried as an unevaluated pair hi + lo through
+ * Fast2Sum) and the composition of each stored population from w_i rho
+ * (an FMA TwoProduct, with the FP32 weights' own rounding folded in) and the
+ * equilibrium and non-equilibrium parts, so that each stored population is
+ * rounded once.  Everything else stays plain FP32.  The cost and the
+ * accuracy of both FP32 forms are measured in this library's tests and
+ * benchmark. */
+typedef enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16S = 2, LBM_BF16S = 3, LBM_FP32C = 4 } lbm_precision;
 
 typedef struct {
     int32_t nx, ny;                 /* lattice size, both >= 1 */

@@ -97,7 +97,8 @@ int planes_for(int prec) { return (prec == LBM_FP16S || prec == LBM_BF16S) ? 20 
 size_t esize(int prec) {
     switch (prec) {
         case LBM_FP64: return 8;
-        case LBM_FP32: return 4;
+        case LBM_FP32:
+        case LBM_FP32C: return 4;
         case LBM_FP16S:
         case LBM_BF16S: return 2;
         default: return 0;
@@ -250,6 +251,7 @@ cudaError_t staged_attr() {
 
 cudaError_t staged_attr_for(int prec) {
     if (prec == LBM_FP32) return staged_attr<float>();
+    if (prec == LBM_FP32C) return staged_attr<f32c>();
     if (prec == LBM_FP16S) return staged_attr<__half>();
     return staged_attr<__nv_bfloat16>();
 }
@@ -279,7 +281,8 @@ PFN_cuTensorMapEncodeTiled_v12000 batch_encode_fn() {
 // Window width (columns) of the staged march for a storage format.
 int staged_window(int prec) {
     switch (prec) {
-        case LBM_FP32: return StagedPlan<float, kTileX, 1>::kW;
+        case LBM_FP32:
+        case LBM_FP32C: return StagedPlan<float, kTileX, 1>::kW;
         default: return StagedPlan<__half, kTileX, 1>::kW;
     }
 }
@@ -290,7 +293,7 @@ bool encode_instance_maps(CUtensorMap* out, const BatchInst& I, int prec, size_t
                           uint16_t* links) {
     auto fn = batch_encode_fn();
     if (!fn) return false;
-    const CUtensorMapDataType dt = prec == LBM_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+    const CUtensorMapDataType dt = (prec == LBM_FP32 || prec == LBM_FP32C) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : prec == LBM_FP16S ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                        : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     char* base[2] = {fa + I.off * es, fb + I.off * es};
@@ -399,6 +402,9 @@ cudaError_t step_once(lbm_batch_t* b, int parity, cudaStream_t st) {
         if (b->prec == LBM_FP32)
             return launch_batch_staged<float>((float*)b->fa, (float*)b->fb, b->dinst, b->dstiles, b->dmaps,
                                               b->ntiles, parity, st);
+        if (b->prec == LBM_FP32C)
+            return launch_batch_staged<f32c>((f32c*)b->fa, (f32c*)b->fb, b->dinst, b->dstiles, b->dmaps,
+                                             b->ntiles, parity, st);
         if (b->prec == LBM_FP16S)
             return launch_batch_staged<__half>((__half*)b->fa, (__half*)b->fb, b->dinst, b->dstiles, b->dmaps,
                                                b->ntiles, parity, st);
@@ -408,6 +414,7 @@ cudaError_t step_once(lbm_batch_t* b, int parity, cudaStream_t st) {
     switch (b->prec) {
         case LBM_FP64: return launch_batch_step<double>((double*)b->fa, (double*)b->fb, b->dinst, b->dtiles, b->links, b->ntiles, parity, st);
         case LBM_FP32: return launch_batch_step<float>((float*)b->fa, (float*)b->fb, b->dinst, b->dtiles, b->links, b->ntiles, parity, st);
+        case LBM_FP32C: return launch_batch_step<f32c>((f32c*)b->fa, (f32c*)b->fb, b->dinst, b->dtiles, b->links, b->ntiles, parity, st);
         case LBM_FP16S: return launch_batch_step<__half>((__half*)b->fa, (__half*)b->fb, b->dinst, b->dtiles, b->links, b->ntiles, parity, st);
         default: return launch_batch_step<__nv_bfloat16>((__nv_bfloat16*)b->fa, (__nv_bfloat16*)b->fb, b->dinst, b->dtiles, b->links, b->ntiles, parity, st);
     }
@@ -564,6 +571,9 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
         if (precision == LBM_FP32)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_staged_kernel<float>, kTileX,
                                                           StagedPlan<float, kTileX, 1>::kBytes);
+        else if (precision == LBM_FP32C)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_staged_kernel<f32c>, kTileX,
+                                                          StagedPlan<f32c, kTileX, 1>::kBytes);
         else
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_staged_kernel<__half>, kTileX,
                                                           StagedPlan<__half, kTileX, 1>::kBytes);
@@ -670,6 +680,7 @@ int lbm_batch_create(const lbm_instance* inst, int32_t n, int32_t precision, int
         switch (precision) {
             case LBM_FP64: launch_init<double>(in, I, b->fa, b->links, d_rho, b->stream); break;
             case LBM_FP32: launch_init<float>(in, I, b->fa, b->links, d_rho, b->stream); break;
+            case LBM_FP32C: launch_init<f32c>(in, I, b->fa, b->links, d_rho, b->stream); break;
             case LBM_FP16S: launch_init<__half>(in, I, b->fa, b->links, d_rho, b->stream); break;
             default: launch_init<__nv_bfloat16>(in, I, b->fa, b->links, d_rho, b->stream); break;
         }
@@ -824,7 +835,8 @@ int lbm_batch_save(lbm_batch_t* b, int32_t i, double* f) {
     auto get = [&](size_t k) -> double {
         switch (b->prec) {
             case LBM_FP64: return ((const double*)raw.data())[k];
-            case LBM_FP32: return ((const float*)raw.data())[k];
+            case LBM_FP32:
+            case LBM_FP32C: return ((const float*)raw.data())[k];
             case LBM_FP16S: return __half2float(((const __half*)raw.data())[k]);
             default: return __bfloat162float(((const __nv_bfloat16*)raw.data())[k]);
         }

@@ -118,7 +118,8 @@ int fail(lbm_t* h, int code, const char* fmt, ...) {
 size_t elem_size(int prec) {
     switch (prec) {
         case LBM_FP64: return 8;
-        case LBM_FP32: return 4;
+        case LBM_FP32:
+        case LBM_FP32C: return 4;
         case LBM_FP16S:
         case LBM_BF16S: return 2;
         default: return 0;
@@ -278,6 +279,7 @@ cudaError_t launch_step(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsSt
     switch (h->p.precision) {
         case LBM_FP64: return launch_one<double>(h, src, tn, acc, obs, st);
         case LBM_FP32: return launch_one<float>(h, src, tn, acc, obs, st);
+        case LBM_FP32C: return launch_one<f32c>(h, src, tn, acc, obs, st);
         case LBM_FP16S: return launch_one<__half>(h, src, tn, acc, obs, st);
         default: return launch_one<__nv_bfloat16>(h, src, tn, acc, obs, st);
     }
@@ -297,6 +299,7 @@ cudaError_t launch_fields(lbm_t* h, double* out, int rb, int re) {
     switch (h->p.precision) {
         case LBM_FP64: return launch_fields_t<double>(h, out, rb, re);
         case LBM_FP32: return launch_fields_t<float>(h, out, rb, re);
+        case LBM_FP32C: return launch_fields_t<f32c>(h, out, rb, re);
         case LBM_FP16S: return launch_fields_t<__half>(h, out, rb, re);
         default: return launch_fields_t<__nv_bfloat16>(h, out, rb, re);
     }
@@ -325,7 +328,8 @@ bool make_maps(lbm_t* h) {
     CUtensorMapDataType dt;
     switch (h->p.precision) {
         case LBM_FP64: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT64; break;
-        case LBM_FP32: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
+        case LBM_FP32:
+        case LBM_FP32C: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; break;
         case LBM_FP16S: dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; break;
         default: dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16; break;
     }
@@ -356,7 +360,8 @@ bool make_maps(lbm_t* h) {
         cuuint32_t W = 0;
         switch (h->p.precision) {
             case LBM_FP64: W = k ? StagedPlan<double, 128, 1>::kW : StagedPlan<double, 64, 1>::kW; break;
-            case LBM_FP32: W = k ? StagedPlan<float, 128, 1>::kW : StagedPlan<float, 64, 1>::kW; break;
+            case LBM_FP32:
+            case LBM_FP32C: W = k ? StagedPlan<float, 128, 1>::kW : StagedPlan<float, 64, 1>::kW; break;
             default: W = k ? StagedPlan<__half, 128, 1>::kW : StagedPlan<__half, 64, 1>::kW; break;
         }
         for (int b = 0; b < 2; b++) {
@@ -376,7 +381,8 @@ bool make_maps(lbm_t* h) {
         cuuint32_t W = 0;
         switch (h->p.precision) {
             case LBM_FP64: W = PrivatePlan<double, 1, 1>::kW; break;
-            case LBM_FP32: W = PrivatePlan<float, 1, 1>::kW; break;
+            case LBM_FP32:
+            case LBM_FP32C: W = PrivatePlan<float, 1, 1>::kW; break;
             default: W = PrivatePlan<__half, 1, 1>::kW; break;
         }
         for (int b = 0; b < 2; b++) {
@@ -440,6 +446,7 @@ int occupancy(const lbm_t* h, int var, int bx, int depth) {
     switch (h->p.precision) {
         case LBM_FP64: return occupancy_prec<double>(var, bx, depth);
         case LBM_FP32: return occupancy_prec<float>(var, bx, depth);
+        case LBM_FP32C: return occupancy_prec<f32c>(var, bx, depth);
         case LBM_FP16S: return occupancy_prec<__half>(var, bx, depth);
         default: return occupancy_prec<__nv_bfloat16>(var, bx, depth);
     }
@@ -585,7 +592,8 @@ int autotune(lbm_t* h) {
 double to_double(const void* base, size_t k, int prec) {
     switch (prec) {
         case LBM_FP64: return ((const double*)base)[k];
-        case LBM_FP32: return ((const float*)base)[k];
+        case LBM_FP32:
+        case LBM_FP32C: return ((const float*)base)[k];
         case LBM_FP16S: return __half2float(((const __half*)base)[k]);
         default: return __bfloat162float(((const __nv_bfloat16*)base)[k]);
     }
@@ -594,7 +602,8 @@ double to_double(const void* base, size_t k, int prec) {
 void from_double(void* base, size_t k, int prec, double v) {
     switch (prec) {
         case LBM_FP64: ((double*)base)[k] = v; break;
-        case LBM_FP32: ((float*)base)[k] = (float)v; break;
+        case LBM_FP32:
+        case LBM_FP32C: ((float*)base)[k] = (float)v; break;
         case LBM_FP16S: ((__half*)base)[k] = __float2half_rn((float)v); break;
         default: ((__nv_bfloat16*)base)[k] = __float2bfloat16_rn((float)v); break;
     }
@@ -815,6 +824,7 @@ int lbm_create(const uint8_t* mask, const double* rho_init, const lbm_params* p,
     switch (p->precision) {
         case LBM_FP64: init_kernel<double><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (double*)h->fbase[0], nx, ny, h->pitch, px); break;
         case LBM_FP32: init_kernel<float><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (float*)h->fbase[0], nx, ny, h->pitch, px); break;
+        case LBM_FP32C: init_kernel<f32c><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (f32c*)h->fbase[0], nx, ny, h->pitch, px); break;
         case LBM_FP16S: init_kernel<__half><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (__half*)h->fbase[0], nx, ny, h->pitch, px); break;
         default: init_kernel<__nv_bfloat16><<<grd, blk, 0, h->stream>>>(d_rho, h->links, (__nv_bfloat16*)h->fbase[0], nx, ny, h->pitch, px); break;
     }

@@ -64,6 +64,20 @@ struct Grid {
                           // fluid rows split into `strips` equal parts
 };
 
+// FP32 storage stepped with the compensated FP32 arithmetic (Codec<f32c>):
+// the same four bytes as a float, a distinct type so that every kernel
+// template can be instantiated for it.
+struct f32c {
+    float v;
+    f32c() = default;
+    __host__ __device__ constexpr f32c(float x) : v(x) {}
+    __host__ __device__ constexpr operator float() const { return v; }
+};
+static_assert(sizeof(f32c) == 4 && alignof(f32c) == 4, "f32c must be laid out as a float");
+
+using ::__ldg;
+__device__ __forceinline__ f32c __ldg(const f32c* p) { return f32c(::__ldg(reinterpret_cast<const float*>(p))); }
+
 // ---------------------------------------------------------------------------
 // storage codecs
 //
@@ -82,6 +96,7 @@ template <>
 struct Codec<double> {
     using R = double;
     static constexpr bool kNodeShift = false;
+    static constexpr bool kCompensated = false;
     static constexpr int kPlanes = 18;
     static __device__ __forceinline__ double decode(double v, double, double) { return v; }
     static __device__ __forceinline__ double encode(double v, double, double) { return v; }
@@ -94,6 +109,7 @@ template <>
 struct Codec<float> {
     using R = float;
     static constexpr bool kNodeShift = false;
+    static constexpr bool kCompensated = false;
     static constexpr int kPlanes = 18;
     static __device__ __forceinline__ float decode(float v, float, float) { return v; }
     static __device__ __forceinline__ float encode(float v, float, float) { return v; }
@@ -106,6 +122,7 @@ template <>
 struct Codec<__half> {
     using R = float;
     static constexpr bool kNodeShift = true;
+    static constexpr bool kCompensated = false;
     static constexpr int kPlanes = 20;
     // f = s + w rhohat and s = f - w rhohat, each one fused multiply-add
     static __device__ __forceinline__ float decode(__half v, float w, float rh) {
@@ -123,6 +140,7 @@ template <>
 struct Codec<__nv_bfloat16> {
     using R = float;
     static constexpr bool kNodeShift = true;
+    static constexpr bool kCompensated = false;
     static constexpr int kPlanes = 20;
     static __device__ __forceinline__ float decode(__nv_bfloat16 v, float w, float rh) {
         return __fmaf_rn(w, rh, __bfloat162float(v));
@@ -133,6 +151,31 @@ struct Codec<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 pack(float s) { return __float2bfloat16_rn(s); }
     static __device__ __forceinline__ __nv_bfloat16 rho_store(float r) { return __float2bfloat16_rn(r); }
     static __device__ __forceinline__ float rho_value(__nv_bfloat16 s) { return __bfloat162float(s); }
+};
+
+// FP32 storage, compensated FP32 arithmetic.  Plain FP32 arithmetic leaves a
+// velocity error several times the one that FP32 storage alone causes
+// (rounding of the stored populations with exact arithmetic): the two stages
+// that set it are the density sums (several roundings of a sum of nine
+// values) and the composition f*_i = w_i rho + t_i (the rounding of w_i rho,
+// of the FP32 weights themselves, and of the closure of the rest
+// population).  This codec makes those two stages accurate with
+// error-free transformations in FP32 (Dekker's Fast2Sum and the FMA form of
+// TwoProduct): rho is carried as an unevaluated sum hi + lo, w_i rho as
+// wh + wl with the weights' own FP32 rounding folded into wl, and each
+// stored population is rounded once from wh + (t_i + wl (1 + D_i)).  The
+// rest of the step (force, moments, equilibria) stays plain FP32.
+template <>
+struct Codec<f32c> {
+    using R = float;
+    static constexpr bool kNodeShift = false;
+    static constexpr bool kCompensated = true;
+    static constexpr int kPlanes = 18;
+    static __device__ __forceinline__ float decode(f32c v, float, float) { return v.v; }
+    static __device__ __forceinline__ f32c encode(float v, float, float) { return f32c(v); }
+    static __device__ __forceinline__ f32c pack(float v) { return f32c(v); }
+    static __device__ __forceinline__ f32c rho_store(float r) { return f32c(r); }
+    static __device__ __forceinline__ float rho_value(f32c s) { return s.v; }
 };
 
 // D2Q9, textbook order: c_0 = (0,0); c_1..c_4 = (1,0),(0,1),(-1,0),(0,-1);
@@ -278,6 +321,62 @@ __host__ __device__ __forceinline__ int weight_class(int i) { return i == 0 ? 0 
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 
+// rho = sum_i f_i of one species' pulled populations, summed in the order
+// i = 0..8.  Plain codecs: one running FP32 (FP64) sum, lo = 0.
+// Compensated codec: Dekker's Fast2Sum at every addition (the rest
+// population comes first and every population is smaller than the running
+// sum, the condition under which each error term is exact), the errors
+// accumulated and folded in at the end: hi + lo equals the exact sum to
+// about 2^-48 relative, and hi is the sum rounded once.
+template <typename C, typename R>
+__device__ __forceinline__ void density_of(const R (&f)[9], R& hi, R& lo) {
+    if constexpr (C::kCompensated) {
+        R s = f[0], e = R(0);
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            const R t = xadd(s, f[i]);
+            e = xadd(e, xsub(f[i], xsub(t, s)));
+            s = t;
+        }
+        hi = xadd(s, e);
+        lo = xsub(e, xsub(hi, s));
+    } else {
+        R a = R(0);
+#pragma unroll
+        for (int i = 0; i < 9; i++) a += f[i];
+        hi = a;
+        lo = R(0);
+    }
+}
+
+// Sum of v over the 16 lanes of each half-warp (butterfly), the halo
+// density of one species.  The compensated codec carries each level's error
+// (Knuth's TwoSum, no ordering needed) and returns the sum rounded once, so
+// a halo column's density agrees with the one its owner computes.
+template <typename C, typename R>
+__device__ __forceinline__ R halfwarp_density(R v) {
+    if constexpr (C::kCompensated) {
+        R s = v, e = R(0);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+            const R b = __shfl_xor_sync(0xffffffffu, s, o);
+            const R eb = __shfl_xor_sync(0xffffffffu, e, o);
+            const R t = xadd(s, b);
+            const R bb = xsub(t, s);
+            const R err = xadd(xsub(s, xsub(t, bb)), xsub(b, bb));
+            e = xadd(xadd(e, eb), err);
+            s = t;
+        }
+        return xadd(s, e);
+    } else {
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        return v;
+    }
+}
+
 // Per-thread observables of one step.
 template <typename R>
 struct ObsLocal {
@@ -287,12 +386,13 @@ struct ObsLocal {
 
 // Force, moments and BGK collision at one fluid node, then the store of the
 // 18 post-collision populations (and of their periodic ghost images).
-//   f[a][i]   pulled populations, rho0/rho1 their sums
+//   f[a][i]   pulled populations, rho0/rho1 their sums (density_of), rl0/rl1
+//             the low parts of those sums (zero for the plain codecs)
 //   nb[b][k]  rho^b at the 8 neighbours x + c_k (k = 1..8 in index k-1)
 //   dst       pointer to element (x, y) of plane (species 0, direction 0)
 //   x, nx     the node's column and the grid width (ghost images when periodic)
 template <typename S, typename R>
-__device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1, const R (&nb)[2][8],
+__device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1, R rl0, R rl1, const R (&nb)[2][8],
                                               const NodeParams<R>& P, S* __restrict__ dst, int plane,
                                               int x, int nx, int periodic, ObsLocal<R>& ob) {
     using C = Codec<S>;
@@ -332,6 +432,17 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
         R Ds[9];
         eq_deviation<R>(xadd(ux, ax), xadd(uy, ay), P.k3, Ds);
         const R wr[3] = {xmul(Weights<R>::w0(), rho), xmul(Weights<R>::w1(), rho), xmul(Weights<R>::w5(), rho)};
+        // compensated codec: w_k rho = wr[k] + wl[k] to about 2^-48, the FMA
+        // TwoProduct of the FP32 weight and rho_hi, plus the FP32 weight's
+        // distance to 4/9, 1/9, 1/36 and rho's low part
+        R wl[3] = {R(0), R(0), R(0)};
+        if constexpr (C::kCompensated) {
+            const R rl = a ? rl1 : rl0;
+            const R wf[3] = {Weights<R>::w0(), Weights<R>::w1(), Weights<R>::w5()};
+            const R wlo[3] = {R(-0x1.c71c72p-29), R(-0x1.c71c72p-31), R(0x1.c71c72p-30)};
+#pragma unroll
+            for (int k = 0; k < 3; k++) wl[k] = xfma(wlo[k], rho, xfma(wf[k], rl, xfma(wf[k], rho, -wr[k])));
+        }
         S* d = dst + a * 9 * plane;
         R delta = R(0);                                 // 16-bit formats: rho - rhohat
         if (C::kNodeShift) {
@@ -344,7 +455,10 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
 #pragma unroll
         for (int i = 0; i < 9; i++) {
             const R w = wr[weight_class(i)];
-            fn[i] = xfma(-w, Du[i], xsub(f[a][i], w));
+            if constexpr (C::kCompensated)
+                fn[i] = xfma(-w, Du[i], xsub(xsub(f[a][i], w), wl[weight_class(i)]));
+            else
+                fn[i] = xfma(-w, Du[i], xsub(f[a][i], w));
         }
         if (P.reg) {
             // Eq. (Regualize): f'_i = w_i / (2 T0^2) Q_i : Pi with Q_i = c_i c_i - T0 I
@@ -381,10 +495,23 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
         for (int i = 1; i < 9; i++) {
             const R w = wr[weight_class(i)];
             const R ti = xfma(w, Ds[i], xmul(om1, fn[i]));
-            out[a][i] = C::kNodeShift ? xfma(wgt<R>(i), delta, ti) : xadd(w, ti);
-            if (C::kNodeShift) fn[i] = ti;
+            if constexpr (C::kCompensated) {
+                // (wr + wl)(1 + D_s) + om1 f' rounded once: the low part of
+                // w rho rides with t_i, scaled like the rest of f^eq
+                const R lo = wl[weight_class(i)];
+                out[a][i] = xadd(w, xadd(ti, xfma(lo, Ds[i], lo)));
+                fn[i] = ti;
+            } else {
+                out[a][i] = C::kNodeShift ? xfma(wgt<R>(i), delta, ti) : xadd(w, ti);
+                if (C::kNodeShift) fn[i] = ti;
+            }
         }
-        if (C::kNodeShift) {
+        if constexpr (C::kCompensated) {
+            // the f*_i of a node sum to rho, and the w_i D_s,i and f'_i of
+            // a node sum to zero, so f*_0 = w_0 rho - sum_{i>0} t_i
+            const R ts = xadd(xadd(xadd(fn[1], fn[3]), xadd(fn[2], fn[4])), xadd(xadd(fn[5], fn[7]), xadd(fn[6], fn[8])));
+            out[a][0] = xadd(wr[0], xsub(wl[0], ts));
+        } else if (C::kNodeShift) {
             const R ts = xadd(xadd(xadd(fn[1], fn[3]), xadd(fn[2], fn[4])), xadd(xadd(fn[5], fn[7]), xadd(fn[6], fn[8])));
             out[a][0] = xfma(wgt<R>(0), delta, -ts);
         } else {

@@ -67,12 +67,14 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
     auto wrap_y = [&](int y) { return y < 0 ? y + ny : (y >= ny ? y - ny : y); };
 
     // Pull the 18 populations of row y at column cx.  Returns true at a
-    // solid node (then f is untouched and r0, r1 = wall potentials).
-    auto pull = [&](int y, R(&f)[2][9], R& r0, R& r1) -> bool {
+    // solid node (then f is untouched and r0, r1 = wall potentials); l0, l1
+    // receive the low parts of the density sums (density_of).
+    auto pull = [&](int y, R(&f)[2][9], R& r0, R& r1, R& l0, R& l1) -> bool {
         const unsigned lk = links[y * pitch + cx];
         if (lk & kSolid) {
             r0 = P.rw0;
             r1 = P.rw1;
+            l0 = l1 = R(0);
             return true;
         }
         const int ym = y == 0 ? ny - 1 : y - 1;
@@ -106,14 +108,8 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
             f[0][i] = C::decode(__ldg(fin + pl[i] * plane + nd[i]), wgt<R>(i), r0s);
             f[1][i] = C::decode(__ldg(fin + (9 + pl[i]) * plane + nd[i]), wgt<R>(i), r1s);
         }
-        R a = R(0), b = R(0);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            a += f[0][i];
-            b += f[1][i];
-        }
-        r0 = a;
-        r1 = b;
+        density_of<C>(f[0], r0, l0);
+        density_of<C>(f[1], r1, l1);
         return false;
     };
 
@@ -139,10 +135,7 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
             if (C::kNodeShift) rs = C::rho_value(__ldg(fin + (18 + sp) * plane + node));
             v = C::decode(__ldg(fin + (sp * 9 + pln) * plane + node), wgt<R>(i), rs);
         }
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v = halfwarp_density<C>(v);
         if ((lane & 15) == 0) {
             const R val = (lk & kSolid) ? (sp ? P.rw1 : P.rw0) : v;
             reinterpret_cast<R*>(&s_rho[sl][right ? BX + 1 : 0])[sp] = val;
@@ -151,20 +144,21 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
 
     R cur[2][9], nxt[2][9];
     R rc0 = R(0), rc1 = R(0), rn0 = R(0), rn1 = R(0);
+    R lc0 = R(0), lc1 = R(0), ln0 = R(0), ln1 = R(0);
     bool solid_cur = true, solid_nxt = true;
 
     // prologue: densities of rows y0 - 1 and y0
     {
         const int y = wrap_y(y0 - 1);
         if (rho_col) {
-            R tmp[2][9], a, b;
-            pull(y, tmp, a, b);
+            R tmp[2][9], a, b, la, lb;
+            pull(y, tmp, a, b, la, lb);
             s_rho[slot(y0 - 1)][t + 1] = make_pair_of<R>(a, b);
         }
         halo(y, slot(y0 - 1));
     }
     if (rho_col) {
-        solid_cur = pull(y0, cur, rc0, rc1);
+        solid_cur = pull(y0, cur, rc0, rc1, lc0, lc1);
         s_rho[slot(y0)][t + 1] = make_pair_of<R>(rc0, rc1);
     }
     halo(y0, slot(y0));
@@ -173,7 +167,7 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
         const int yn = r + 1 == ny ? 0 : r + 1;
         const int sn = slot(r + 1);
         if (rho_col) {
-            solid_nxt = pull(yn, nxt, rn0, rn1);
+            solid_nxt = pull(yn, nxt, rn0, rn1, ln0, ln1);
             s_rho[sn][t + 1] = make_pair_of<R>(rn0, rn1);
         }
         halo(yn, sn);
@@ -211,7 +205,7 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
                     node_fields<R>(cur, rc0, rc1, nb, P, fields + (size_t)(r - fr0) * nx + cx,
                                    (size_t)nx * frows);
                 } else {
-                    collide_store<S, R>(cur, rc0, rc1, nb, P, fout + r * pitch + cx, plane, cx, nx,
+                    collide_store<S, R>(cur, rc0, rc1, lc0, lc1, nb, P, fout + r * pitch + cx, plane, cx, nx,
                                         periodic_x, ob);
                 }
             }
@@ -224,6 +218,8 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
             for (int i = 0; i < 9; i++) cur[a][i] = nxt[a][i];
         rc0 = rn0;
         rc1 = rn1;
+        lc0 = ln0;
+        lc1 = ln1;
         solid_cur = solid_nxt;
     }
 }

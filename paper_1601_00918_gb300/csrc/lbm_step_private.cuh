@@ -129,12 +129,14 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
 
     // Pull the populations of the row held by stage jc (rows above/below in
     // jm/jp) at population column w / link column lw.  True at a solid node,
-    // whose "density" is the wall potential.
-    auto pull = [&](int jm, int jc, int jp, int w, int lw, R(&f)[2][9], R& r0, R& r1) -> bool {
+    // whose "density" is the wall potential; l0, l1 receive the low parts of
+    // the density sums (density_of).
+    auto pull = [&](int jm, int jc, int jp, int w, int lw, R(&f)[2][9], R& r0, R& r1, R& l0, R& l1) -> bool {
         const unsigned lk = lnks(jc)[lw];
         if (lk & kSolid) {
             r0 = P.rw0;
             r1 = P.rw1;
+            l0 = l1 = R(0);
             return true;
         }
         const S* pm = pops(jm);
@@ -180,19 +182,13 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
                 f[1][i] = C::decode(q[i][(9 + pl[i]) * W], wgt<R>(i), r1s);
             }
         }
-        R a = R(0), b = R(0);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            a += f[0][i];
-            b += f[1][i];
-        }
-        r0 = a;
-        r1 = b;
+        density_of<C>(f[0], r0, l0);
+        density_of<C>(f[1], r1, l1);
         return false;
     };
 
-    // density only, for the halo columns: the same sources as pull(), summed
-    // as they are read
+    // density only, for the halo columns: the same sources and the same sum
+    // (density_of) as pull()
     auto pull_rho = [&](int jm, int jc, int jp, int w, int lw, R& r0, R& r1) {
         const unsigned lk = lnks(jc)[lw];
         if (lk & kSolid) {
@@ -201,7 +197,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
             return;
         }
         const S* rows[3] = {pops(jm), pops(jc), pops(jp)};
-        R a = R(0), b = R(0);
+        R g[2][9];
         if (lk == 0) {
             // interior node
 #pragma unroll
@@ -212,28 +208,27 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
                     r0s = C::rho_value(q[18 * W]);
                     r1s = C::rho_value(q[19 * W]);
                 }
-                a += C::decode(q[i * W], wgt<R>(i), r0s);
-                b += C::decode(q[(9 + i) * W], wgt<R>(i), r1s);
+                g[0][i] = C::decode(q[i * W], wgt<R>(i), r0s);
+                g[1][i] = C::decode(q[(9 + i) * W], wgt<R>(i), r1s);
             }
-            r0 = a;
-            r1 = b;
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int i = 0; i < 9; i++) {
-            const bool bb = (lk >> i) & 1u;             // bit 0 is never set: the rest population stays
-            const S* q = bb ? rows[1] + w : rows[1 - d2q9_cy(i)] + w - d2q9_cx(i);
-            const int pl = bb ? d2q9_opp(i) : i;
-            R r0s = R(0), r1s = R(0);
-            if (C::kNodeShift) {
-                r0s = C::rho_value(q[18 * W]);
-                r1s = C::rho_value(q[19 * W]);
+            for (int i = 0; i < 9; i++) {
+                const bool bb = (lk >> i) & 1u;             // bit 0 is never set: the rest population stays
+                const S* q = bb ? rows[1] + w : rows[1 - d2q9_cy(i)] + w - d2q9_cx(i);
+                const int pl = bb ? d2q9_opp(i) : i;
+                R r0s = R(0), r1s = R(0);
+                if (C::kNodeShift) {
+                    r0s = C::rho_value(q[18 * W]);
+                    r1s = C::rho_value(q[19 * W]);
+                }
+                g[0][i] = C::decode(q[pl * W], wgt<R>(i), r0s);
+                g[1][i] = C::decode(q[(9 + pl) * W], wgt<R>(i), r1s);
             }
-            a += C::decode(q[pl * W], wgt<R>(i), r0s);
-            b += C::decode(q[(9 + pl) * W], wgt<R>(i), r1s);
         }
-        r0 = a;
-        r1 = b;
+        R l0, l1;
+        density_of<C>(g[0], r0, l0);
+        density_of<C>(g[1], r1, l1);
     };
 
     if (lane == 0) {
@@ -251,6 +246,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
         // 0 and 31) in rows r - 1, r, r + 1 of the row being collided
         R rm0 = R(0), rm1 = R(0), rc0 = R(0), rc1 = R(0), rn0 = R(0), rn1 = R(0);
         R hm0 = R(0), hm1 = R(0), hc0 = R(0), hc1 = R(0), hn0 = R(0), hn1 = R(0);
+        R lc0 = R(0), lc1 = R(0), ln0 = R(0), ln1 = R(0);
         bool sa = true, sb = true;
 
         // prologue: densities of rows y0 - 1 (stages 0, 1, 2) and y0 (1, 2, 3)
@@ -260,7 +256,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
         pull_rho(0, 1, 2, wi, li, rm0, rm1);
         if (halo_lane) pull_rho(0, 1, 2, hw, hl, hm0, hm1);
         wait_full(3);
-        sa = pull(1, 2, 3, wi, li, fa, rc0, rc1);
+        sa = pull(1, 2, 3, wi, li, fa, rc0, rc1, lc0, lc1);
         if (halo_lane) pull_rho(1, 2, 3, hw, hl, hc0, hc1);
         // stages 0 and 1 are done: refill their slots
         __syncwarp();
@@ -283,7 +279,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
             rn0 = rn1 = R(0);
             hn0 = hn1 = R(0);
             s_nxt = true;
-            s_nxt = pull(j, j + 1, j + 2, wi, li, nxt, rn0, rn1);
+            s_nxt = pull(j, j + 1, j + 2, wi, li, nxt, rn0, rn1, ln0, ln1);
             if (halo_lane) pull_rho(j, j + 1, j + 2, hw, hl, hn0, hn1);
             // stage j (row r) is no longer read: lane 0 refills its slot
             __syncwarp();
@@ -298,12 +294,14 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
             nb[0][6] = from_left(rm0, hm0);   nb[1][6] = from_left(rm1, hm1);    // (x - 1, r - 1)
             nb[0][7] = from_right(rm0, hm0);  nb[1][7] = from_right(rm1, hm1);   // (x + 1, r - 1)
             if (active && !s_cur)
-                collide_store<S, R>(cur, rc0, rc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx, grid.periodic_x,
+                collide_store<S, R>(cur, rc0, rc1, lc0, lc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx, grid.periodic_x,
                                     ob);
             rm0 = rc0;
             rm1 = rc1;
             rc0 = rn0;
             rc1 = rn1;
+            lc0 = ln0;
+            lc1 = ln1;
             hm0 = hc0;
             hm1 = hc1;
             hc0 = hn0;

@@ -188,12 +188,14 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
 
     // Pull the populations of the row held by stage jc (rows above/below in
     // jm/jp) at population window column w / link window column lw.  Returns
-    // true at a solid node.
-    auto pull = [&](int jm, int jc, int jp, int w, int lw, R(&f)[2][9], R& r0, R& r1) -> bool {
+    // true at a solid node; r0, r1 (l0, l1) receive the densities (their low
+    // parts, density_of).
+    auto pull = [&](int jm, int jc, int jp, int w, int lw, R(&f)[2][9], R& r0, R& r1, R& l0, R& l1) -> bool {
         const unsigned lk = lnks(jc)[lw];
         if (lk & kSolid) {
             r0 = P.rw0;
             r1 = P.rw1;
+            l0 = l1 = R(0);
             return true;
         }
         const S* pm = pops(jm);
@@ -240,14 +242,8 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
             f[1][i] = C::decode(q[(9 + pl[i]) * W], wgt<R>(i), r1s);
         }
         }
-        R a = R(0), bsum = R(0);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            a += f[0][i];
-            bsum += f[1][i];
-        }
-        r0 = a;
-        r1 = bsum;
+        density_of<C>(f[0], r0, l0);
+        density_of<C>(f[1], r1, l1);
         return false;
     };
 
@@ -278,10 +274,7 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
             if (C::kNodeShift) rs = C::rho_value(q[(18 + sp) * W]);
             v = C::decode(q[(sp * 9 + pln) * W], wgt<R>(i), rs);
         }
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v = halfwarp_density<C>(v);
         if ((lane & 15) == 0)
             reinterpret_cast<R*>(&s_rho[sl][right ? BX + 1 : 0])[sp] = (lk & kSolid) ? (sp ? P.rw1 : P.rw0) : v;
     };
@@ -298,6 +291,7 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
         }
         R fa[2][9], fb[2][9];
         R rc0 = R(0), rc1 = R(0), rn0 = R(0), rn1 = R(0);
+        R lc0 = R(0), lc1 = R(0), ln0 = R(0), ln1 = R(0);
         bool sa = true, sb = true;
 
         // prologue: densities of the rows first - dir (stage 1) and first (stage 2)
@@ -307,13 +301,13 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
         // every thread pulls (its window column always exists); densities of
         // columns beyond nx are read only by threads that do not collide
         {
-            R a, b;
-            pull(below(0), 1, above(0), wi, li, fb, a, b);
+            R a, b, la, lb;
+            pull(below(0), 1, above(0), wi, li, fb, a, b, la, lb);
             s_rho[slot(first - dir)][t + 1] = make_pair_of<R>(a, b);
         }
         halo(below(0), 1, above(0), slot(first - dir));
         wait_stage(3);
-        sa = pull(below(1), 2, above(1), wi, li, fa, rc0, rc1);
+        sa = pull(below(1), 2, above(1), wi, li, fa, rc0, rc1, lc0, lc1);
         s_rho[slot(first)][t + 1] = make_pair_of<R>(rc0, rc1);
         halo(below(1), 2, above(1), slot(first));
         // stages 0 and 1 are no longer needed: refill their slots now, so
@@ -333,7 +327,7 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
             const int j = k + 2;                      // stages j, j+1, j+2 hold rows r, r+dir, r+2dir
             const int sn = slot(r + dir);
             wait_stage(j + 2);
-            s_nxt = pull(below(j), j + 1, above(j), wi, li, nxt, rn0, rn1);
+            s_nxt = pull(below(j), j + 1, above(j), wi, li, nxt, rn0, rn1, ln0, ln1);
             s_rho[sn][t + 1] = make_pair_of<R>(rn0, rn1);
             halo(below(j), j + 1, above(j), sn);
             __syncthreads();
@@ -358,11 +352,13 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
                     nb[0][6] = sw.x; nb[1][6] = sw.y;
                     nb[0][7] = se.x; nb[1][7] = se.y;
                 }
-                collide_store<S, R>(cur, rc0, rc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx,
+                collide_store<S, R>(cur, rc0, rc1, lc0, lc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx,
                                     periodic_x, ob);
             }
             rc0 = rn0;
             rc1 = rn1;
+            lc0 = ln0;
+            lc1 = ln1;
         };
 
         const int nk = y1 - y0;

@@ -136,11 +136,12 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
         if (lane == 0) mbar_arrive(&empty[j % NS]);
     };
 
-    auto pull = [&](int jm, int jc, int jp, int w, R(&f)[2][9], R& r0, R& r1) -> bool {
+    auto pull = [&](int jm, int jc, int jp, int w, R(&f)[2][9], R& r0, R& r1, R& l0, R& l1) -> bool {
         const unsigned lk = lnks(jc)[w];
         if (lk & kSolid) {
             r0 = P.rw0;
             r1 = P.rw1;
+            l0 = l1 = R(0);
             return true;
         }
         const S* pm = pops(jm);
@@ -184,14 +185,8 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
                 f[1][i] = C::decode(q[i][(9 + pl[i]) * W], wgt<R>(i), r1s);
             }
         }
-        R a = R(0), b = R(0);
-#pragma unroll
-        for (int i = 0; i < 9; i++) {
-            a += f[0][i];
-            b += f[1][i];
-        }
-        r0 = a;
-        r1 = b;
+        density_of<C>(f[0], r0, l0);
+        density_of<C>(f[1], r1, l1);
         return false;
     };
 
@@ -217,10 +212,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
             if (C::kNodeShift) rs = C::rho_value(q[(18 + sp) * W]);
             v = C::decode(q[(sp * 9 + pln) * W], wgt<R>(i), rs);
         }
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v = halfwarp_density<C>(v);
         if ((lane & 15) == 0) reinterpret_cast<R*>(&wr[sl][col])[sp] = (lk & kSolid) ? (sp ? P.rw1 : P.rw0) : v;
     };
     auto halos = [&](int jm, int jc, int jp, int sl) {
@@ -243,6 +235,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
         if (t == 0) produce(NS - 1);
         R cur[2][9], nxt[2][9];
         R rc0 = R(0), rc1 = R(0), rn0 = R(0), rn1 = R(0);
+        R lc0 = R(0), lc1 = R(0), ln0 = R(0), ln1 = R(0);
         bool solid_cur = true, solid_nxt = true;
         const int c = lane + 1;                         // this lane's column in the warp ring
 
@@ -251,15 +244,15 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
         wait_full(1);
         wait_full(2);
         if (rho_col) {
-            R tmp[2][9], a, b;
-            pull(0, 1, 2, wi, tmp, a, b);
+            R tmp[2][9], a, b, la, lb;
+            pull(0, 1, 2, wi, tmp, a, b, la, lb);
             wr[slot(y0 - 1)][c] = make_pair_of<R>(a, b);
         }
         halos(0, 1, 2, slot(y0 - 1));
         release(0);
         wait_full(3);
         if (rho_col) {
-            solid_cur = pull(1, 2, 3, wi, cur, rc0, rc1);
+            solid_cur = pull(1, 2, 3, wi, cur, rc0, rc1, lc0, lc1);
             wr[slot(y0)][c] = make_pair_of<R>(rc0, rc1);
         }
         halos(1, 2, 3, slot(y0));
@@ -271,7 +264,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
             const int sn = slot(r + 1);
             wait_full(j + 2);
             if (rho_col) {
-                solid_nxt = pull(j, j + 1, j + 2, wi, nxt, rn0, rn1);
+                solid_nxt = pull(j, j + 1, j + 2, wi, nxt, rn0, rn1, ln0, ln1);
                 wr[sn][c] = make_pair_of<R>(rn0, rn1);
             }
             halos(j, j + 1, j + 2, sn);
@@ -292,7 +285,7 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
                     nb[0][6] = sw.x; nb[1][6] = sw.y;
                     nb[0][7] = se.x; nb[1][7] = se.y;
                 }
-                collide_store<S, R>(cur, rc0, rc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx,
+                collide_store<S, R>(cur, rc0, rc1, lc0, lc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx,
                                     grid.periodic_x, ob);
             }
             // the ring slot of row r - 1 is rewritten two iterations later,
@@ -303,6 +296,8 @@ __global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : 4))
                 for (int i = 0; i < 9; i++) cur[a][i] = nxt[a][i];
             rc0 = rn0;
             rc1 = rn1;
+            lc0 = ln0;
+            lc1 = ln1;
             solid_cur = solid_nxt;
         }
     }

@@ -20,8 +20,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgb300lbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5
-LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S = 0, 1, 2, 3
-PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S}
+LBM_FP64, LBM_FP32, LBM_FP16S, LBM_BF16S, LBM_FP32C = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16s": LBM_FP16S, "bf16s": LBM_BF16S, "fp32c": LBM_FP32C}
 
 # symbols declared in include/lbm.h
 EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "lbm_get_fields",

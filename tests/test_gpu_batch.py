@@ -86,9 +86,10 @@ def test_batch_regularized_matches_oracle(lbm):
         np.testing.assert_allclose(f_b, P.run(P.init(d["rho_init"]), 40), rtol=0, atol=1e-12)
 
 
-def test_batch_steps_fp32_match_oracle(lbm):
+@pytest.mark.parametrize("precision", ["fp32", "fp32c"])
+def test_batch_steps_fp32_match_oracle(lbm, precision):
     inst = uneven_instances()[:2]
-    b = lbm.Batch(inst, precision="fp32")
+    b = lbm.Batch(inst, precision=precision)
     try:
         b.step(30)
         got = [b.save(i) for i in range(len(inst))]
@@ -102,7 +103,7 @@ def test_batch_steps_fp32_match_oracle(lbm):
 
 
 @pytest.mark.parametrize("rows", [None, 1, 3, 8, 64])
-@pytest.mark.parametrize("precision,atol", [("fp32", 2e-5), ("fp16s", 2e-3)])
+@pytest.mark.parametrize("precision,atol", [("fp32", 2e-5), ("fp32c", 2e-5), ("fp16s", 2e-3)])
 def test_staged_batch_tiles_match_oracle(lbm, rows, precision, atol, monkeypatch):
     """FP32 and FP16-shifted batches step with the staged (TMA) march over
     tiles of 128 columns x R rows holding fluid: with R chosen by the
