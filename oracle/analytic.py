@@ -122,9 +122,3 @@ def taylor_green_factor(nu: float, k: float, t):
     equal wavenumbers k in x and y."""
     return np.exp(-2.0 * nu * k * k * np.asarray(t, dtype=np.float64))
 
-
-def mean_field_coexistence_g(rho_hi: float, rho_lo: float) -> float:
-    """|G| of the continuum mean-field coexistence of a symmetric binary
-    mixture with ideal-gas species and the interaction of
-    Eq. (comp_interaction): ln(rho_hi/rho_lo) = |G| (rho_hi - rho_lo)."""
-    return math.log(rho_hi / rho_lo) / (rho_hi - rho_lo)

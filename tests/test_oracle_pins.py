@@ -334,34 +334,149 @@ def test_layered_poiseuille_reduces_to_parabola():
     assert mc * du_in == pytest.approx(mo * du_out, rel=1e-3)
 
 
+def diffuse_layered_reference(rho_o, rho_w, tau, g):
+    """Steady velocity of force-driven flow between walls for a given
+    layered density profile (rows 0..n-1 of fluid, walls half a node
+    outside them), from the 1-D momentum balance of the continuum limit:
+    the shear stress at the face between rows k and k + 1 equals the force
+    density g (rho^o + rho^w) summed from that face to the centre line, the
+    velocity gradient there is that stress over mu = rho nu_mix (face
+    average), and the velocity of the wall row is its stress times half a
+    node over mu, plus the closed-form halfway bounce-back slip
+    g [(2 tau_mix - 1)^2 - 3/4] / (6 nu_mix) of the wall row's mixture.  The
+    interface enters only through the measured densities: no sharp-interface
+    assumption."""
+    rt = rho_o + rho_w
+    nu = [analytic.bgk_viscosity(t) for t in tau]
+    nu_mix = (rho_o * nu[0] + rho_w * nu[1]) / rt
+    mu = rt * nu_mix
+    force = g * rt
+    cum = np.cumsum(force)
+    stress = -(cum[:-1] - 0.5 * cum[-1])
+    u = np.concatenate([[0.0], np.cumsum(stress / (0.5 * (mu[1:] + mu[:-1])))])
+    tau_w = nu_mix[0] / T0 + 0.5
+    slip = g * ((2.0 * tau_w - 1.0) ** 2 - 0.75) / (6.0 * nu_mix[0])
+    return u + 0.5 * (0.5 * cum[-1]) / mu[0] + slip
+
+
 @pytest.mark.parametrize("tau_core,tau_wall", [(1.0, 1.0), (1.5, 1.0), (1.0, 0.85)])
 def test_layered_poiseuille_two_components(tau_core, tau_wall):
     """Section 3.2: steady force-driven flow of an oil core between water wall
-    layers (64 fluid rows, layers 12 rows thick) matches the analytic layered
-    profile with mu = rho nu_mix of each layer's bulk to 5 % in relative L2.
-    The remainder is the diffuse interface (a few nodes wide) and does not
-    shrink with more steps: the profile is converged at 30 000 steps.  A sign
-    error in the forcing, a wrong mixture viscosity or a missing body-force
-    term each move it far outside the bound."""
+    layers (64 fluid rows, layers 12 rows thick).
+
+    Reference: the 1-D momentum balance integrated over the oracle's own
+    density profile with the mixture viscosity of Section 2, plus the
+    pinned halfway bounce-back slip (diffuse_layered_reference).  What is
+    left is bounded piece by piece:
+    * inside each bulk layer the profile is a parabola, on which a
+      second-order lattice scheme is exact: in the wall layer (away from the
+      interface) the velocity matches to 1e-3 of the centre velocity, and in
+      the core the discrete curvature is -g / nu_mix to 1e-3;
+    * across each interface the scheme's second-order remainder acts on a
+      transition of width w (the tanh width of Eq. den-fitting, fitted):
+      the central-difference remainder is dx^2 / 24 times the third
+      derivative, which on a tanh of width w is at most 4 / w^2 times the
+      first, so relative to the velocity increment du_i across the
+      interface zone the offset left is at most du_i (dx / w)^2 / 6.
+    The sharp-interface closed form (analytic.layered_poiseuille) is within
+    5 % in relative L2 for context; the diffuse reference explains that gap
+    (the total density dips by about 25 % inside the interface)."""
     width, outer, g = 64, 12, 1e-6
     mask = wl.straight_channel(2, width)
     rho = wl.layered_channel(2, width, outer, core_species=0)
     P = oracle.Problem(mask, tau=(tau_core, tau_wall), G=G_REPULSIVE, rho_wall=(0.03, 1.0), g=(g, 0.0),
                        periodic=(True, False))
     r, u, _ = P.fields(P.run(P.init(rho), 30000))
-    ux, rt = u[0, 1:-1, 0], r[:, 1:-1, 0]
-    nu = analytic.bgk_viscosity
-
-    def mu(row):
-        ro, rw = rt[0, row], rt[1, row]
-        return (ro + rw) * (ro * nu(tau_core) + rw * nu(tau_wall)) / (ro + rw)
-
+    ux, ro, rw = u[0, 1:-1, 0], r[0, 1:-1, 0], r[1, 1:-1, 0]
+    rt = ro + rw
+    ref = diffuse_layered_reference(ro, rw, (tau_core, tau_wall), g)
+    umax = ref.max()
+    # wall layer, rows 0..6 (the interface zone starts near row 9)
+    assert np.max(np.abs(ux[:7] - ref[:7])) <= 1e-3 * umax
+    # core, rows 20..43: parabola of the core fluid's viscosity
+    nu_mix = (ro * analytic.bgk_viscosity(tau_core) + rw * analytic.bgk_viscosity(tau_wall)) / rt
+    core = slice(20, 44)
+    curv = ux[core][2:] - 2 * ux[core][1:-1] + ux[core][:-2]
+    np.testing.assert_allclose(curv, -g / nu_mix[core][1:-1], rtol=1e-3)
+    # interface: width from the tanh fit, increment across the zone where
+    # the total density departs from its bulk value by more than 1 %
+    c1, c2, c3, c4 = analytic.fit_interface(np.arange(0, width // 2), ro[:width // 2], outer)
+    w = 1.0 / abs(c2)
+    zone = np.nonzero(np.abs(rt[:width // 2] / rt[width // 2] - 1.0) > 0.01)[0]
+    du_i = ref[zone.max() + 1] - ref[zone.min() - 1]
+    bound = du_i * (1.0 / w) ** 2 / 6.0
+    assert 1.0 <= w <= 4.0, w
+    assert np.max(np.abs(ux - ref)) <= bound, (np.max(np.abs(ux - ref)) / umax, bound / umax)
+    # the sharp closed form, for context
     y = np.arange(1, width + 1) - (width + 1) / 2.0
-    u_an = analytic.layered_poiseuille(y, width / 2.0, width / 2.0 - outer, g * rt.sum(axis=0).mean(),
-                                       mu(5), mu(width // 2))
+    mu = rt * nu_mix
+    u_an = analytic.layered_poiseuille(y, width / 2.0, width / 2.0 - outer, g * rt.mean(), mu[4], mu[width // 2])
     assert np.linalg.norm(ux - u_an) / np.linalg.norm(u_an) < 0.05
     assert np.all(ux > 0)
     assert np.max(np.abs(u[1])) < 1e-3 * ux.max()
+
+
+# ----------------------------------------------------------------------------
+# the per-node step, the interaction strength, the interface fit
+# ----------------------------------------------------------------------------
+def _random_state(P, seed):
+    """A state a few steps away from a random mixture (non-equilibrium
+    populations everywhere), stored post-collision."""
+    rho = wl.random_perturbed(P.nx, P.ny, seed=seed, amp=0.3)
+    return P.run(P.init(rho), 3)
+
+
+@pytest.mark.parametrize("case", ["periodic_box", "walled_channel"])
+def test_step_nodes_equals_step(case):
+    """oracle_step_nodes (neighbour densities recomputed per node) writes at
+    every node exactly what oracle_step (density field first) writes: a
+    periodic box with a body force, and a sinusoidal channel with walls, wall
+    potentials of both species and the regularised collision."""
+    if case == "periodic_box":
+        mask = wl.periodic_box(23, 17)
+        P = oracle.Problem(mask, tau=(0.9, 1.3), G=G_REPULSIVE, g=(1e-4, -2e-5))
+    else:
+        mask = wl.sinusoidal_channel(40, 20, 6.0, 3.0, 20.0)
+        P = oracle.Problem(mask, tau=(1.0, 0.8), G=G_REPULSIVE, rho_wall=(0.6, 0.1), g=(2e-5, 0.0),
+                           periodic=(True, False), collision="regularized")
+    f = _random_state(P, seed=11)
+    full, _ = P.step(f)
+    ys, xs = np.mgrid[0:P.ny, 0:P.nx]
+    nodes = P.step_nodes(f, xs.ravel(), ys.ravel())          # [k, 2, 9]
+    got = nodes.reshape(P.ny, P.nx, 2, 9).transpose(2, 3, 0, 1)
+    np.testing.assert_allclose(got, full, rtol=0, atol=1e-15)
+
+
+def test_flat_interface_coexistence_at_the_chosen_g():
+    """The interaction strength G = -1.79 is fixed by the bulk densities the
+    workloads start from (1.0 and 0.03): a flat interface (128 x 4,
+    tau = 1, 20 000 steps) relaxes to a majority density within 2 % of 1.0
+    and a majority/minority ratio within 1 % of 1/0.03 in each phase, the
+    two phases mirror images of each other.  A 10 % weaker interaction
+    moves the ratio by more than 10 %, so the check fixes |G|."""
+    def bulk(G):
+        P = oracle.Problem(wl.periodic_box(128, 4), tau=(1.0, 1.0), G=G)
+        r, _, _ = P.fields(P.run(P.init(wl.flat_interface(128, 4)), 20000))
+        return r[0, 2, 64], r[1, 2, 64], r[0, 2, 0], r[1, 2, 0]      # oil phase, water phase
+    oo, ow, wo, ww = bulk(G_REPULSIVE)
+    assert oo == pytest.approx(1.0, rel=0.02) and ww == pytest.approx(oo, rel=1e-9)
+    assert oo / ow == pytest.approx(1.0 / 0.03, rel=0.01)
+    assert ww / wo == pytest.approx(1.0 / 0.03, rel=0.01)
+    oo2, ow2, _, _ = bulk(0.9 * G_REPULSIVE)
+    assert abs(oo2 / ow2 - 1.0 / 0.03) > 0.1 / 0.03
+
+
+@pytest.mark.parametrize("R,cx,cy", [(17.3, 64.0, 64.0), (9.71, 40.0, 41.0), (24.05, 63.0, 60.0)])
+def test_droplet_radius_of_a_synthetic_tanh_disc(R, cx, cy):
+    """droplet_radius on a disc whose density is exactly the tanh profile
+    of Eq. (den-fitting) around a known radius (width 2, the workloads'
+    droplet) gives that radius to 1e-3; fit_interface gives the profile's
+    own constants (amplitude, inverse width, position, mean)."""
+    rho = wl.droplet(128, 128, R, cx, cy)
+    assert analytic.droplet_radius(rho[0], cx, cy) == pytest.approx(R, abs=1e-3)
+    xs = np.arange(int(cx + R) - 7, int(cx + R) + 8)          # one interface only
+    c1, c2, c3, c4 = analytic.fit_interface(xs, rho[0][int(cy), xs], cx + R)
+    assert (c1, c2, c3, c4) == pytest.approx((-0.485, 0.5, cx + R, 0.515), abs=1e-6)
 
 
 # ----------------------------------------------------------------------------
