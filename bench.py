@@ -143,9 +143,16 @@ class ClockSampler:
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k] == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows), "in_timed_region": inside}
+        out = {"sm_mhz": statistics.median(sm) if sm else None,
+               "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+               "samples": len(rows), "in_timed_region": inside}
+        if not inside:
+            # the timed region was shorter than the sampling period: the
+            # summary is of the samples around it, not inside it
+            out["too_short_to_sample"] = True
+            if t0 is not None and t1 is not None:
+                out["timed_region_s"] = t1 - t0
+        return out
 
 
 def dist_env():

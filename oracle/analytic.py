@@ -13,8 +13,6 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 T0 = 1.0 / 3.0

@@ -34,6 +34,8 @@ def test_clock_summary_keeps_the_timed_region():
     s = c.stop(10.0, 11.0)
     assert s["samples"] == 4 and not s["in_timed_region"]
     assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert s["too_short_to_sample"] and s["timed_region_s"] == 1.0
+    assert "too_short_to_sample" not in c.stop(1.5, 3.0)
 
 
 def test_recorded_traffic_needs_the_same_kernel(tmp_path, monkeypatch):
