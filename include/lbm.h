@@ -191,9 +191,15 @@ int lbm_wait_selftest(void *cuda_stream, double *seconds);
  *         nodes (solid nodes are not written)
  *   obs   device lbm_obs receiving this step's observables (step = 1,
  *         oil_disp_x = this step's displacement), or NULL
- *   p     host parameters: precision must be LBM_FP32; nx * ny <= 2097152;
- *         p->cuda_stream is the stream of all work; variant and workspace
- *         fields are ignored
+ *   p     host parameters: precision must be LBM_FP32; nx * ny <= 2097152
+ *         (any shape within that, e.g. 1 x 2097152); tau, G, g and rho_wall
+ *         are checked as in lbm_create; p->cuda_stream is the stream of all
+ *         work; variant and workspace fields are ignored
+ * Pulls and force neighbours always wrap in both directions: periodic_x and
+ * periodic_y are ignored, and the mask cannot be checked on the host (it is
+ * device memory).  For a direction meant to be closed, keep its first and
+ * last line solid, as lbm_create requires; a fluid node on such a line
+ * would be stepped as if the lattice were periodic there.
  * The scratch is one static device array of 4 MiB + 1 KiB that every GPU
  * which loads this library holds until the process exits.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress) with
@@ -329,6 +335,138 @@ int lbm_mlp_train(lbm_mlp_t *h, const float *x, const float *y, int32_t n, int32
                   float lr, uint64_t seed, float *last_loss);
 void lbm_mlp_destroy(lbm_mlp_t *h);
 const char *lbm_mlp_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * The paper's question from channel descriptions (Sections 3.1, 3.3, 3.4)
+ *
+ * Section 3.4 states the problem as: a periodic sinusoidal channel holds an
+ * oil slug in water; for the channel's geometry, the slug's length, the
+ * wall's wettability (a contact angle) and the two viscosities, find the
+ * homogeneous body force g at which the static slug starts to move, and
+ * report it as a Bond number Bo = rho g L D / sigma (Eq. Bo_number).  The
+ * calls below take exactly that description and do every set-up step in the
+ * library.  Readings fixed here (the paper leaves them open): planar 2-D
+ * channel, fluid iff |y - y_c| <= h(x) = h0 - A cos(2 pi x / lambda) with
+ * h0 = 0.1875 lambda, n_periods periods, height 2 ceil(h0 + A) + 2, slug
+ * centred on the neck at x = lambda floor(n_periods / 2) with tanh ends of
+ * width 2 (densities 1.0 / 0.03); G = -1.79; tau^w = 1 and
+ * tau^o = max(3 r nu^w + 1/2, 0.75) for the viscosity ratio r = nu^o / nu^w;
+ * "moving" = the oil centre of mass travels more than lambda / 2 in one
+ * probe window; L = nx (the periodic length), D = h0 - A (the neck
+ * half-width).  Host arrays in and out; errors of these calls are read with
+ * lbm_channel_last_error().
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t lambda;               /* wavelength in nodes, 8 .. 65536 */
+    double amp_ratio;             /* A / h0, in [0, 0.95] */
+    double slug_len_over_lambda;  /* slug length / lambda, in (0, n_periods - 1] */
+    double theta_deg;             /* contact angle through water, in (0, 180) degrees */
+    double visc_ratio;            /* nu^o / nu^w, > 0 */
+    int32_t n_periods;            /* periods along x, 2 .. 64 (0 = 4) */
+} lbm_channel_spec;
+
+/* Lattice size of a channel: nx = lambda n_periods, ny = 2 ceil(h0 + A) + 2.
+ * LBM_EINVAL for a spec out of range. */
+int lbm_channel_shape(const lbm_channel_spec *s, int32_t *nx, int32_t *ny);
+
+/* Wall mask (host uint8 [ny][nx], 1 = solid) and initial densities (host
+ * double [2][ny][nx]) of a channel with its slug; either pointer may be NULL.
+ * No GPU work. */
+int lbm_channel_geometry(const lbm_channel_spec *s, uint8_t *mask, double *rho_init);
+
+/* Section 3.3 on the GPU: the contact angle (degrees, through water) of a
+ * slug between flat plates H = 32 apart (192 columns, periodic in x, oil
+ * over the middle half, tau = 1, G = -1.79), after `steps` steps, for each
+ * signed wall potential r[i] (r > 0: rho_s^w = r, r < 0: rho_s^o = -r;
+ * |r| <= 2).  Interface points where the oil fraction crosses 1/2 on every
+ * row at least 3 rows from a wall, Pratt's algebraic circle fit,
+ * Eq. (contact_angle); theta[i] is the mean of the slug's two ends.  All n
+ * slugs run as one batch in `precision`, on cuda_stream (NULL = legacy
+ * default). */
+int lbm_wetting_calibrate(const double *r, int32_t n, int64_t steps, int32_t precision, void *cuda_stream,
+                          double *theta);
+
+/* Section 3.1 on the GPU: surface tension of the model (G = -1.79, tau = 1)
+ * from the Laplace law over four static droplets (R = 12, 16, 20, 24 in a
+ * 128 x 128 periodic box, `steps` steps): radius from where rho^o crosses
+ * its mid value along the central row and column, pressure jump between
+ * the centre and the far corner from p = T0 rho - G T0 rho^o rho^w, least
+ * squares dp = sigma / R + c.  *rho_bulk = rho^o + rho^w in the middle of
+ * a phase of a flat interface (two bands in a periodic 128 x 4 strip, run
+ * in the same batch): the bulk total density at zero curvature. */
+int lbm_surface_tension(int64_t steps, int32_t precision, void *cuda_stream, double *sigma, double *rho_bulk);
+
+/* Section 3.4, planar form (host, FP64): rho g_crit L / sigma of a slug of
+ * oil area `area` in a channel h(x) = h0 - amp cos(2 pi x / lam), resting
+ * with its rear contact line near x_rest, contact angle theta_deg through
+ * water.  Menisci are arcs centred on the axis meeting the wall (inclined
+ * by atan h'(x)) at theta; at rest rho g L equals sigma times the front
+ * curvature minus the rear one; the front follows the rear by conservation
+ * of the oil area (the channel between the contact chords plus the circular
+ * segments beyond them); loaded quasi-statically the slug climbs each
+ * rising branch of that balance and jumps ahead past each local maximum,
+ * and it counts as moving at the first jump longer than lam / 2.  0 when
+ * the channel offers no capillary resistance. */
+int lbm_planar_critical_balance(double theta_deg, double area, double h0, double amp, double lam, double x_rest,
+                                double *balance);
+
+/* Contact angle (degrees, through water) of one end of a slug between flat
+ * plates with fluid rows y_lo..y_hi, from host densities rho [2][ny][nx]
+ * (host, FP64): the measurement inside lbm_wetting_calibrate.  right = 1:
+ * the slug's right end, 0: its left end.  LBM_EINVAL when fewer than three
+ * rows show an interface. */
+int lbm_contact_angle(const double *rho, int32_t nx, int32_t ny, int32_t y_lo, int32_t y_hi, int32_t right,
+                      double *theta);
+
+/* Wall potentials (rho_s^o, rho_s^w) whose calibrated contact angle is
+ * theta_deg, from a table r[n] (ascending) -> theta[n] (descending): linear
+ * interpolation of r in theta, clipped to the table's range, then r > 0 ->
+ * rho_s^w = r, r < 0 -> rho_s^o = -r (host). */
+int lbm_wall_potentials(const double *r, const double *theta, int32_t n, double theta_deg, double *rho_wall);
+
+typedef struct {
+    double rel_bracket;          /* stop at (g_hi - g_lo) <= rel_bracket g_hi (<= 0: 0.02) */
+    int64_t t_eq, t_obs;         /* steps at g = 0 before the probes; steps per probe (>= 1) */
+    int32_t max_probes;          /* per channel, bracket checks included (<= 0: 24) */
+    int32_t precision;           /* storage of the channels' populations (lbm_precision) */
+    int32_t collision;           /* as lbm_params.collision (1, regularised, keeps low tau stable) */
+    int32_t use_surrogate;       /* 1: start from the surrogate's bracket */
+    lbm_mlp_t *surrogate;        /* the network (use_surrogate = 1) */
+    float feature_mean[5];       /* feature normalisation the network was trained with: */
+    float feature_std[5];        /*   x = (features - mean) / std (std 0 taken as 1) */
+    double k_sigma;              /* surrogate bracket exp(mu -+ k_sigma sigma) (<= 0: 2), at least 5 % wide */
+    double bracket_lo, bracket_hi; /* otherwise: these factors of the planar balance's force (<= 0: 0.5, 2) */
+    const double *calib_r;       /* calibration table (ascending r, descending theta), or */
+    const double *calib_theta;   /*   calib_n = 0: the library runs lbm_wetting_calibrate */
+    int32_t calib_n;             /*   over 13 potentials in [-0.6, 0.6] (20 000 FP32 steps, cached) */
+    double sigma, rho_bulk;      /* of the Bond number; <= 0: lbm_surface_tension (6000 FP32 steps, cached) */
+    double timeout_s;            /* host wall-clock limit of the bisection (<= 0: none) */
+    void *cuda_stream;           /* stream of all GPU work, or NULL */
+} lbm_channel_opts;
+
+typedef struct {
+    double g_lo, g_hi;           /* final bracket: static at g_lo, moving at g_hi */
+    double bo_lo, bo_hi;         /* the same as Bond numbers rho g L D / sigma */
+    double g_start_lo, g_start_hi; /* starting bracket (planar balance or surrogate) */
+    double g_analytic;           /* planar balance's critical force of the initial fill */
+    double rho_wall[2];          /* wall potentials used */
+    double tau[2];               /* relaxation times used */
+    double sigma, rho_bulk;      /* of the Bond number */
+    int32_t nx, ny;              /* lattice of the channel */
+    int32_t probes;              /* probe windows taken */
+    int32_t status;              /* as lbm_crit_result.status */
+} lbm_channel_result;
+
+/* Bisect the critical body force of every channel (all in one batch, one
+ * launch per step, decisions in FP64 on the device): channel and slug from
+ * the spec, wall potentials for theta from the calibration table, tau from
+ * the viscosity ratio, starting bracket from the planar balance (bracket
+ * checks widen it when wrong) or the surrogate, then
+ * lbm_critical_pressure_batch.  Returns LBM_ETIMEOUT (results filled) when
+ * timeout_s ran out. */
+int lbm_critical_pressure_channels(const lbm_channel_spec *specs, int32_t n, const lbm_channel_opts *o,
+                                   lbm_channel_result *out);
+const char *lbm_channel_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -19,8 +19,11 @@ LIB = os.path.join(HERE, "libgb300lbm.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: no contraction of a * b + c into fused multiply-adds, so that
+# host arithmetic rounds the same on x86-64 and on AArch64 (where the
+# compiler would otherwise fuse)
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-I", INCLUDE]
+         "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-I", INCLUDE]
 
 
 def nvcc() -> str:

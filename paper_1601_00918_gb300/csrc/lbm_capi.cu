@@ -1079,27 +1079,29 @@ unsigned char* g_noalloc_ptr[kMaxDevices] = {};
 static_assert(sizeof(StepParams) + sizeof(ObsAccum) + sizeof(ObsState) <= kNoAllocHead, "scratch head");
 
 // Link words of a dense [ny][nx] lattice (no ghost columns), plus the
-// parameters and cleared accumulators, into the scratch.
+// parameters and cleared accumulators, into the scratch.  Rows are visited
+// grid-stride in y, so any admitted shape launches with gridDim.y <= 65535.
 __global__ void noalloc_prepare_kernel(const uint8_t* __restrict__ mask, unsigned char* __restrict__ scratch, int nx,
                                        int ny, StepParams prm) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
-    if (x == 0 && y == 0) {
+    if (x == 0 && blockIdx.y == 0) {
         *(StepParams*)scratch = prm;
         ObsAccum* acc = (ObsAccum*)(scratch + sizeof(StepParams));
         ObsState* obs = (ObsState*)(scratch + sizeof(StepParams) + sizeof(ObsAccum));
         memset(acc, 0, sizeof(ObsAccum));
         memset(obs, 0, sizeof(ObsState));
     }
-    if (x >= nx || y >= ny) return;
-    unsigned w = mask[y * nx + x] ? (1u << kSolidBit) : 0u;
-    for (int i = 1; i < 9; i++) {
-        int sx = x - d2q9_cx(i), sy = y - d2q9_cy(i);
-        sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-        sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-        if (mask[sy * nx + sx]) w |= 1u << i;
+    if (x >= nx) return;
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        unsigned w = mask[y * nx + x] ? (1u << kSolidBit) : 0u;
+        for (int i = 1; i < 9; i++) {
+            int sx = x - d2q9_cx(i), sy = y - d2q9_cy(i);
+            sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+            if (mask[sy * nx + sx]) w |= 1u << i;
+        }
+        ((uint16_t*)(scratch + kNoAllocHead))[y * nx + x] = uint16_t(w);
     }
-    ((uint16_t*)(scratch + kNoAllocHead))[y * nx + x] = uint16_t(w);
 }
 
 __global__ void noalloc_obs_kernel(const unsigned char* __restrict__ scratch, lbm_obs* __restrict__ out) {
@@ -1126,7 +1128,11 @@ extern "C" int lbm_step_noalloc(const uint8_t* mask, const float* f_in, float* f
     if (p->eq_order != 2 && p->eq_order != 3) return fail(nullptr, LBM_EINVAL, "eq_order must be 2 or 3");
     if (p->collision != 0 && p->collision != 1) return fail(nullptr, LBM_EINVAL, "collision must be 0 or 1");
     for (int a = 0; a < 2; a++)
-        if (!(p->tau[a] > 0.5)) return fail(nullptr, LBM_EINVAL, "tau[%d] must exceed 1/2", a);
+        if (!(p->tau[a] > 0.5) || !std::isfinite(p->tau[a]))
+            return fail(nullptr, LBM_EINVAL, "tau[%d] must be finite and exceed 1/2", a);
+    if (!std::isfinite(p->G) || !std::isfinite(p->g[0]) || !std::isfinite(p->g[1]) ||
+        !std::isfinite(p->rho_wall[0]) || !std::isfinite(p->rho_wall[1]))
+        return fail(nullptr, LBM_EINVAL, "G, g and rho_wall must be finite");
     int dev = 0;
     CUDA_TRY(nullptr, cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, LBM_EINVAL, "device %d out of range", dev);
@@ -1154,14 +1160,16 @@ extern "C" int lbm_step_noalloc(const uint8_t* mask, const float* f_in, float* f
     prm.G = p->G;
     prm.k3 = p->eq_order >= 3 ? 4.5 : 0.0;
     prm.reg = p->collision == 1 ? 1.0 : 0.0;
-    noalloc_prepare_kernel<<<dim3((nx + 127) / 128, ny), 128, 0, st>>>(mask, scratch, nx, ny, prm);
+    noalloc_prepare_kernel<<<dim3((nx + 127) / 128, std::min(ny, 65535)), 128, 0, st>>>(mask, scratch, nx, ny, prm);
     CUDA_TRY(nullptr, cudaGetLastError());
     Grid g;
     g.nx = nx;
     g.ny = ny;
     g.pitch = nx;            // dense rows, no ghost columns
     g.periodic_x = 0;        // no ghost images to write (pulls still wrap)
-    g.rows_per_block = std::max(4, std::min(ny, 32));
+    // rows per CTA strip: 32 (fewer on short grids), more when ny / 32
+    // would exceed the 65535 limit of gridDim.y
+    g.rows_per_block = std::max(std::max(4, std::min(ny, 32)), (ny + 65534) / 65535);
     g.row_begin = 0;
     g.row_end = ny;
     g.strips = 1;

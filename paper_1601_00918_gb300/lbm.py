@@ -30,7 +30,10 @@ EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "l
            "lbm_batch_set_body_force", "lbm_batch_save", "lbm_critical_pressure_batch",
            "lbm_batch_destroy", "lbm_batch_last_error", "lbm_mlp_create", "lbm_mlp_params",
            "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam", "lbm_mlp_train", "lbm_mlp_destroy",
-           "lbm_mlp_last_error", "lbm_step_noalloc", "lbm_wait_selftest", "lbm_batch_kernel_info")
+           "lbm_mlp_last_error", "lbm_step_noalloc", "lbm_wait_selftest", "lbm_batch_kernel_info",
+           "lbm_channel_shape", "lbm_channel_geometry", "lbm_wetting_calibrate", "lbm_surface_tension",
+           "lbm_planar_critical_balance", "lbm_contact_angle", "lbm_wall_potentials",
+           "lbm_critical_pressure_channels", "lbm_channel_last_error")
 
 
 class LbmError(RuntimeError):
@@ -80,6 +83,38 @@ class BisectOpts(ctypes.Structure):
 class CritResult(ctypes.Structure):
     _fields_ = [("g_lo", ctypes.c_double), ("g_hi", ctypes.c_double), ("probes", ctypes.c_int32),
                 ("status", ctypes.c_int32)]
+
+
+class ChannelSpec(ctypes.Structure):
+    _fields_ = [("lam", ctypes.c_int32), ("amp_ratio", ctypes.c_double),
+                ("slug_len_over_lambda", ctypes.c_double), ("theta_deg", ctypes.c_double),
+                ("visc_ratio", ctypes.c_double), ("n_periods", ctypes.c_int32)]
+
+
+class ChannelOpts(ctypes.Structure):
+    _fields_ = [("rel_bracket", ctypes.c_double), ("t_eq", ctypes.c_int64), ("t_obs", ctypes.c_int64),
+                ("max_probes", ctypes.c_int32), ("precision", ctypes.c_int32), ("collision", ctypes.c_int32),
+                ("use_surrogate", ctypes.c_int32), ("surrogate", ctypes.c_void_p),
+                ("feature_mean", ctypes.c_float * 5), ("feature_std", ctypes.c_float * 5),
+                ("k_sigma", ctypes.c_double), ("bracket_lo", ctypes.c_double), ("bracket_hi", ctypes.c_double),
+                ("calib_r", ctypes.POINTER(ctypes.c_double)), ("calib_theta", ctypes.POINTER(ctypes.c_double)),
+                ("calib_n", ctypes.c_int32), ("sigma", ctypes.c_double), ("rho_bulk", ctypes.c_double),
+                ("timeout_s", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+
+
+class ChannelResult(ctypes.Structure):
+    _fields_ = [("g_lo", ctypes.c_double), ("g_hi", ctypes.c_double), ("bo_lo", ctypes.c_double),
+                ("bo_hi", ctypes.c_double), ("g_start_lo", ctypes.c_double), ("g_start_hi", ctypes.c_double),
+                ("g_analytic", ctypes.c_double), ("rho_wall", ctypes.c_double * 2), ("tau", ctypes.c_double * 2),
+                ("sigma", ctypes.c_double), ("rho_bulk", ctypes.c_double), ("nx", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("probes", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"g_lo": self.g_lo, "g_hi": self.g_hi, "bo_lo": self.bo_lo, "bo_hi": self.bo_hi,
+                "g_start_lo": self.g_start_lo, "g_start_hi": self.g_start_hi, "g_analytic": self.g_analytic,
+                "rho_wall": (self.rho_wall[0], self.rho_wall[1]), "tau": (self.tau[0], self.tau[1]),
+                "sigma": self.sigma, "rho_bulk": self.rho_bulk, "nx": self.nx, "ny": self.ny,
+                "probes": self.probes, "status": self.status}
 
 
 _lib = None
@@ -135,6 +170,22 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_mlp_last_error.restype = ctypes.c_char_p
     for name in ("lbm_mlp_create", "lbm_mlp_params", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
                  "lbm_mlp_train"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.lbm_channel_shape.argtypes = [P(ChannelSpec), P(ctypes.c_int32), P(ctypes.c_int32)]
+    lib.lbm_channel_geometry.argtypes = [P(ChannelSpec), P(ctypes.c_uint8), dp]
+    lib.lbm_wetting_calibrate.argtypes = [dp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, vp, dp]
+    lib.lbm_surface_tension.argtypes = [ctypes.c_int64, ctypes.c_int32, vp, dp, dp]
+    lib.lbm_planar_critical_balance.argtypes = [ctypes.c_double] * 6 + [dp]
+    lib.lbm_contact_angle.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, dp]
+    lib.lbm_wall_potentials.argtypes = [dp, dp, ctypes.c_int32, ctypes.c_double, dp]
+    lib.lbm_critical_pressure_channels.argtypes = [P(ChannelSpec), ctypes.c_int32, P(ChannelOpts),
+                                                   P(ChannelResult)]
+    lib.lbm_channel_last_error.argtypes = []
+    lib.lbm_channel_last_error.restype = ctypes.c_char_p
+    for name in ("lbm_channel_shape", "lbm_channel_geometry", "lbm_wetting_calibrate", "lbm_surface_tension",
+                 "lbm_planar_critical_balance", "lbm_contact_angle", "lbm_wall_potentials",
+                 "lbm_critical_pressure_channels"):
         getattr(lib, name).restype = ctypes.c_int
     lib.lbm_destroy.argtypes = [vp]
     lib.lbm_destroy.restype = None
@@ -527,3 +578,108 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------
+# the paper's question from channel descriptions (Sections 3.1, 3.3, 3.4)
+# ----------------------------------------------------------------------------
+def _ccheck(rc, ok=(LBM_OK,)):
+    if rc not in ok:
+        raise LbmError(rc, (library().lbm_channel_last_error() or b"").decode())
+    return rc
+
+
+def channel_spec(spec) -> ChannelSpec:
+    """C struct of a channel description (any object with lam, amp_ratio,
+    slug_len_over_lambda, theta_deg, visc_ratio and optionally n_periods)."""
+    return ChannelSpec(int(spec.lam), float(spec.amp_ratio), float(spec.slug_len_over_lambda),
+                       float(spec.theta_deg), float(spec.visc_ratio), int(getattr(spec, "n_periods", 4)))
+
+
+def lbm_channel_geometry(spec):
+    """(mask [ny, nx] uint8, rho_init [2, ny, nx]) of a channel with its slug."""
+    cs = channel_spec(spec)
+    nx, ny = ctypes.c_int32(), ctypes.c_int32()
+    _ccheck(library().lbm_channel_shape(ctypes.byref(cs), ctypes.byref(nx), ctypes.byref(ny)))
+    mask = np.empty((ny.value, nx.value), dtype=np.uint8)
+    rho = np.empty((2, ny.value, nx.value))
+    _ccheck(library().lbm_channel_geometry(ctypes.byref(cs), mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                           _dptr(rho)))
+    return mask, rho
+
+
+def lbm_wetting_calibrate(r_values, steps=20000, precision="fp32", stream=None):
+    r = np.ascontiguousarray(r_values, dtype=np.float64)
+    theta = np.empty_like(r)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _ccheck(library().lbm_wetting_calibrate(_dptr(r), len(r), int(steps), prec,
+                                            ctypes.c_void_p(stream) if stream else None, _dptr(theta)))
+    return theta
+
+
+def lbm_surface_tension(steps=6000, precision="fp32", stream=None):
+    sigma, rho = ctypes.c_double(), ctypes.c_double()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _ccheck(library().lbm_surface_tension(int(steps), prec, ctypes.c_void_p(stream) if stream else None,
+                                          ctypes.byref(sigma), ctypes.byref(rho)))
+    return sigma.value, rho.value
+
+
+def lbm_planar_critical_balance(theta_deg, area, h0, amp, lam, x_rest):
+    out = ctypes.c_double()
+    _ccheck(library().lbm_planar_critical_balance(float(theta_deg), float(area), float(h0), float(amp),
+                                                  float(lam), float(x_rest), ctypes.byref(out)))
+    return out.value
+
+
+def lbm_contact_angle(rho, y_lo, y_hi, right=True):
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    _, ny, nx = rho.shape
+    out = ctypes.c_double()
+    _ccheck(library().lbm_contact_angle(_dptr(rho), nx, ny, int(y_lo), int(y_hi), int(bool(right)),
+                                        ctypes.byref(out)))
+    return out.value
+
+
+def lbm_wall_potentials(r, theta, theta_deg):
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    out = (ctypes.c_double * 2)()
+    _ccheck(library().lbm_wall_potentials(_dptr(r), _dptr(th), len(r), float(theta_deg), out))
+    return (out[0], out[1])
+
+
+def lbm_critical_pressure_channels(specs, precision="fp32", collision="regularized", rel_bracket=0.02,
+                                   t_eq=1000, t_obs=2000, max_probes=24, surrogate=None, feature_mean=None,
+                                   feature_std=None, k_sigma=2.0, bracket=(0.5, 2.0), table=None, sigma=0.0,
+                                   rho_bulk=0.0, timeout_s=0.0, stream=None, check=True):
+    """Bisect the critical body force of every channel description inside
+    the library; returns a list of result dicts (lbm_channel_result)."""
+    n = len(specs)
+    arr = (ChannelSpec * n)(*[channel_spec(s) for s in specs])
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o = ChannelOpts()
+    o.rel_bracket = float(rel_bracket)
+    o.t_eq, o.t_obs, o.max_probes = int(t_eq), int(t_obs), int(max_probes)
+    o.precision, o.collision = prec, _collision_code(collision)
+    keep = []
+    if surrogate is not None:
+        o.use_surrogate = 1
+        o.surrogate = surrogate.h
+        o.feature_mean = (ctypes.c_float * 5)(*[float(v) for v in feature_mean])
+        o.feature_std = (ctypes.c_float * 5)(*[float(v) for v in feature_std])
+        o.k_sigma = float(k_sigma)
+    o.bracket_lo, o.bracket_hi = float(bracket[0]), float(bracket[1])
+    if table is not None:
+        r = np.ascontiguousarray(table.r, dtype=np.float64)
+        th = np.ascontiguousarray(table.theta, dtype=np.float64)
+        keep += [r, th]
+        o.calib_r, o.calib_theta, o.calib_n = _dptr(r), _dptr(th), len(r)
+    o.sigma, o.rho_bulk = float(sigma), float(rho_bulk)
+    o.timeout_s = float(timeout_s)
+    o.cuda_stream = stream
+    out = (ChannelResult * n)()
+    rc = library().lbm_critical_pressure_channels(arr, n, ctypes.byref(o), out)
+    if check:
+        _ccheck(rc, ok=(LBM_OK, LBM_ETIMEOUT))
+    return [r.as_dict() for r in out]

@@ -63,12 +63,14 @@ def wall_potentials(theta_deg: float):
 
 
 def instance_of(spec: wl.ChannelSpec, table=None) -> dict:
-    """Batch instance of a channel spec; `table` (wetting.WettingTable) gives
-    calibrated wall potentials."""
-    w = wl.channel_instance(spec)
+    """Batch instance of a channel spec (channel and slug from the library,
+    lbm_channel_geometry); `table` (wetting.WettingTable) gives calibrated
+    wall potentials."""
+    from . import lbm as _lib
+    mask, rho = _lib.lbm_channel_geometry(spec)
     rw = table.potentials_for(spec.theta_deg) if table is not None else wall_potentials(spec.theta_deg)
-    return dict(mask=w.mask, rho_init=w.rho, tau=relaxation_times(spec.visc_ratio), G=G_INTERACTION,
-                rho_wall=rw, g=(0.0, 0.0), periodic=w.periodic, disp_threshold=0.5 * spec.lam,
+    return dict(mask=mask, rho_init=rho, tau=relaxation_times(spec.visc_ratio), G=G_INTERACTION,
+                rho_wall=rw, g=(0.0, 0.0), periodic=(True, False), disp_threshold=0.5 * spec.lam,
                 collision=COLLISION)
 
 
@@ -164,6 +166,27 @@ def ramp_critical(lbm, specs, g_start, ratio: float = 1.05, n_levels: int = 40, 
     finally:
         b.close()
     return out, time.perf_counter() - t0
+
+
+def run_channels(lbm, specs, precision="fp32", rel_bracket=0.02, t_eq=1000, t_obs=2000, max_probes=24,
+                 timeout_s=0.0, table=None, surrogate=None, scale_x=None, k_sigma=2.0, sigma=None, rho=None):
+    """The whole question inside the library (lbm_critical_pressure_channels):
+    channel and slug, wall potentials from `table` (or the library's own
+    calibration), relaxation times, starting bracket from the planar
+    balance or from `surrogate` (with its feature scaling scale_x = (mean,
+    std)), the batched bisection and the Bond numbers; returns (results,
+    seconds)."""
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    kw = {}
+    if surrogate is not None:
+        kw = dict(surrogate=surrogate, feature_mean=scale_x[0], feature_std=scale_x[1], k_sigma=k_sigma)
+    t0 = time.perf_counter()
+    res = lbm.lbm_critical_pressure_channels(
+        specs, precision=precision, collision=COLLISION, rel_bracket=rel_bracket, t_eq=t_eq, t_obs=t_obs,
+        max_probes=max_probes, table=table, sigma=sigma or 0.0, rho_bulk=rho or 0.0, timeout_s=timeout_s,
+        stream=stream, **kw)
+    return res, time.perf_counter() - t0
 
 
 def run_plain(lbm, specs, g_lo, g_hi, **kw):

@@ -222,10 +222,10 @@ def sweep_specs(n: int, seed: int, lambdas=(128, 192, 256, 384, 512)) -> list:
 def channel_instance(spec: ChannelSpec) -> Workload:
     """Mask and slug fill of one sweep instance: mean half-width h0 =
     0.1875 lambda, amplitude A = amp_ratio h0, n_periods periods, slug centred
-    on the neck at x = 2 lambda."""
+    on the neck at x = lambda floor(n_periods / 2)."""
     nx, ny = spec.nx, spec.ny
     mask = sinusoidal_channel(nx, ny, spec.h0, spec.amp, float(spec.lam))
-    centre = 2.0 * spec.lam
+    centre = float(spec.lam * (spec.n_periods // 2))
     half = 0.5 * spec.slug_len_over_lambda * spec.lam
     rho = slug(nx, ny, centre - half, centre + half)
     return Workload(f"channel_{nx}x{ny}", mask, rho, (True, False))

@@ -1,6 +1,10 @@
-"""Host-side parts of paper_1601_00918_gb300/wetting.py against the oracle's
-capillary tools (no GPU): the contact-angle measurement on synthetic
-interfaces and the planar 2-D critical balance."""
+"""Host-side parts of the wetting and channel calls of the library
+(lbm_contact_angle, lbm_wall_potentials, lbm_planar_critical_balance,
+lbm_channel_geometry; no GPU) through paper_1601_00918_gb300/wetting.py,
+against the oracle's capillary tools and the shared input module: the
+contact-angle measurement on synthetic interfaces, the inversion of the
+calibration table, the planar 2-D critical balance and the channel
+geometry."""
 import math
 
 import numpy as np
@@ -37,15 +41,6 @@ def test_contact_angle_of_synthetic_interfaces(theta_deg):
     assert wetting.contact_angle(ro, rw, 1, 32, "right") == pytest.approx(theta_deg, abs=0.5)
 
 
-def test_circle_through_points():
-    t = np.linspace(-1.0, 0.4, 30)
-    A, B, C, D = wetting.circle_through(5.0 + 25.0 * np.cos(t), 1.5 + 25.0 * np.sin(t))
-    assert (-B / (2 * A), -C / (2 * A), 1.0 / (2 * abs(A))) == pytest.approx((5.0, 1.5, 25.0), abs=1e-8)
-    # collinear points: a line (A = 0)
-    A, B, C, D = wetting.circle_through(np.full(9, 3.0), np.arange(9.0))
-    assert abs(A) < 1e-12 and abs(C) < 1e-9
-
-
 def test_potentials_for_inverts_the_table():
     tab = wetting.WettingTable(np.array([-0.4, 0.0, 0.4]), np.array([135.0, 90.0, 45.0]), 32, 1000)
     assert tab.potentials_for(90.0) == (0.0, 0.0)
@@ -60,3 +55,19 @@ def test_potentials_for_inverts_the_table():
 def test_critical_balance_matches_the_oracle(theta_deg, area, x_rest):
     ref = cap.critical_force(math.radians(theta_deg), area, 12.0, 6.0, 64.0, x_rest)[0]
     assert wetting.critical_balance(theta_deg, area, 12.0, 6.0, 64.0, x_rest) == pytest.approx(ref, rel=2e-3)
+
+
+@pytest.mark.parametrize("lam,ratio,slug,periods", [(32, 0.2, 1.0, 4), (64, 0.5, 1.5, 4), (128, 0.6, 2.0, 4),
+                                                    (48, 0.37, 1.3, 3), (40, 0.0, 0.8, 2)])
+def test_channel_geometry_is_the_input_module_channel(lam, ratio, slug, periods):
+    """lbm_channel_geometry builds the same channel and slug as the shared
+    input module (workloads.channel_instance): the mask exactly, the
+    densities to the rounding of tanh."""
+    from paper_1601_00918_gb300 import lbm
+    from paper_1601_00918_gb300 import workloads as wl
+    spec = wl.ChannelSpec(lam=lam, amp_ratio=ratio, slug_len_over_lambda=slug, theta_deg=70.0, visc_ratio=2.0,
+                          n_periods=periods)
+    mask, rho = lbm.lbm_channel_geometry(spec)
+    w = wl.channel_instance(spec)
+    np.testing.assert_array_equal(mask, w.mask)
+    np.testing.assert_allclose(rho, w.rho, rtol=0, atol=1e-15)
