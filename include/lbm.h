@@ -347,9 +347,10 @@ const char *lbm_mlp_last_error(void);
  * calls below take exactly that description and do every set-up step in the
  * library.  Readings fixed here (the paper leaves them open): planar 2-D
  * channel, fluid iff |y - y_c| <= h(x) = h0 - A cos(2 pi x / lambda) with
- * h0 = 0.1875 lambda, n_periods periods, height 2 ceil(h0 + A) + 2, slug
- * centred on the neck at x = lambda floor(n_periods / 2) with tanh ends of
- * width 2 (densities 1.0 / 0.03); G = -1.79; tau^w = 1 and
+ * h0 = 0.1875 lambda, n_periods periods, height 2 ceil(h0 + A) + 2, n_slugs
+ * identical slugs on equally spaced necks (one slug: the neck at
+ * x = lambda floor(n_periods / 2)) with tanh ends of width 2 (densities
+ * 1.0 / 0.03); G = -1.79; tau^w = 1 and
  * tau^o = max(3 r nu^w + 1/2, 0.75) for the viscosity ratio r = nu^o / nu^w;
  * "moving" = the oil centre of mass travels more than lambda / 2 in one
  * probe window; L = nx (the periodic length), D = h0 - A (the neck
@@ -363,6 +364,10 @@ typedef struct {
     double theta_deg;             /* contact angle through water, in (0, 180) degrees */
     double visc_ratio;            /* nu^o / nu^w, > 0 */
     int32_t n_periods;            /* periods along x, 2 .. 64 (0 = 4) */
+    int32_t n_slugs;              /* identical slugs (0 = 1), dividing n_periods; slug k is centred on
+                                     the neck at x = lambda (n_periods / (2 n_slugs) + k n_periods / n_slugs);
+                                     each slug at most n_periods / n_slugs - 1/4 wavelengths long (one
+                                     slug: n_periods - 1) */
 } lbm_channel_spec;
 
 /* Lattice size of a channel: nx = lambda n_periods, ny = 2 ceil(h0 + A) + 2.
@@ -448,7 +453,8 @@ typedef struct {
     double g_lo, g_hi;           /* final bracket: static at g_lo, moving at g_hi */
     double bo_lo, bo_hi;         /* the same as Bond numbers rho g L D / sigma */
     double g_start_lo, g_start_hi; /* starting bracket (planar balance or surrogate) */
-    double g_analytic;           /* planar balance's critical force of the initial fill */
+    double g_analytic;           /* planar balance's critical force of the initial fill (n_slugs times
+                                    one slug's: every slug holds the same capillary balance) */
     double rho_wall[2];          /* wall potentials used */
     double tau[2];               /* relaxation times used */
     double sigma, rho_bulk;      /* of the Bond number */

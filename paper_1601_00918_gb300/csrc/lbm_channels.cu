@@ -68,16 +68,19 @@ int cfail(int code, const char* fmt, ...) {
 // ---------------------------------------------------------------------------
 struct Geom {
     int nx, ny;
-    double lam, h0, amp, yc, centre, half;
+    int slugs;            // identical slugs, centred on necks spaced n_periods / slugs apart
+    double lam, h0, amp, yc, centre, half, spacing;
 };
 
 int periods_of(const lbm_channel_spec& s) { return s.n_periods > 0 ? s.n_periods : 4; }
+int slugs_of(const lbm_channel_spec& s) { return s.n_slugs > 0 ? s.n_slugs : 1; }
 
 bool geom_of(const lbm_channel_spec& s, Geom* g) {
-    const int np = periods_of(s);
+    const int np = periods_of(s), ns = slugs_of(s);
     if (s.lambda < 8 || s.lambda > (1 << 16) || np < 2 || np > 64) return false;
+    if (ns > np || np % ns != 0) return false;
     if (!(s.amp_ratio >= 0.0 && s.amp_ratio <= 0.95)) return false;
-    if (!(s.slug_len_over_lambda > 0.0 && s.slug_len_over_lambda <= np - 1.0)) return false;
+    if (!(s.slug_len_over_lambda > 0.0 && s.slug_len_over_lambda <= np / ns - (ns > 1 ? 0.25 : 1.0))) return false;
     if (!(s.theta_deg > 0.0 && s.theta_deg < 180.0) || !(s.visc_ratio > 0.0) || !std::isfinite(s.visc_ratio))
         return false;
     g->lam = (double)s.lambda;
@@ -86,7 +89,9 @@ bool geom_of(const lbm_channel_spec& s, Geom* g) {
     g->nx = s.lambda * np;
     g->ny = 2 * (int)std::ceil(g->h0 + g->amp) + 2;
     g->yc = (g->ny - 1) / 2.0;
-    g->centre = g->lam * (np / 2);
+    g->slugs = ns;
+    g->spacing = g->lam * (np / ns);
+    g->centre = g->lam * (np / (2 * ns));      // the first slug; the others follow every `spacing`
     g->half = 0.5 * s.slug_len_over_lambda * g->lam;
     return true;
 }
@@ -104,7 +109,11 @@ void fill(const Geom& g, uint8_t* mask, double* rho) {
             const size_t k = (size_t)y * g.nx + x;
             if (mask) mask[k] = solid ? 1 : 0;
             if (rho) {
-                const double sl = step2(x - (g.centre - g.half)) - step2(x - (g.centre + g.half));
+                double sl = 0.0;
+                for (int j = 0; j < g.slugs; j++) {
+                    const double c = g.centre + j * g.spacing;
+                    sl += step2(x - (c - g.half)) - step2(x - (c + g.half));
+                }
                 const double ro = kRhoLo + (kRhoHi - kRhoLo) * sl;
                 rho[k] = ro;
                 rho[n + k] = kRhoHi + kRhoLo - ro;
@@ -769,7 +778,8 @@ int lbm_critical_pressure_channels(const lbm_channel_spec* specs, int32_t n, con
         double bal = 0.0;
         const int rc = planar_balance(s.theta_deg, area, g.h0, g.amp, g.lam, g.centre - g.half, &bal);
         if (rc) return cfail(rc, "spec %d: %s", i, g_chan_err.c_str());
-        r.g_analytic = lap.sigma * bal / (lap.rho_bulk * g.nx);
+        // every slug resists with the same capillary balance: rho g L = n_slugs sigma bal
+        r.g_analytic = g.slugs * (lap.sigma * bal / (lap.rho_bulk * g.nx));
         if (o->use_surrogate) {
             const double neck = 2.0 * (g.h0 - g.amp);
             const double x[5] = {s.amp_ratio, s.slug_len_over_lambda, std::cos(s.theta_deg * kPi / 180.0),

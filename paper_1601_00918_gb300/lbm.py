@@ -88,7 +88,7 @@ class CritResult(ctypes.Structure):
 class ChannelSpec(ctypes.Structure):
     _fields_ = [("lam", ctypes.c_int32), ("amp_ratio", ctypes.c_double),
                 ("slug_len_over_lambda", ctypes.c_double), ("theta_deg", ctypes.c_double),
-                ("visc_ratio", ctypes.c_double), ("n_periods", ctypes.c_int32)]
+                ("visc_ratio", ctypes.c_double), ("n_periods", ctypes.c_int32), ("n_slugs", ctypes.c_int32)]
 
 
 class ChannelOpts(ctypes.Structure):
@@ -591,9 +591,11 @@ def _ccheck(rc, ok=(LBM_OK,)):
 
 def channel_spec(spec) -> ChannelSpec:
     """C struct of a channel description (any object with lam, amp_ratio,
-    slug_len_over_lambda, theta_deg, visc_ratio and optionally n_periods)."""
+    slug_len_over_lambda, theta_deg, visc_ratio and optionally n_periods,
+    n_slugs)."""
     return ChannelSpec(int(spec.lam), float(spec.amp_ratio), float(spec.slug_len_over_lambda),
-                       float(spec.theta_deg), float(spec.visc_ratio), int(getattr(spec, "n_periods", 4)))
+                       float(spec.theta_deg), float(spec.visc_ratio), int(getattr(spec, "n_periods", 4)),
+                       int(getattr(spec, "n_slugs", 1)))
 
 
 def lbm_channel_geometry(spec):

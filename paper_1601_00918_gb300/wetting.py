@@ -82,11 +82,11 @@ def critical_balance(theta_deg: float, area: float, h0: float, amp: float, lam: 
 
 
 def initial_fill(spec: wl.ChannelSpec):
-    """(oil area, rear end) of a channel's initial slug: the channel area
-    between the slug's ends, centred on the neck at x = lambda
-    floor(n_periods / 2)."""
+    """(oil area, rear end) of a channel's first initial slug: the channel
+    area between the slug's ends, centred on the neck at x = lambda
+    floor(n_periods / (2 n_slugs))."""
     lam = float(spec.lam)
-    centre = lam * (spec.n_periods // 2)
+    centre = lam * (spec.n_periods // (2 * spec.n_slugs))
     half = 0.5 * spec.slug_len_over_lambda * lam
     k = 2.0 * math.pi / lam
     area = 2.0 * spec.h0 * (2.0 * half) - 2.0 * spec.amp / k * (math.sin(k * (centre + half)) -
@@ -96,7 +96,8 @@ def initial_fill(spec: wl.ChannelSpec):
 
 def analytic_g_crit(spec: wl.ChannelSpec, theta_deg: float, sigma: float = SIGMA, rho: float = RHO_BULK):
     """g_crit of a sweep channel from the 2-D balance: the slug's oil area and
-    rest position are taken from its initial fill."""
+    rest position are taken from its initial fill; n_slugs identical slugs
+    each hold the same capillary balance, so rho g L = n_slugs sigma bal."""
     area, x_rest = initial_fill(spec)
     bal = critical_balance(theta_deg, area, spec.h0, spec.amp, float(spec.lam), x_rest)
-    return sigma * bal / (rho * spec.nx)
+    return spec.n_slugs * (sigma * bal / (rho * spec.nx))

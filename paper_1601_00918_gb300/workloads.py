@@ -185,6 +185,7 @@ class ChannelSpec:
     theta_deg: float         # contact angle through the water phase
     visc_ratio: float        # nu^o / nu^w
     n_periods: int = 4
+    n_slugs: int = 1         # identical slugs on equally spaced necks
 
     @property
     def h0(self) -> float:
@@ -221,11 +222,21 @@ def sweep_specs(n: int, seed: int, lambdas=(128, 192, 256, 384, 512)) -> list:
 
 def channel_instance(spec: ChannelSpec) -> Workload:
     """Mask and slug fill of one sweep instance: mean half-width h0 =
-    0.1875 lambda, amplitude A = amp_ratio h0, n_periods periods, slug centred
-    on the neck at x = lambda floor(n_periods / 2)."""
+    0.1875 lambda, amplitude A = amp_ratio h0, n_periods periods, n_slugs
+    identical slugs centred on the necks at x = lambda (n_periods /
+    (2 n_slugs) + k n_periods / n_slugs) (one slug: x = lambda
+    floor(n_periods / 2))."""
     nx, ny = spec.nx, spec.ny
     mask = sinusoidal_channel(nx, ny, spec.h0, spec.amp, float(spec.lam))
-    centre = float(spec.lam * (spec.n_periods // 2))
+    k = spec.n_slugs
+    spacing = float(spec.lam * (spec.n_periods // k))
+    first = float(spec.lam * (spec.n_periods // (2 * k)))
     half = 0.5 * spec.slug_len_over_lambda * spec.lam
-    rho = slug(nx, ny, centre - half, centre + half)
+    x = np.arange(nx)[None, :] + np.zeros((ny, 1))
+    s = np.zeros((ny, nx))
+    for j in range(k):
+        c = first + j * spacing
+        s = s + (_step(x - (c - half)) - _step(x - (c + half)))
+    ro = RHO_LO + (RHO_HI - RHO_LO) * s
+    rho = np.stack([ro, RHO_HI + RHO_LO - ro])
     return Workload(f"channel_{nx}x{ny}", mask, rho, (True, False))

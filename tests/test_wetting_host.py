@@ -71,3 +71,39 @@ def test_channel_geometry_is_the_input_module_channel(lam, ratio, slug, periods)
     w = wl.channel_instance(spec)
     np.testing.assert_array_equal(mask, w.mask)
     np.testing.assert_allclose(rho, w.rho, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("lam,periods,slugs,slug", [(32, 4, 2, 1.5), (64, 6, 3, 1.2), (48, 8, 4, 1.75),
+                                                    (40, 4, 4, 0.5)])
+def test_multi_slug_geometry_is_the_input_module_channel(lam, periods, slugs, slug):
+    """Several identical slugs on equally spaced necks: the library's channel
+    equals the shared input module's, mask exactly, densities to the
+    rounding of tanh."""
+    from paper_1601_00918_gb300 import lbm
+    from paper_1601_00918_gb300 import workloads as wl
+    spec = wl.ChannelSpec(lam=lam, amp_ratio=0.4, slug_len_over_lambda=slug, theta_deg=50.0, visc_ratio=1.0,
+                          n_periods=periods, n_slugs=slugs)
+    mask, rho = lbm.lbm_channel_geometry(spec)
+    w = wl.channel_instance(spec)
+    np.testing.assert_array_equal(mask, w.mask)
+    np.testing.assert_allclose(rho, w.rho, rtol=0, atol=1e-15)
+    # the oil is split into `slugs` runs along the centre row
+    row = rho[0, spec.ny // 2] > 0.5
+    assert int(np.sum(row[1:] & ~row[:-1]) + (row[0] and not row[-1])) == slugs
+
+
+def test_planar_force_adds_up_over_identical_slugs():
+    """Every slug holds the same capillary balance, so k identical slugs in
+    a period need k times the force of one (Section 3.4 balance over the
+    period, rho g L = sum of the slugs' capillary jumps): two slugs in four
+    periods need exactly the force of one slug in two periods, and twice
+    that of one slug in four."""
+    from paper_1601_00918_gb300 import workloads as wl
+    one4 = wl.ChannelSpec(lam=64, amp_ratio=0.5, slug_len_over_lambda=1.5, theta_deg=60.0, visc_ratio=1.0)
+    one2 = wl.ChannelSpec(lam=64, amp_ratio=0.5, slug_len_over_lambda=1.5, theta_deg=60.0, visc_ratio=1.0,
+                          n_periods=2)
+    two4 = wl.ChannelSpec(lam=64, amp_ratio=0.5, slug_len_over_lambda=1.5, theta_deg=60.0, visc_ratio=1.0,
+                          n_slugs=2)
+    g1, g12, g2 = (wetting.analytic_g_crit(s, 60.0) for s in (one4, one2, two4))
+    assert g2 == pytest.approx(g12, rel=1e-12)
+    assert g2 == pytest.approx(2.0 * g1, rel=1e-12)
