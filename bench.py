@@ -382,6 +382,7 @@ def native_arm(args):
     crit = critical_pressure_arm(args) if rank == 0 and args.sweep_n > 0 else None
     bstep = batched_step_arm(args, peak) if rank == 0 and args.batch_n > 0 else None
     small = small_grids_arm() if rank == 0 and not args.no_small else None
+    d3 = d3q19_arm(args, peak) if rank == 0 and args.d3_steps > 0 else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -402,7 +403,7 @@ def native_arm(args):
                              "traffic_gbs": traffic / per_launch_s / 1e9 if traffic else None},
                 "all_nodes_value": value * nx * ny / n_fluid,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "cpu_baseline": cpu,
-                "critical_pressure": crit, "batched_step": bstep, "small_grids": small}
+                "critical_pressure": crit, "batched_step": bstep, "small_grids": small, "d3q19_tube": d3}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -550,6 +551,50 @@ def gated_specs(n, seed, lam):
     periods) at one wavelength."""
     from paper_1601_00918_gb300 import sweep
     return sweep.small_specs(n, seed=seed, lambdas=(lam,))
+
+
+def d3q19_arm(args, peak):
+    """The step on the paper's own lattice and geometry: D3Q19 in a periodic
+    sinusoidal tube (radius 24 - 10 cos(2 pi x / 512), circular cross
+    sections, 2048 x 66 x 66 nodes) holding an oil slug, FP32 and FP64.
+    GLUPS over fluid nodes, and the fraction of the measured copy rate of
+    the algorithmic bytes (read + write of the 38 populations: 304 B per
+    fluid node in FP32, 608 B in FP64; the density pass and its re-read of
+    the populations are overhead and count against it)."""
+    import torch
+    from paper_1601_00918_gb300 import lbm
+    from paper_1601_00918_gb300 import workloads as wl
+    nx, nc = 2048, 66
+    mask = wl.sinusoidal_tube(nx, nc, 24.0, 10.0, 512.0)
+    rho = wl.tube_slug(nx, nc, 768.0, 1280.0)
+    n_fluid = int(np.count_nonzero(mask == 0))
+    out = {"workload": f"sinusoidal_tube_{nx}x{nc}x{nc}", "nodes": int(mask.size), "fluid_nodes": n_fluid,
+           "steps": args.d3_steps}
+    for prec in ("fp32", "fp64"):
+        sim = lbm.Simulation3(mask, rho, tau=(1.0, 1.0), G=G_INTERACTION, rho_wall=(0.3, 0.05),
+                              g=(1e-6, 0.0, 0.0), periodic=(True, False, False), precision=prec,
+                              collision="regularized")
+        try:
+            sim.step(3)
+            stream = torch.cuda.current_stream()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(args.d3_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            obs = sim.observables()
+        finally:
+            sim.close()
+        assert obs["nan_flag"] == 0
+        alg = n_fluid * 38 * 2 * BYTES_PER_POP[prec]
+        gbs = alg / (ms * 1e-3 / args.d3_steps) / 1e9
+        out[prec] = {"value": n_fluid * args.d3_steps / (ms * 1e-3) / 1e9, "unit": UNIT,
+                     "ms_per_step": ms / args.d3_steps, "alg_bytes_per_launch_pair": alg, "achieved_gbs": gbs,
+                     "frac": gbs / peak, "kernels": "density3_kernel + collide3_kernel"}
+    return out
 
 
 def critical_pressure_arm(args):
@@ -703,6 +748,7 @@ def main():
     ap.add_argument("--batch-n", type=int, default=512, help="channels of the batched-step measurement (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=160, help="timed steps of the batched-step measurement")
     ap.add_argument("--no-small", action="store_true", help="skip the small-grid latency lines")
+    ap.add_argument("--d3-steps", type=int, default=200, help="timed steps of the D3Q19 tube line (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -211,6 +211,57 @@ int lbm_wait_selftest(void *cuda_stream, double *seconds);
 int lbm_step_noalloc(const uint8_t *mask, const float *f_in, float *f_out, lbm_obs *obs,
                      const lbm_params *p);
 
+/* ---------------------------------------------------------------------------
+ * The same step on the paper's own lattice, D3Q19 (Section 2)
+ *
+ * Nineteen velocities in three dimensions: c_0 = 0; c_1..c_6 the face
+ * neighbours +x, -x, +y, -y, +z, -z (weight 1/18); c_7..c_18 the edge
+ * neighbours (+x+y), (-x-y), (+x-y), (-x+y), (+x+z), (-x-z), (+x-z), (-x+z),
+ * (+y+z), (-y-z), (+y-z), (-y+z) (weight 1/36); rest 1/3; T0 = 1/3.  The
+ * method is the one of lbm_create (interaction and wall force, body force,
+ * mixture relaxation, force through the equilibrium shift, BGK or
+ * regularised non-equilibrium part, halfway bounce-back).  Grids are
+ * [nz][ny][nx] with x fastest; populations f[2][19][nz][ny][nx].  FP64 and
+ * FP32 storage.  Two launches per step: a density pass and a pull
+ * collide-stream pass that reads the neighbour densities of the force from
+ * the density field.  The paper's sinusoidal tube (Section 3.4, circular
+ * cross sections) is a mask of this kind.
+ * ------------------------------------------------------------------------- */
+typedef struct lbm3d_t lbm3d_t; /* opaque */
+
+typedef struct {
+    int32_t nx, ny, nz;           /* lattice size, each >= 1; ny, nz <= 65535 */
+    int32_t periodic[3];          /* 1 = periodic along x, y, z (else solid boundary planes) */
+    double tau[2];                /* tau^o, tau^w (> 1/2) */
+    double G;                     /* Eq. (comp_interaction) */
+    double rho_wall[2];           /* rho_s^o, rho_s^w */
+    double g[3];                  /* body-force acceleration */
+    int32_t precision;            /* LBM_FP64 or LBM_FP32 */
+    int32_t eq_order;             /* 3 = Eq. (feq) as printed, 2 = without cubic terms */
+    int32_t collision;            /* 0 BGK, 1 regularised (Eq. Regualize) */
+    void *cuda_stream;            /* stream of all work, or NULL */
+} lbm3d_params;
+
+/* Create from a host mask [nz][ny][nx] (1 = solid) and host initial
+ * densities [2][nz][ny][nx] (the state starts at f*_i = w_i rho_init).
+ * Errors: LBM_EINVAL (sizes, parameters, precision, a non-periodic
+ * direction whose boundary planes hold fluid, densities at fluid nodes not
+ * finite, negative or both zero), LBM_ENOMEM, LBM_ECUDA. */
+int lbm3d_create(const uint8_t *mask, const double *rho_init, const lbm3d_params *p, lbm3d_t **out);
+/* Advance nsteps (asynchronous). */
+int lbm3d_step(lbm3d_t *h, int64_t nsteps);
+/* Observables of the latest step (as lbm_observables; oil_mom_x along x). */
+int lbm3d_observables(lbm3d_t *h, lbm_obs *out);
+/* Densities rho [2][nz][ny][nx] and mixture velocity u [3][nz][ny][nx]
+ * (with half the force) of the current state; either may be NULL.
+ * Allocates a temporary device buffer of 40 bytes per node. */
+int lbm3d_get_fields(lbm3d_t *h, double *rho, double *u);
+/* Stored populations to / from a host array f[2][19][nz][ny][nx]. */
+int lbm3d_save(lbm3d_t *h, double *f);
+int lbm3d_load(lbm3d_t *h, const double *f);
+void lbm3d_destroy(lbm3d_t *h);
+const char *lbm3d_last_error(const lbm3d_t *h);
+
 /* Free the handle and the device memory it owns.  NULL is ignored. */
 void lbm_destroy(lbm_t *h);
 

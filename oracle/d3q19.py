@@ -4,10 +4,8 @@ lattice (the paper's own velocity set, Section 2).
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  ``lbm3d_oracle.c`` holds
 the step (the same method as ``lbm_oracle.c`` on nineteen velocities in
 three dimensions); this module compiles it with gcc and loads it through
-ctypes.  It also builds the paper's 3-D geometry: a periodic tube whose
-radius varies as h(x) = h0 - A cos(2 pi x / lambda) ("all the cross
-sectional areas are circles", Section 3.4), fluid iff (y - y_c)^2 +
-(z - z_c)^2 <= h(x)^2.
+ctypes.  The 3-D inputs (the paper's sinusoidal tube) come from the shared
+input module, paper_1601_00918_gb300/workloads.py.
 """
 from __future__ import annotations
 
@@ -131,18 +129,3 @@ class Problem3:
         _load().oracle3_fields(ctypes.byref(self.p), _ptr(self.mask, ctypes.c_uint8), _ptr(f, ctypes.c_double),
                                _ptr(rho, ctypes.c_double), _ptr(u, ctypes.c_double))
         return rho, u
-
-
-def sinusoidal_tube(nx: int, n_cross: int, h0: float, amp: float, lam: float) -> np.ndarray:
-    """Mask [n_cross, n_cross, nx] of the periodic tube of radius
-    h(x) = h0 - A cos(2 pi x / lam) about the centre line (y, z) =
-    ((n_cross - 1) / 2, (n_cross - 1) / 2); the boundary planes in y and z are
-    solid."""
-    c = (n_cross - 1) / 2.0
-    x = np.arange(nx)[None, None, :]
-    y = np.arange(n_cross)[None, :, None]
-    z = np.arange(n_cross)[:, None, None]
-    h = h0 - amp * np.cos(2.0 * np.pi * x / lam)
-    m = ((y - c) ** 2 + (z - c) ** 2 > h * h).astype(np.uint8)
-    m[0], m[-1], m[:, 0], m[:, -1] = 1, 1, 1, 1
-    return m

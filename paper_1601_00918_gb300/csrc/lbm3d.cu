@@ -1,0 +1,525 @@
+// Two-component lattice-Boltzmann step on the paper's own lattice, D3Q19
+// (Section 2), and its C ABI (lbm3d_* in include/lbm.h).
+//
+// Method: as the two-dimensional step (lbm_common.cuh), per node and
+// species a, with nineteen velocities c_0 = 0, the six face neighbours
+// (weight 1/18) and the twelve edge neighbours (weight 1/36), T0 = 1/3:
+//   pull      f_i^a(x) = f*_i^a(x - c_i), or f*_opp(i)^a(x) at a solid source
+//             (halfway bounce-back);
+//   density   rho^a = sum_i f_i^a, rho_s^a at a solid node;
+//   force     F^a/rho^a = G sum_i w_i c_i rho^b(x + c_i) + g (Eq. comp_interaction);
+//   moments   u_mix = (j^o + j^w)/rho, nu_mix, tau_mix = nu_mix/T0 + 1/2;
+//   collide   f*_i = f_i^eq(rho^a, u_mix + F^a/rho^a) + (1 - 1/tau_mix) f'_i,
+//             f' = f - f^eq(rho^a, u_mix) or its regularised projection
+//             (Eqs. LBM_BGK, Regualize, feq, collision_term).
+//
+// Design: two launches per step.  The density pass pulls every fluid
+// node's 38 populations and writes its two densities (solid nodes: the
+// wall potentials) into a density field; the collide-stream pass pulls
+// them again, reads the 18 neighbour densities of the force from that field
+// (mostly L1/L2 hits: the field of an 8-million-node tube is 64 MB) and
+// writes the 38 post-collision populations.  One thread per node, x fastest
+// in the thread index, so every population plane is read and written
+// coalesced.  Storage: f[species][direction][z][y][x], dense, ping-pong;
+// link words (32-bit: bit i = the pull source of direction i is solid, bit
+// 31 = the node is solid).  FP64 and FP32; the FP32 rest population takes
+// what the other eighteen leave of rho (mass exact to rounding).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_common.cuh"
+
+using namespace gb300lbm;
+
+namespace {
+
+constexpr int kQ = 19;
+constexpr int kT = 128;                 // threads per block
+constexpr unsigned kSolid3 = 1u << 31;
+
+// D3Q19 in the order: rest; +x, -x, +y, -y, +z, -z; then the edges
+// (+x+y), (-x-y), (+x-y), (-x+y), (+x+z), (-x-z), (+x-z), (-x+z),
+// (+y+z), (-y-z), (+y-z), (-y+z): direction 2k-1 and 2k are opposite.
+__host__ __device__ __forceinline__ int cx3(int i) {
+    constexpr int c[kQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return c[i];
+}
+__host__ __device__ __forceinline__ int cy3(int i) {
+    constexpr int c[kQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return c[i];
+}
+__host__ __device__ __forceinline__ int cz3(int i) {
+    constexpr int c[kQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return c[i];
+}
+__host__ __device__ __forceinline__ int opp3(int i) { return i == 0 ? 0 : (i & 1 ? i + 1 : i - 1); }
+template <typename R>
+__host__ __device__ __forceinline__ R w3(int i) {
+    return i == 0 ? R(1.0 / 3.0) : (i <= 6 ? R(1.0 / 18.0) : R(1.0 / 36.0));
+}
+
+struct Params3 {
+    double nu[2], G, g[3], rho_wall[2], k3, reg;
+};
+
+struct Dims {
+    int nx, ny, nz;
+    long long n;     // nodes
+};
+
+__device__ __forceinline__ long long wrapped(const Dims& d, int x, int y, int z) {
+    x = x < 0 ? x + d.nx : (x >= d.nx ? x - d.nx : x);
+    y = y < 0 ? y + d.ny : (y >= d.ny ? y - d.ny : y);
+    z = z < 0 ? z + d.nz : (z >= d.nz ? z - d.nz : z);
+    return ((long long)z * d.ny + y) * d.nx + x;
+}
+
+// The 38 pulled populations of node k at (x, y, z) with link word lk.
+template <typename R>
+__device__ __forceinline__ void pull3(const R* __restrict__ f, const Dims& d, long long k, int x, int y, int z,
+                                      unsigned lk, R (&fl)[2][kQ]) {
+#pragma unroll
+    for (int i = 0; i < kQ; i++) {
+        const bool bb = (lk >> i) & 1u;
+        const long long src = bb ? k : wrapped(d, x - cx3(i), y - cy3(i), z - cz3(i));
+        const int pl = bb ? opp3(i) : i;
+        fl[0][i] = __ldg(f + (long long)pl * d.n + src);
+        fl[1][i] = __ldg(f + (long long)(kQ + pl) * d.n + src);
+    }
+}
+
+// Launch shape of both passes: blocks of kT consecutive x, one block row
+// per (y, z) line (grid x, ny, nz): coordinates without divisions.
+__device__ __forceinline__ bool node_of(const Dims& d, int& x, int& y, int& z, long long& k) {
+    x = blockIdx.x * kT + threadIdx.x;
+    y = blockIdx.y;
+    z = blockIdx.z;
+    k = ((long long)z * d.ny + y) * d.nx + x;
+    return x < d.nx;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kT) density3_kernel(const R* __restrict__ f, const unsigned* __restrict__ links,
+                                                      R* __restrict__ rho, Dims d, const Params3* __restrict__ p) {
+    int x, y, z;
+    long long k;
+    if (!node_of(d, x, y, z, k)) return;
+    const unsigned lk = links[k];
+    if (lk & kSolid3) {
+        rho[k] = R(p->rho_wall[0]);
+        rho[d.n + k] = R(p->rho_wall[1]);
+        return;
+    }
+    R fl[2][kQ];
+    pull3<R>(f, d, k, x, y, z, lk, fl);
+    R a = R(0), b = R(0);
+#pragma unroll
+    for (int i = 0; i < kQ; i++) {
+        a += fl[0][i];
+        b += fl[1][i];
+    }
+    rho[k] = a;
+    rho[d.n + k] = b;
+}
+
+// Eq. (feq) deviation from rest, D_i = E_i + O_i with E = -1.5 u^2 +
+// 4.5 (c.u)^2 and O = (c.u) (3 - k3 u^2 + k3 (c.u)^2) (T0 = 1/3).
+template <typename R>
+__device__ __forceinline__ R dev3(int i, R ux, R uy, R uz, R uu, R k3) {
+    const R cu = R(cx3(i)) * ux + R(cy3(i)) * uy + R(cz3(i)) * uz;
+    return R(-1.5) * uu + R(4.5) * cu * cu + cu * (R(3) - k3 * uu + k3 * cu * cu);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 6 : 3) collide3_kernel(const R* __restrict__ f, R* __restrict__ fo,
+                                                      const unsigned* __restrict__ links, const R* __restrict__ rho,
+                                                      Dims d, const Params3* __restrict__ p, ObsAccum* __restrict__ acc,
+                                                      ObsState* __restrict__ obs, double* __restrict__ fields) {
+    int x, y, z;
+    long long k;
+    const bool inside = node_of(d, x, y, z, k);
+    ObsLocal<R> ob;
+    const bool live = inside && !(links[inside ? k : 0] & kSolid3);
+    if (live) {
+        const unsigned lk = links[k];
+        R fl[2][kQ];
+        pull3<R>(f, d, k, x, y, z, lk, fl);
+        R r[2], j[2][3];
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            R s = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+            for (int i = 0; i < kQ; i++) {
+                s += fl[a][i];
+                jx += R(cx3(i)) * fl[a][i];
+                jy += R(cy3(i)) * fl[a][i];
+                jz += R(cz3(i)) * fl[a][i];
+            }
+            r[a] = s;
+            j[a][0] = jx;
+            j[a][1] = jy;
+            j[a][2] = jz;
+        }
+        // F^a/rho^a = G sum_i w_i c_i rho^b(x + c_i) + g
+        R sb[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+#pragma unroll
+        for (int i = 1; i < kQ; i++) {
+            const long long nb = wrapped(d, x + cx3(i), y + cy3(i), z + cz3(i));
+            const R wo = w3<R>(i) * rho[nb], ww = w3<R>(i) * rho[d.n + nb];
+            sb[0][0] += R(cx3(i)) * wo;
+            sb[0][1] += R(cy3(i)) * wo;
+            sb[0][2] += R(cz3(i)) * wo;
+            sb[1][0] += R(cx3(i)) * ww;
+            sb[1][1] += R(cy3(i)) * ww;
+            sb[1][2] += R(cz3(i)) * ww;
+        }
+        const R G = R(p->G);
+        R acc3[2][3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            acc3[0][q] = G * sb[1][q] + R(p->g[q]);   // species o feels rho^w
+            acc3[1][q] = G * sb[0][q] + R(p->g[q]);   // species w feels rho^o
+        }
+        const R rt = r[0] + r[1];
+        const R inv = R(1) / rt;
+        R u[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) u[q] = (j[0][q] + j[1][q]) * inv;
+        if (fields) {
+            const long long n = d.n;
+            fields[k] = double(r[0]);
+            fields[n + k] = double(r[1]);
+#pragma unroll
+            for (int q = 0; q < 3; q++)
+                fields[(2 + q) * n + k] = double(u[q] + R(0.5) * (r[0] * acc3[0][q] + r[1] * acc3[1][q]) * inv);
+        } else {
+            const R nu_mix = (r[0] * R(p->nu[0]) + r[1] * R(p->nu[1])) * inv;
+            const R om1 = R(1) - R(1) / (R(3) * nu_mix + R(0.5));
+            const R k3 = R(p->k3);
+            const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+                const R rho_a = r[a];
+                const R us[3] = {u[0] + acc3[a][0], u[1] + acc3[a][1], u[2] + acc3[a][2]};
+                const R uus = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
+                R fn[kQ];
+#pragma unroll
+                for (int i = 0; i < kQ; i++) {
+                    const R wr = w3<R>(i) * rho_a;
+                    fn[i] = (fl[a][i] - wr) - wr * dev3<R>(i, u[0], u[1], u[2], uu, k3);
+                }
+                if (p->reg != 0.0) {
+                    // Eq. (Regualize): f'_i = w_i/(2 T0^2) Q_i : Pi, Q_i = c_i c_i - T0 I
+                    R P[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};   // xx yy zz xy xz yz
+#pragma unroll
+                    for (int i = 1; i < kQ; i++) {
+                        const R cx = R(cx3(i)), cy = R(cy3(i)), cz = R(cz3(i));
+                        P[0] += cx * cx * fn[i];
+                        P[1] += cy * cy * fn[i];
+                        P[2] += cz * cz * fn[i];
+                        P[3] += cx * cy * fn[i];
+                        P[4] += cx * cz * fn[i];
+                        P[5] += cy * cz * fn[i];
+                    }
+                    const R tr = P[0] + P[1] + P[2];
+#pragma unroll
+                    for (int i = 0; i < kQ; i++) {
+                        const R cx = R(cx3(i)), cy = R(cy3(i)), cz = R(cz3(i));
+                        const R qp = cx * cx * P[0] + cy * cy * P[1] + cz * cz * P[2] +
+                                     R(2) * (cx * cy * P[3] + cx * cz * P[4] + cy * cz * P[5]) - R(1.0 / 3.0) * tr;
+                        fn[i] = R(4.5) * w3<R>(i) * qp;
+                    }
+                }
+                R out[kQ];
+                R rest = rho_a;
+#pragma unroll
+                for (int i = 1; i < kQ; i++) {
+                    const R wr = w3<R>(i) * rho_a;
+                    out[i] = wr + (wr * dev3<R>(i, us[0], us[1], us[2], uus, k3) + om1 * fn[i]);
+                    rest -= out[i];
+                }
+                out[0] = rest;   // the f*_i of a node sum to rho for both forms of f'
+#pragma unroll
+                for (int i = 0; i < kQ; i++) fo[(long long)(a * kQ + i) * d.n + k] = out[i];
+            }
+            ob.m0 += r[0];
+            ob.m1 += r[1];
+            ob.px += j[0][0] + R(0.5) * r[0] * acc3[0][0];
+            R v2 = R(0);
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                const R vq = u[q] + R(0.5) * (r[0] * acc3[0][q] + r[1] * acc3[1][q]) * inv;
+                v2 += vq * vq;
+            }
+            ob.umax2 = fmax(ob.umax2, v2);
+            ob.bad = ob.bad || !(r[0] >= R(0) && r[1] >= R(0));
+        }
+    } else if (fields && inside) {
+        const long long n = d.n;
+        fields[k] = p->rho_wall[0];
+        fields[n + k] = p->rho_wall[1];
+        fields[2 * n + k] = fields[3 * n + k] = fields[4 * n + k] = 0.0;
+    }
+    if (fields) return;
+    reduce_observables<R, kT>(ob, acc, obs, false, gridDim.x * gridDim.y * gridDim.z);
+}
+
+__global__ void links3_kernel(const uint8_t* __restrict__ mask, unsigned* __restrict__ links, Dims d) {
+    const long long k = (long long)blockIdx.x * kT + threadIdx.x;
+    if (k >= d.n) return;
+    const int x = (int)(k % d.nx), y = (int)((k / d.nx) % d.ny), z = (int)(k / ((long long)d.nx * d.ny));
+    unsigned w = mask[k] ? kSolid3 : 0u;
+    for (int i = 1; i < kQ; i++)
+        if (mask[wrapped(d, x - cx3(i), y - cy3(i), z - cz3(i))]) w |= 1u << i;
+    links[k] = w;
+}
+
+thread_local std::string g_err3;
+
+int fail3(lbm3d_t* h, int code, const char* fmt, ...);
+
+}  // namespace
+
+struct lbm3d_t {
+    lbm3d_params p{};
+    Dims d{};
+    size_t es = 0;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    unsigned* links = nullptr;
+    void* rho = nullptr;
+    Params3* dprm = nullptr;
+    ObsAccum* dacc = nullptr;
+    ObsState* dobs = nullptr;
+    std::vector<uint8_t> mask;
+    cudaStream_t stream = nullptr;
+    std::string err;
+};
+
+namespace {
+
+int fail3(lbm3d_t* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_err3 = buf;
+    return code;
+}
+
+#define TRY3(h, call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return fail3((h), LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+unsigned blocks_of(long long n) { return (unsigned)((n + kT - 1) / kT); }
+
+template <typename R>
+cudaError_t step3(lbm3d_t* h, double* fields) {
+    const R* fin = (const R*)h->f[h->cur];
+    const dim3 grid((h->d.nx + kT - 1) / kT, h->d.ny, h->d.nz);
+    density3_kernel<R><<<grid, kT, 0, h->stream>>>(fin, h->links, (R*)h->rho, h->d, h->dprm);
+    collide3_kernel<R><<<grid, kT, 0, h->stream>>>(fin, (R*)h->f[1 - h->cur], h->links, (const R*)h->rho, h->d,
+                                                   h->dprm, h->dacc, h->dobs, fields);
+    return cudaGetLastError();
+}
+
+cudaError_t step_any(lbm3d_t* h, double* fields) {
+    return h->p.precision == LBM_FP64 ? step3<double>(h, fields) : step3<float>(h, fields);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm3d_create(const uint8_t* mask, const double* rho_init, const lbm3d_params* p, lbm3d_t** out) {
+    if (!out) return fail3(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!mask || !rho_init || !p) return fail3(nullptr, LBM_EINVAL, "NULL argument");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail3(nullptr, LBM_EINVAL, "nx, ny, nz must be >= 1");
+    if (p->ny > 65535 || p->nz > 65535) return fail3(nullptr, LBM_EINVAL, "ny and nz must be <= 65535");
+    const long long n = (long long)p->nx * p->ny * p->nz;
+    if (n * 2 * kQ >= (1LL << 40)) return fail3(nullptr, LBM_EINVAL, "grid too large");
+    if (p->precision != LBM_FP64 && p->precision != LBM_FP32)
+        return fail3(nullptr, LBM_EINVAL, "precision must be LBM_FP64 or LBM_FP32");
+    if (p->eq_order != 2 && p->eq_order != 3) return fail3(nullptr, LBM_EINVAL, "eq_order must be 2 or 3");
+    if (p->collision != 0 && p->collision != 1) return fail3(nullptr, LBM_EINVAL, "collision must be 0 or 1");
+    for (int a = 0; a < 2; a++)
+        if (!(p->tau[a] > 0.5) || !std::isfinite(p->tau[a]))
+            return fail3(nullptr, LBM_EINVAL, "tau[%d] must be finite and exceed 1/2", a);
+    if (!std::isfinite(p->G) || !std::isfinite(p->rho_wall[0]) || !std::isfinite(p->rho_wall[1]) ||
+        !std::isfinite(p->g[0]) || !std::isfinite(p->g[1]) || !std::isfinite(p->g[2]))
+        return fail3(nullptr, LBM_EINVAL, "G, g and rho_wall must be finite");
+    const int dims[3] = {p->nx, p->ny, p->nz};
+    for (int q = 0; q < 3; q++) {
+        if (p->periodic[q]) continue;
+        for (long long k = 0; k < n; k++) {
+            const int c[3] = {(int)(k % p->nx), (int)((k / p->nx) % p->ny), (int)(k / ((long long)p->nx * p->ny))};
+            if ((c[q] == 0 || c[q] == dims[q] - 1) && !mask[k])
+                return fail3(nullptr, LBM_EINVAL, "direction %d is not periodic but its boundary plane has fluid", q);
+        }
+    }
+    for (long long k = 0; k < n; k++) {
+        if (mask[k]) continue;
+        const double a = rho_init[k], b = rho_init[n + k];
+        if (!std::isfinite(a) || !std::isfinite(b) || a < 0.0 || b < 0.0 || a + b <= 0.0)
+            return fail3(nullptr, LBM_EINVAL, "rho_init at fluid node %lld is not finite, negative or zero", k);
+    }
+    lbm3d_t* h = new lbm3d_t;
+    h->p = *p;
+    h->d = Dims{p->nx, p->ny, p->nz, n};
+    h->es = p->precision == LBM_FP64 ? 8 : 4;
+    h->stream = (cudaStream_t)p->cuda_stream;
+    h->mask.assign(mask, mask + n);
+    auto bail = [&](int rc) {
+        lbm3d_destroy(h);
+        return rc;
+    };
+    const size_t fbytes = (size_t)n * 2 * kQ * h->es;
+    for (int b = 0; b < 2; b++)
+        if (cudaMalloc(&h->f[b], fbytes) != cudaSuccess) return bail(fail3(nullptr, LBM_ENOMEM, "populations"));
+    if (cudaMalloc((void**)&h->links, (size_t)n * 4) != cudaSuccess ||
+        cudaMalloc(&h->rho, (size_t)n * 2 * h->es) != cudaSuccess ||
+        cudaMalloc((void**)&h->dprm, sizeof(Params3)) != cudaSuccess ||
+        cudaMalloc((void**)&h->dacc, sizeof(ObsAccum)) != cudaSuccess ||
+        cudaMalloc((void**)&h->dobs, sizeof(ObsState)) != cudaSuccess)
+        return bail(fail3(nullptr, LBM_ENOMEM, "device memory"));
+    Params3 hp{};
+    for (int a = 0; a < 2; a++) {
+        hp.nu[a] = (p->tau[a] - 0.5) / 3.0;
+        hp.rho_wall[a] = p->rho_wall[a];
+    }
+    for (int q = 0; q < 3; q++) hp.g[q] = p->g[q];
+    hp.G = p->G;
+    hp.k3 = p->eq_order >= 3 ? 4.5 : 0.0;
+    hp.reg = p->collision == 1 ? 1.0 : 0.0;
+    uint8_t* dmask = nullptr;
+    if (cudaMalloc((void**)&dmask, (size_t)n) != cudaSuccess) return bail(fail3(nullptr, LBM_ENOMEM, "mask"));
+    cudaError_t e = cudaMemcpyAsync(dmask, mask, (size_t)n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        links3_kernel<<<blocks_of(n), kT, 0, h->stream>>>(dmask, h->links, h->d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->dprm, &hp, sizeof hp, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dacc, 0, sizeof(ObsAccum), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dobs, 0, sizeof(ObsState), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dmask);
+    if (e != cudaSuccess) return bail(fail3(nullptr, LBM_ECUDA, "set-up: %s", cudaGetErrorString(e)));
+    // initial state f*_i = w_i rho_init at fluid nodes
+    std::vector<double> f((size_t)n * 2 * kQ);
+    for (int a = 0; a < 2; a++)
+        for (int i = 0; i < kQ; i++)
+            for (long long k = 0; k < n; k++)
+                f[(size_t)(a * kQ + i) * n + k] = mask[k] ? 0.0 : w3<double>(i) * rho_init[(size_t)a * n + k];
+    const int rc = lbm3d_load(h, f.data());
+    if (rc) {
+        g_err3 = h->err;
+        return bail(rc);
+    }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm3d_step(lbm3d_t* h, int64_t nsteps) {
+    if (!h || nsteps < 0) return fail3(h, LBM_EINVAL, "bad argument");
+    for (int64_t s = 0; s < nsteps; s++) {
+        TRY3(h, step_any(h, nullptr));
+        h->cur = 1 - h->cur;
+    }
+    return LBM_OK;
+}
+
+int lbm3d_observables(lbm3d_t* h, lbm_obs* out) {
+    if (!h || !out) return fail3(h, LBM_EINVAL, "NULL argument");
+    ObsState s{};
+    TRY3(h, cudaMemcpyAsync(&s, h->dobs, sizeof s, cudaMemcpyDeviceToHost, h->stream));
+    TRY3(h, cudaStreamSynchronize(h->stream));
+    out->mass[0] = s.mass[0];
+    out->mass[1] = s.mass[1];
+    out->oil_mom_x = s.px;
+    out->oil_disp_x = s.disp;
+    out->max_u = s.umax;
+    out->step = s.step;
+    out->nan_flag = s.nan_flag;
+    out->timeout_flag = s.timeout_flag;
+    if (s.nan_flag) return fail3(h, LBM_EUNSTABLE, "a fluid node reached a NaN or negative density");
+    return LBM_OK;
+}
+
+int lbm3d_save(lbm3d_t* h, double* f) {
+    if (!h || !f) return fail3(h, LBM_EINVAL, "NULL argument");
+    const size_t len = (size_t)h->d.n * 2 * kQ;
+    std::vector<char> raw(len * h->es);
+    TRY3(h, cudaMemcpyAsync(raw.data(), h->f[h->cur], raw.size(), cudaMemcpyDeviceToHost, h->stream));
+    TRY3(h, cudaStreamSynchronize(h->stream));
+    for (size_t q = 0; q < len; q++)
+        f[q] = h->es == 8 ? ((const double*)raw.data())[q] : (double)((const float*)raw.data())[q];
+    for (int a = 0; a < 2; a++)
+        for (int i = 0; i < kQ; i++)
+            for (long long k = 0; k < h->d.n; k++)
+                if (h->mask[k]) f[(size_t)(a * kQ + i) * h->d.n + k] = 0.0;
+    return LBM_OK;
+}
+
+int lbm3d_load(lbm3d_t* h, const double* f) {
+    if (!h || !f) return fail3(h, LBM_EINVAL, "NULL argument");
+    const size_t len = (size_t)h->d.n * 2 * kQ;
+    std::vector<char> raw(len * h->es);
+    for (size_t q = 0; q < len; q++) {
+        const long long k = (long long)(q % (size_t)h->d.n);
+        const double v = h->mask[k] ? 0.0 : f[q];
+        if (h->es == 8) ((double*)raw.data())[q] = v;
+        else ((float*)raw.data())[q] = (float)v;
+    }
+    TRY3(h, cudaMemcpyAsync(h->f[h->cur], raw.data(), raw.size(), cudaMemcpyHostToDevice, h->stream));
+    TRY3(h, cudaMemsetAsync(h->dacc, 0, sizeof(ObsAccum), h->stream));
+    TRY3(h, cudaMemsetAsync(h->dobs, 0, sizeof(ObsState), h->stream));
+    TRY3(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+int lbm3d_get_fields(lbm3d_t* h, double* rho, double* u) {
+    if (!h) return fail3(h, LBM_EINVAL, "NULL handle");
+    const long long n = h->d.n;
+    double* dfields = nullptr;
+    TRY3(h, cudaMalloc((void**)&dfields, sizeof(double) * 5 * (size_t)n));
+    cudaError_t e = step_any(h, dfields);
+    std::vector<double> hf((size_t)5 * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hf.data(), dfields, hf.size() * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dfields);
+    if (e != cudaSuccess) return fail3(h, LBM_ECUDA, "fields: %s", cudaGetErrorString(e));
+    if (rho) std::memcpy(rho, hf.data(), sizeof(double) * 2 * n);
+    if (u) std::memcpy(u, hf.data() + 2 * n, sizeof(double) * 3 * n);
+    return LBM_OK;
+}
+
+void lbm3d_destroy(lbm3d_t* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(h->f[0]);
+    cudaFree(h->f[1]);
+    cudaFree(h->links);
+    cudaFree(h->rho);
+    cudaFree(h->dprm);
+    cudaFree(h->dacc);
+    cudaFree(h->dobs);
+    delete h;
+}
+
+const char* lbm3d_last_error(const lbm3d_t* h) { return h ? h->err.c_str() : g_err3.c_str(); }
+
+}  // extern "C"

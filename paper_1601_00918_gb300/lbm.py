@@ -33,7 +33,9 @@ EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "l
            "lbm_mlp_last_error", "lbm_step_noalloc", "lbm_wait_selftest", "lbm_batch_kernel_info",
            "lbm_channel_shape", "lbm_channel_geometry", "lbm_wetting_calibrate", "lbm_surface_tension",
            "lbm_planar_critical_balance", "lbm_contact_angle", "lbm_wall_potentials",
-           "lbm_critical_pressure_channels", "lbm_channel_last_error")
+           "lbm_critical_pressure_channels", "lbm_channel_last_error", "lbm3d_create", "lbm3d_step",
+           "lbm3d_observables", "lbm3d_get_fields", "lbm3d_save", "lbm3d_load", "lbm3d_destroy",
+           "lbm3d_last_error")
 
 
 class LbmError(RuntimeError):
@@ -83,6 +85,13 @@ class BisectOpts(ctypes.Structure):
 class CritResult(ctypes.Structure):
     _fields_ = [("g_lo", ctypes.c_double), ("g_hi", ctypes.c_double), ("probes", ctypes.c_int32),
                 ("status", ctypes.c_int32)]
+
+
+class Params3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("periodic", ctypes.c_int32 * 3), ("tau", ctypes.c_double * 2), ("G", ctypes.c_double),
+                ("rho_wall", ctypes.c_double * 2), ("g", ctypes.c_double * 3), ("precision", ctypes.c_int32),
+                ("eq_order", ctypes.c_int32), ("collision", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
 
 
 class ChannelSpec(ctypes.Structure):
@@ -186,6 +195,19 @@ def library(path: str | None = None) -> ctypes.CDLL:
     for name in ("lbm_channel_shape", "lbm_channel_geometry", "lbm_wetting_calibrate", "lbm_surface_tension",
                  "lbm_planar_critical_balance", "lbm_contact_angle", "lbm_wall_potentials",
                  "lbm_critical_pressure_channels"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.lbm3d_create.argtypes = [P(ctypes.c_uint8), dp, P(Params3), P(vp)]
+    lib.lbm3d_step.argtypes = [vp, ctypes.c_int64]
+    lib.lbm3d_observables.argtypes = [vp, P(Obs)]
+    lib.lbm3d_get_fields.argtypes = [vp, dp, dp]
+    lib.lbm3d_save.argtypes = [vp, dp]
+    lib.lbm3d_load.argtypes = [vp, dp]
+    lib.lbm3d_destroy.argtypes = [vp]
+    lib.lbm3d_destroy.restype = None
+    lib.lbm3d_last_error.argtypes = [vp]
+    lib.lbm3d_last_error.restype = ctypes.c_char_p
+    for name in ("lbm3d_create", "lbm3d_step", "lbm3d_observables", "lbm3d_get_fields", "lbm3d_save",
+                 "lbm3d_load"):
         getattr(lib, name).restype = ctypes.c_int
     lib.lbm_destroy.argtypes = [vp]
     lib.lbm_destroy.restype = None
@@ -685,3 +707,74 @@ def lbm_critical_pressure_channels(specs, precision="fp32", collision="regulariz
     if check:
         _ccheck(rc, ok=(LBM_OK, LBM_ETIMEOUT))
     return [r.as_dict() for r in out]
+
+
+# ----------------------------------------------------------------------------
+# the D3Q19 step (lbm3d_*)
+# ----------------------------------------------------------------------------
+def _check3(rc, h=None, ok=(LBM_OK,)):
+    if rc not in ok:
+        raise LbmError(rc, (library().lbm3d_last_error(h) or b"").decode())
+    return rc
+
+
+class Simulation3:
+    """Owning wrapper of an lbm3d handle on torch's current stream.  mask
+    [nz, ny, nx] (1 = solid), rho_init [2, nz, ny, nx]."""
+
+    def __init__(self, mask, rho_init, tau=(1.0, 1.0), G=0.0, rho_wall=(0.0, 0.0), g=(0.0, 0.0, 0.0),
+                 periodic=(True, True, True), precision="fp64", eq_order=3, collision="bgk", device=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        rho = np.ascontiguousarray(rho_init, dtype=np.float64)
+        self.nz, self.ny, self.nx = mask.shape
+        assert rho.shape == (2,) + mask.shape
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        with torch.cuda.device(device):
+            stream = torch.cuda.current_stream().cuda_stream
+        p = Params3(self.nx, self.ny, self.nz, (ctypes.c_int32 * 3)(*[int(v) for v in periodic]),
+                    (ctypes.c_double * 2)(*tau), float(G), (ctypes.c_double * 2)(*rho_wall),
+                    (ctypes.c_double * 3)(*g), prec, int(eq_order), _collision_code(collision),
+                    ctypes.c_void_p(stream) if stream else None)
+        h = ctypes.c_void_p()
+        _check3(library().lbm3d_create(mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dptr(rho),
+                                       ctypes.byref(p), ctypes.byref(h)))
+        self.h = h.value
+
+    def step(self, n=1):
+        _check3(library().lbm3d_step(self.h, int(n)), self.h)
+
+    def observables(self, check=True):
+        o = Obs()
+        rc = library().lbm3d_observables(self.h, ctypes.byref(o))
+        if check:
+            _check3(rc, self.h)
+        return o.as_dict()
+
+    def fields(self):
+        rho = np.empty((2, self.nz, self.ny, self.nx))
+        u = np.empty((3, self.nz, self.ny, self.nx))
+        _check3(library().lbm3d_get_fields(self.h, _dptr(rho), _dptr(u)), self.h)
+        return rho, u
+
+    def save(self):
+        f = np.empty((2, 19, self.nz, self.ny, self.nx))
+        _check3(library().lbm3d_save(self.h, _dptr(f)), self.h)
+        return f
+
+    def load(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _check3(library().lbm3d_load(self.h, _dptr(f)), self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            library().lbm3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

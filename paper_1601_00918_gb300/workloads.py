@@ -66,6 +66,32 @@ def sinusoidal_channel(nx: int, ny: int, h0: float, amp: float, lam: float,
     return m
 
 
+def sinusoidal_tube(nx: int, n_cross: int, h0: float, amp: float, lam: float) -> np.ndarray:
+    """Mask [n_cross, n_cross, nx] (z, y, x) of the paper's 3-D geometry: a
+    periodic tube of circular cross sections (Section 3.4) whose radius is
+    h(x) = h0 - A cos(2 pi x / lam) about the centre line (y, z) =
+    ((n_cross - 1) / 2, (n_cross - 1) / 2); fluid iff (y - y_c)^2 +
+    (z - z_c)^2 <= h(x)^2; the boundary planes in y and z are solid."""
+    c = (n_cross - 1) / 2.0
+    x = np.arange(nx)[None, None, :]
+    y = np.arange(n_cross)[None, :, None]
+    z = np.arange(n_cross)[:, None, None]
+    h = h0 - amp * np.cos(2.0 * np.pi * x / lam)
+    m = ((y - c) ** 2 + (z - c) ** 2 > h * h).astype(np.uint8)
+    m[0], m[-1], m[:, 0], m[:, -1] = 1, 1, 1, 1
+    return m
+
+
+def tube_slug(nx: int, n_cross: int, x_rear: float, x_front: float, rho_hi: float = RHO_HI,
+              rho_lo: float = RHO_LO) -> np.ndarray:
+    """Densities [2, n_cross, n_cross, nx] of an oil slug filling the tube
+    between x_rear and x_front (tanh ends of width 2), water elsewhere."""
+    x = np.arange(nx)[None, None, :] + np.zeros((n_cross, n_cross, 1))
+    s = _step(x - x_rear) - _step(x - x_front)
+    ro = rho_lo + (rho_hi - rho_lo) * s
+    return np.stack([ro, rho_hi + rho_lo - ro])
+
+
 # ----------------------------------------------------------------------------
 # initial densities
 # ----------------------------------------------------------------------------

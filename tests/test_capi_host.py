@@ -27,7 +27,7 @@ def declared_functions():
         if fn.endswith(".h"):
             text = open(os.path.join(ROOT, "include", fn)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names |= set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text))
+            names |= set(re.findall(r"\b(lbm[0-9a-z]*_[a-z0-9_]+)\s*\(", text))
     return names
 
 

@@ -129,14 +129,10 @@ def test_mass_conservation_in_the_sinusoidal_tube():
     radius 6 - 2.5 cos(2 pi x / 24)) with an oil slug, wall potentials and
     a body force: each species' mass is conserved to 1e-13 over 60 steps
     (halfway bounce-back returns every population that meets a wall)."""
-    mask = d3q19.sinusoidal_tube(48, 18, 6.0, 2.5, 24.0)
-    nz, ny, nx = mask.shape
-    x = np.arange(nx)[None, None, :] + np.zeros((nz, ny, 1))
-    s = 0.5 * (np.tanh((x - 14.0) / 2.0) - np.tanh((x - 34.0) / 2.0))
-    ro = 0.03 + 0.97 * s
+    mask = wl.sinusoidal_tube(48, 18, 6.0, 2.5, 24.0)
     P = d3q19.Problem3(mask, tau=(1.0, 0.9), G=G, rho_wall=(0.1, 0.4), g=(1e-5, 0.0, 0.0),
                        periodic=(True, False, False), collision="regularized")
-    f0 = P.init(np.stack([ro, 1.03 - ro]))
+    f0 = P.init(wl.tube_slug(48, 18, 14.0, 34.0))
     _, hist = P.run(f0, 60, history=True)
     m0 = np.array([f0[0].sum(), f0[1].sum()])
     np.testing.assert_allclose(hist[:, 0], m0[0], rtol=1e-13)
