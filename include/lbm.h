@@ -466,6 +466,26 @@ int lbm_surface_tension(int64_t steps, int32_t precision, void *cuda_stream, dou
 int lbm_planar_critical_balance(double theta_deg, double area, double h0, double amp, double lam, double x_rest,
                                 double *balance);
 
+/* The same balance with contact-angle hysteresis: the front meniscus (oil
+ * advancing, water receding) meets the wall at theta_front_deg, the rear one
+ * (water advancing) at theta_rear_deg, both through water; equal angles give
+ * lbm_planar_critical_balance.  A receding water angle below the advancing
+ * one raises the critical force (the Section 3.4 analysis with
+ * Delta theta != 0). */
+int lbm_planar_critical_balance_hysteresis(double theta_front_deg, double theta_rear_deg, double area, double h0,
+                                           double amp, double lam, double x_rest, double *balance);
+
+/* Contact angles of the two menisci of a slug in the planar sinusoidal
+ * channel h(x) = h0 - amp cos(2 pi x / lam) about y_c = (ny - 1) / 2, from
+ * host densities rho [2][ny][nx] (host, FP64).  For each meniscus: the
+ * oil-fraction crossings of 1/2 on every fluid row at least two nodes from
+ * the wall, Pratt's circle through them, its intersection with the wall,
+ * and the angle there between the wall and the interface, through water.
+ * out[6] = {theta_rear, theta_front (degrees), x_rear, x_front (contact
+ * positions), R_rear, R_front (radii)}.  The slug must lie inside the
+ * period on the centre row. */
+int lbm_meniscus_angles(const double *rho, int32_t nx, int32_t ny, double h0, double amp, double lam, double *out);
+
 /* Contact angle (degrees, through water) of one end of a slug between flat
  * plates with fluid rows y_lo..y_hi, from host densities rho [2][ny][nx]
  * (host, FP64): the measurement inside lbm_wetting_calibrate.  right = 1:

@@ -145,13 +145,14 @@ void meniscus(const Channel& c, double theta, double x, bool front, double* kapp
 }
 
 // Oil area between the rear contact line xr and the front one xf: the
-// channel between the two contact chords plus the two segments.
-double oil_area(const Channel& c, double theta, double xr, double xf) {
+// channel between the two contact chords plus the two segments (front
+// meniscus at angle theta_f, rear at theta_r).
+double oil_area(const Channel& c, double theta_f, double theta_r, double xr, double xf) {
     const double k = 2.0 * kPi / c.lam;
     const double inner = 2.0 * c.h0 * (xf - xr) - 2.0 * c.amp / k * (std::sin(k * xf) - std::sin(k * xr));
     double kf, sf, kr, sr;
-    meniscus(c, theta, xf, true, &kf, &sf);
-    meniscus(c, theta, xr, false, &kr, &sr);
+    meniscus(c, theta_f, xf, true, &kf, &sf);
+    meniscus(c, theta_r, xr, false, &kr, &sr);
     return inner + sf + sr;
 }
 
@@ -161,9 +162,13 @@ double oil_area(const Channel& c, double theta, double xr, double xf) {
 // position (front from the area by bisection), the slug climbs each rising
 // branch and jumps ahead past each local maximum, and it counts as moving
 // at the first jump longer than lambda / 2 (or out of the period).
-int planar_balance(double theta_deg, double area, double h0, double amp, double lam, double x_rest, double* out) {
+// theta_front_deg / theta_rear_deg: the contact angles through water at
+// the front (advancing oil, receding water) and rear menisci; equal for the
+// static balance, apart when the contact angle shows hysteresis.
+int planar_balance2(double theta_front_deg, double theta_rear_deg, double area, double h0, double amp, double lam,
+                    double x_rest, double* out) {
     const Channel c{h0, amp, lam};
-    const double th = theta_deg * kPi / 180.0;
+    const double thf = theta_front_deg * kPi / 180.0, thr = theta_rear_deg * kPi / 180.0;
     constexpr int n = 2001;
     std::vector<double> s(n), bal(n);
     const double s0 = x_rest - 0.5 * lam, ds = 2.0 * lam / (n - 1);
@@ -173,13 +178,13 @@ int planar_balance(double theta_deg, double area, double h0, double amp, double 
         double lo = s[i] + 1e-6, hi = s[i] + area / (2.0 * std::max(h0 - amp, 1e-9)) + 2.0 * lam;
         for (int it = 0; it < 80; it++) {
             const double mid = 0.5 * (lo + hi);
-            if (oil_area(c, th, s[i], mid) > area) hi = mid;
+            if (oil_area(c, thf, thr, s[i], mid) > area) hi = mid;
             else lo = mid;
         }
         const double xf = 0.5 * (lo + hi);
         double kf, sf, kr, sr;
-        meniscus(c, th, xf, true, &kf, &sf);
-        meniscus(c, th, s[i], false, &kr, &sr);
+        meniscus(c, thf, xf, true, &kf, &sf);
+        meniscus(c, thr, s[i], false, &kr, &sr);
         bal[i] = kf - kr;
         bmax = std::max(bmax, std::fabs(bal[i]));
     }
@@ -205,6 +210,10 @@ int planar_balance(double theta_deg, double area, double h0, double amp, double 
     }
     *out = bal[j];
     return LBM_OK;
+}
+
+int planar_balance(double theta_deg, double area, double h0, double amp, double lam, double x_rest, double* out) {
+    return planar_balance2(theta_deg, theta_deg, area, h0, amp, lam, x_rest, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,6 +380,86 @@ bool contact_angle(const double* rho, int nx, int ny, int y_lo, int y_hi, bool r
         }
     const bool on_oil = right ? xc < x_axis : xc > x_axis;
     *theta = on_oil ? acute : 180.0 - acute;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Section 3.4: contact angles of a slug's menisci in the sinusoidal channel
+// ---------------------------------------------------------------------------
+// One meniscus of a slug in the planar channel h(x) = h0 - amp cos(2 pi x /
+// lam) about y_c = (ny - 1) / 2: on every fluid row at least two nodes from
+// the wall, the oil-fraction crossing of 1/2 nearest to the meniscus's
+// position x_end on the centre row (within lam / 3); Pratt's circle through
+// those points; its intersection with the upper wall y = y_c + h(x) nearest
+// the topmost point; the angle there between the wall (pointing into the
+// water) and the interface (pointing into the fluid), i.e. the contact
+// angle through water.
+bool meniscus_angle(const std::vector<double>& frac, int nx, int ny, double h0, double amp, double lam, double x_end,
+                    bool front, double* theta, double* x_contact, double* radius) {
+    const double yc = (ny - 1) / 2.0, k = 2.0 * kPi / lam;
+    auto h_at = [&](double x) { return h0 - amp * std::cos(k * x); };
+    std::vector<double> xs, ys;
+    const int lo = std::max(1, (int)std::floor(x_end - lam / 3.0)), hi = std::min(nx - 2, (int)std::ceil(x_end + lam / 3.0));
+    for (int y = 1; y < ny - 1; y++) {
+        double best = 0.0;
+        bool found = false;
+        for (int x = lo; x < hi; x++) {
+            if (std::fabs(y - yc) > h_at(x) || std::fabs(y - yc) > h_at(x + 1)) continue;
+            const double a = frac[(size_t)y * nx + x], b = frac[(size_t)y * nx + x + 1];
+            double c;
+            if (front && a > 0.5 && b <= 0.5) c = x + (a - 0.5) / (a - b);
+            else if (!front && a <= 0.5 && b > 0.5) c = x + (0.5 - a) / (b - a);
+            else continue;
+            if (!found || std::fabs(c - x_end) < std::fabs(best - x_end)) best = c;
+            found = true;
+        }
+        if (found && std::fabs(y - yc) <= h_at(best) - 2.0) {
+            xs.push_back(best);
+            ys.push_back((double)y);
+        }
+    }
+    double A, B, C, D;
+    if (xs.size() < 5 || !pratt_fit(xs, ys, &A, &B, &C, &D)) return false;
+    // contact with the upper wall: F(x) = A (x^2 + y^2) + B x + C y + D on y = y_c + h(x)
+    size_t top = 0;
+    for (size_t q = 1; q < ys.size(); q++)
+        if (ys[q] > ys[top]) top = q;
+    auto F = [&](double x) {
+        const double y = yc + h_at(x);
+        return A * (x * x + y * y) + B * x + C * y + D;
+    };
+    const double x0 = xs[top];
+    double xc = 0.0;
+    bool hit = false;
+    constexpr int kSamples = 2400;
+    double prev = F(x0 - 6.0);
+    for (int q = 1; q <= kSamples; q++) {
+        const double xa = x0 - 6.0 + 12.0 * (q - 1) / kSamples, xb = x0 - 6.0 + 12.0 * q / kSamples;
+        const double fb = F(xb);
+        if ((prev < 0.0) != (fb < 0.0)) {
+            const double cand = xa - prev * (xb - xa) / (fb - prev);
+            if (!hit || std::fabs(cand - x0) < std::fabs(xc - x0)) xc = cand;
+            hit = true;
+        }
+        prev = fb;
+    }
+    if (!hit) return false;
+    const double yP = yc + h_at(xc), hp = amp * k * std::sin(k * xc);
+    double ti[2] = {-(2.0 * A * yP + C), 2.0 * A * xc + B};     // tangent of the circle at the contact
+    const double tn = std::hypot(ti[0], ti[1]);
+    if (!(tn > 0.0)) return false;
+    ti[0] /= tn;
+    ti[1] /= tn;
+    if (ti[1] > 0.0) {                                          // pointing into the fluid (down)
+        ti[0] = -ti[0];
+        ti[1] = -ti[1];
+    }
+    const double wn = std::hypot(1.0, hp);
+    const double sgn = front ? 1.0 : -1.0;                      // the water lies ahead of the front, behind the rear
+    const double dot = sgn * (ti[0] + hp * ti[1]) / wn;
+    *theta = std::acos(std::max(-1.0, std::min(1.0, dot))) * 180.0 / kPi;
+    *x_contact = xc;
+    *radius = std::fabs(A) > 0.0 ? 1.0 / (2.0 * std::fabs(A)) : INFINITY;
     return true;
 }
 
@@ -659,6 +748,48 @@ int lbm_channel_geometry(const lbm_channel_spec* s, uint8_t* mask, double* rho_i
     if (!s) return cfail(LBM_EINVAL, "NULL argument");
     if (!geom_of(*s, &g)) return cfail(LBM_EINVAL, "channel spec out of range");
     fill(g, mask, rho_init);
+    return LBM_OK;
+}
+
+int lbm_planar_critical_balance_hysteresis(double theta_front_deg, double theta_rear_deg, double area, double h0,
+                                           double amp, double lam, double x_rest, double* balance) {
+    if (!balance) return cfail(LBM_EINVAL, "NULL argument");
+    if (!(theta_front_deg > 0.0 && theta_front_deg < 180.0) || !(theta_rear_deg > 0.0 && theta_rear_deg < 180.0) ||
+        !(area > 0.0) || !(h0 > 0.0) || !(amp >= 0.0 && amp < h0) || !(lam > 0.0) || !std::isfinite(x_rest))
+        return cfail(LBM_EINVAL, "planar balance: argument out of range");
+    return planar_balance2(theta_front_deg, theta_rear_deg, area, h0, amp, lam, x_rest, balance);
+}
+
+int lbm_meniscus_angles(const double* rho, int32_t nx, int32_t ny, double h0, double amp, double lam, double* out) {
+    if (!rho || !out || nx < 8 || ny < 8 || !(h0 > 0.0) || !(amp >= 0.0 && amp < h0) || !(lam > 0.0))
+        return cfail(LBM_EINVAL, "bad argument");
+    const size_t n = (size_t)nx * ny;
+    const double yc = (ny - 1) / 2.0, k = 2.0 * kPi / lam;
+    std::vector<double> frac(n, 0.0);
+    for (int y = 1; y < ny - 1; y++)
+        for (int x = 0; x < nx; x++) {
+            if (std::fabs(y - yc) > h0 - amp * std::cos(k * x)) continue;
+            const size_t q = (size_t)y * nx + x;
+            const double a = rho[q], b = rho[n + q];
+            frac[q] = a + b > 0.0 ? a / (a + b) : 0.0;
+        }
+    // the slug's ends on the centre row
+    const size_t row = (size_t)(ny / 2) * nx;
+    int i0 = -1, i1 = -1;
+    for (int x = 0; x < nx; x++)
+        if (frac[row + x] > 0.5) {
+            if (i0 < 0) i0 = x;
+            i1 = x;
+        }
+    if (i0 <= 0 || i1 >= nx - 1) return cfail(LBM_EINVAL, "meniscus angles: no slug inside the period on the centre row");
+    for (int side = 0; side < 2; side++) {
+        double th, xc, r;
+        if (!meniscus_angle(frac, nx, ny, h0, amp, lam, side ? i1 : i0, side == 1, &th, &xc, &r))
+            return cfail(LBM_EINVAL, "meniscus angles: too few interface points on the %s meniscus", side ? "front" : "rear");
+        out[side] = th;
+        out[2 + side] = xc;
+        out[4 + side] = r;
+    }
     return LBM_OK;
 }
 

@@ -32,8 +32,8 @@ EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "l
            "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam", "lbm_mlp_train", "lbm_mlp_destroy",
            "lbm_mlp_last_error", "lbm_step_noalloc", "lbm_wait_selftest", "lbm_batch_kernel_info",
            "lbm_channel_shape", "lbm_channel_geometry", "lbm_wetting_calibrate", "lbm_surface_tension",
-           "lbm_planar_critical_balance", "lbm_contact_angle", "lbm_wall_potentials",
-           "lbm_critical_pressure_channels", "lbm_channel_last_error", "lbm3d_create", "lbm3d_step",
+           "lbm_planar_critical_balance", "lbm_planar_critical_balance_hysteresis", "lbm_contact_angle",
+           "lbm_wall_potentials", "lbm_meniscus_angles", "lbm_critical_pressure_channels", "lbm_channel_last_error", "lbm3d_create", "lbm3d_step",
            "lbm3d_observables", "lbm3d_get_fields", "lbm3d_save", "lbm3d_load", "lbm3d_destroy",
            "lbm3d_last_error")
 
@@ -185,6 +185,10 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_wetting_calibrate.argtypes = [dp, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, vp, dp]
     lib.lbm_surface_tension.argtypes = [ctypes.c_int64, ctypes.c_int32, vp, dp, dp]
     lib.lbm_planar_critical_balance.argtypes = [ctypes.c_double] * 6 + [dp]
+    lib.lbm_planar_critical_balance_hysteresis.argtypes = [ctypes.c_double] * 7 + [dp]
+    lib.lbm_meniscus_angles.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, dp]
+    lib.lbm_meniscus_angles.restype = ctypes.c_int
     lib.lbm_contact_angle.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_int32, dp]
     lib.lbm_wall_potentials.argtypes = [dp, dp, ctypes.c_int32, ctypes.c_double, dp]
@@ -193,7 +197,7 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_channel_last_error.argtypes = []
     lib.lbm_channel_last_error.restype = ctypes.c_char_p
     for name in ("lbm_channel_shape", "lbm_channel_geometry", "lbm_wetting_calibrate", "lbm_surface_tension",
-                 "lbm_planar_critical_balance", "lbm_contact_angle", "lbm_wall_potentials",
+                 "lbm_planar_critical_balance", "lbm_planar_critical_balance_hysteresis", "lbm_contact_angle", "lbm_wall_potentials",
                  "lbm_critical_pressure_channels"):
         getattr(lib, name).restype = ctypes.c_int
     lib.lbm3d_create.argtypes = [P(ctypes.c_uint8), dp, P(Params3), P(vp)]
@@ -654,6 +658,24 @@ def lbm_planar_critical_balance(theta_deg, area, h0, amp, lam, x_rest):
     _ccheck(library().lbm_planar_critical_balance(float(theta_deg), float(area), float(h0), float(amp),
                                                   float(lam), float(x_rest), ctypes.byref(out)))
     return out.value
+
+
+def lbm_planar_critical_balance_hysteresis(theta_front, theta_rear, area, h0, amp, lam, x_rest):
+    out = ctypes.c_double()
+    _ccheck(library().lbm_planar_critical_balance_hysteresis(float(theta_front), float(theta_rear), float(area),
+                                                             float(h0), float(amp), float(lam), float(x_rest),
+                                                             ctypes.byref(out)))
+    return out.value
+
+
+def lbm_meniscus_angles(rho, h0, amp, lam):
+    """{theta_rear, theta_front, x_rear, x_front, r_rear, r_front} of a slug
+    in the planar sinusoidal channel (lbm_meniscus_angles)."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    _, ny, nx = rho.shape
+    out = np.zeros(6)
+    _ccheck(library().lbm_meniscus_angles(_dptr(rho), nx, ny, float(h0), float(amp), float(lam), _dptr(out)))
+    return dict(zip(("theta_rear", "theta_front", "x_rear", "x_front", "r_rear", "r_front"), out.tolist()))
 
 
 def lbm_contact_angle(rho, y_lo, y_hi, right=True):

@@ -107,3 +107,57 @@ def test_planar_force_adds_up_over_identical_slugs():
     g1, g12, g2 = (wetting.analytic_g_crit(s, 60.0) for s in (one4, one2, two4))
     assert g2 == pytest.approx(g12, rel=1e-12)
     assert g2 == pytest.approx(2.0 * g1, rel=1e-12)
+
+
+def _synthetic_slug(lam, h0, amp, x_r, x_f, th_r, th_f, w=2.0):
+    """Densities of a slug in the planar sinusoidal channel whose menisci are
+    the arcs of the Section 3.4 planar model: centred on the axis, meeting
+    the wall (inclined by atan h'(x)) at the given contact positions and
+    angles through water; tanh interfaces of width w."""
+    k = 2 * math.pi / lam
+    ny = 2 * int(math.ceil(h0 + amp)) + 2
+    nx = 4 * lam
+    yc = (ny - 1) / 2.0
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+
+    def end(xc, th, front):
+        h = h0 - amp * math.cos(k * xc)
+        phi = math.atan(amp * k * math.sin(k * xc))
+        al = 0.5 * math.pi + (phi if front else -phi) - math.radians(th)
+        R = h / math.sin(al)
+        xm = xc - R * math.cos(al) if front else xc + R * math.cos(al)
+        dist = np.hypot(X - xm, Y - yc)
+        beyond = (X - xm) if front else (xm - X)
+        s = np.minimum(dist - abs(R), beyond) if al > 0 else np.maximum(abs(R) - dist, beyond)
+        return 0.5 * (1 - np.tanh(s / w))
+
+    frac = np.minimum(end(x_f, th_f, True), end(x_r, th_r, False))
+    ro = 0.03 + 0.97 * frac
+    return np.stack([ro, 1.03 - ro])
+
+
+@pytest.mark.parametrize("th_r,th_f", [(40.0, 40.0), (60.0, 52.0), (75.0, 88.0), (120.0, 118.0), (140.0, 139.0)])
+def test_meniscus_angles_of_synthetic_arcs(th_r, th_f):
+    """lbm_meniscus_angles recovers the contact angles (to 0.5 degree) and
+    contact positions (to 0.1 node) of a slug whose menisci are planar-model
+    arcs meeting the inclined walls of a lambda = 128 channel."""
+    from paper_1601_00918_gb300 import lbm
+    rho = _synthetic_slug(128, 24.0, 12.0, 180.3, 390.7, th_r, th_f)
+    m = lbm.lbm_meniscus_angles(rho, 24.0, 12.0, 128.0)
+    assert m["theta_rear"] == pytest.approx(th_r, abs=0.5)
+    assert m["theta_front"] == pytest.approx(th_f, abs=0.5)
+    assert m["x_rear"] == pytest.approx(180.3, abs=0.1) and m["x_front"] == pytest.approx(390.7, abs=0.1)
+
+
+@pytest.mark.parametrize("theta", [40.0, 90.0, 140.0])
+def test_hysteresis_balance(theta):
+    """Equal front and rear angles give the static balance; a receding
+    (front) water angle below the advancing (rear) one raises the force
+    the slug can hold (the analysis with Delta theta != 0); the reverse
+    lowers it."""
+    from paper_1601_00918_gb300 import lbm
+    args = (2600.0, 12.0, 6.0, 64.0, 79.7)
+    b0 = lbm.lbm_planar_critical_balance(theta, *args)
+    assert lbm.lbm_planar_critical_balance_hysteresis(theta, theta, *args) == b0
+    assert lbm.lbm_planar_critical_balance_hysteresis(theta - 4.0, theta + 4.0, *args) > b0
+    assert lbm.lbm_planar_critical_balance_hysteresis(theta + 4.0, theta - 4.0, *args) < b0
