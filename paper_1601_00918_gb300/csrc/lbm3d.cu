@@ -13,14 +13,15 @@
 //             f' = f - f^eq(rho^a, u_mix) or its regularised projection
 //             (Eqs. LBM_BGK, Regualize, feq, collision_term).
 //
-// Design: two launches per step.  The density pass pulls every fluid
-// node's 38 populations and writes its two densities (solid nodes: the
-// wall potentials) into a density field; the collide-stream pass pulls
-// them again, reads the 18 neighbour densities of the force from that field
-// (mostly L1/L2 hits: the field of an 8-million-node tube is 64 MB) and
-// writes the 38 post-collision populations.  One thread per node, x fastest
-// in the thread index, so every population plane is read and written
-// coalesced.  Storage: f[species][direction][z][y][x], dense, ping-pong;
+// Design: two launches per step, both over a list of the fluid nodes only
+// (x fastest, so neighbouring threads hold neighbouring x and every
+// population plane is read and written coalesced; solid nodes cost
+// nothing).  The density pass pulls every fluid node's 38 populations and
+// writes its two densities into a density field (the solid nodes' entries
+// hold the wall potentials, written once at set-up); the collide-stream
+// pass pulls them again, reads the 18 neighbour densities of the force from
+// that field (mostly L1/L2 hits: the field of an 8-million-node tube is
+// 64 MB) and writes the 38 post-collision populations.  Storage: f[species][direction][z][y][x], dense, ping-pong;
 // link words (32-bit: bit i = the pull source of direction i is solid, bit
 // 31 = the node is solid).  FP64 and FP32; the FP32 rest population takes
 // what the other eighteen leave of rho (mass exact to rounding).
@@ -96,28 +97,33 @@ __device__ __forceinline__ void pull3(const R* __restrict__ f, const Dims& d, lo
     }
 }
 
-// Launch shape of both passes: blocks of kT consecutive x, one block row
-// per (y, z) line (grid x, ny, nz): coordinates without divisions.
-__device__ __forceinline__ bool node_of(const Dims& d, int& x, int& y, int& z, long long& k) {
-    x = blockIdx.x * kT + threadIdx.x;
-    y = blockIdx.y;
-    z = blockIdx.z;
+// Both passes run over the fluid nodes only: thread t takes entry t of the
+// fluid list (x fastest, so neighbouring threads hold neighbouring x and
+// every population plane is still read and written coalesced); a node's
+// coordinates are packed as x | y << 16 | z << 32 ... in 64 bits:
+// x in bits 0..20, y in 21..41, z in 42..62.
+__device__ __forceinline__ bool node_of(const Dims& d, const unsigned long long* __restrict__ fluid,
+                                        long long nfluid, int& x, int& y, int& z, long long& k) {
+    const long long t = (long long)blockIdx.x * kT + threadIdx.x;
+    if (t >= nfluid) return false;
+    const unsigned long long c = fluid[t];
+    x = (int)(c & 0x1FFFFFull);
+    y = (int)((c >> 21) & 0x1FFFFFull);
+    z = (int)((c >> 42) & 0x1FFFFFull);
     k = ((long long)z * d.ny + y) * d.nx + x;
-    return x < d.nx;
+    return true;
 }
 
+// Densities of the fluid nodes (the solid nodes' entries hold the wall
+// potentials, written once at set-up).
 template <typename R>
 __global__ void __launch_bounds__(kT) density3_kernel(const R* __restrict__ f, const unsigned* __restrict__ links,
-                                                      R* __restrict__ rho, Dims d, const Params3* __restrict__ p) {
+                                                      R* __restrict__ rho, Dims d,
+                                                      const unsigned long long* __restrict__ fluid, long long nfluid) {
     int x, y, z;
     long long k;
-    if (!node_of(d, x, y, z, k)) return;
+    if (!node_of(d, fluid, nfluid, x, y, z, k)) return;
     const unsigned lk = links[k];
-    if (lk & kSolid3) {
-        rho[k] = R(p->rho_wall[0]);
-        rho[d.n + k] = R(p->rho_wall[1]);
-        return;
-    }
     R fl[2][kQ];
     pull3<R>(f, d, k, x, y, z, lk, fl);
     R a = R(0), b = R(0);
@@ -139,15 +145,15 @@ __device__ __forceinline__ R dev3(int i, R ux, R uy, R uz, R uu, R k3) {
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 6 : 3) collide3_kernel(const R* __restrict__ f, R* __restrict__ fo,
+__global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 5 : 3) collide3_kernel(const R* __restrict__ f, R* __restrict__ fo,
                                                       const unsigned* __restrict__ links, const R* __restrict__ rho,
                                                       Dims d, const Params3* __restrict__ p, ObsAccum* __restrict__ acc,
-                                                      ObsState* __restrict__ obs, double* __restrict__ fields) {
+                                                      ObsState* __restrict__ obs, double* __restrict__ fields,
+                                                      const unsigned long long* __restrict__ fluid, long long nfluid) {
     int x, y, z;
     long long k;
-    const bool inside = node_of(d, x, y, z, k);
+    const bool live = node_of(d, fluid, nfluid, x, y, z, k);
     ObsLocal<R> ob;
-    const bool live = inside && !(links[inside ? k : 0] & kSolid3);
     if (live) {
         const unsigned lk = links[k];
         R fl[2][kQ];
@@ -262,14 +268,27 @@ __global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 6 : 3) collide3_kernel(co
             ob.umax2 = fmax(ob.umax2, v2);
             ob.bad = ob.bad || !(r[0] >= R(0) && r[1] >= R(0));
         }
-    } else if (fields && inside) {
+    }
+    if (fields) return;
+    reduce_observables<R, kT>(ob, acc, obs, false, gridDim.x);
+}
+
+// The wall potentials into the density field at solid nodes (set-up), and
+// the fields of solid nodes (rho_s, zero velocity).
+template <typename R>
+__global__ void solid_density3_kernel(const unsigned* __restrict__ links, R* __restrict__ rho, Dims d,
+                                      const Params3* __restrict__ p, double* __restrict__ fields) {
+    const long long k = (long long)blockIdx.x * kT + threadIdx.x;
+    if (k >= d.n || !(links[k] & kSolid3)) return;
+    if (fields) {
         const long long n = d.n;
         fields[k] = p->rho_wall[0];
         fields[n + k] = p->rho_wall[1];
         fields[2 * n + k] = fields[3 * n + k] = fields[4 * n + k] = 0.0;
+        return;
     }
-    if (fields) return;
-    reduce_observables<R, kT>(ob, acc, obs, false, gridDim.x * gridDim.y * gridDim.z);
+    rho[k] = R(p->rho_wall[0]);
+    rho[d.n + k] = R(p->rho_wall[1]);
 }
 
 __global__ void links3_kernel(const uint8_t* __restrict__ mask, unsigned* __restrict__ links, Dims d) {
@@ -296,6 +315,8 @@ struct lbm3d_t {
     int cur = 0;
     unsigned* links = nullptr;
     void* rho = nullptr;
+    unsigned long long* fluid = nullptr;   // packed coordinates of the fluid nodes, x fastest
+    long long nfluid = 0;
     Params3* dprm = nullptr;
     ObsAccum* dacc = nullptr;
     ObsState* dobs = nullptr;
@@ -328,10 +349,22 @@ unsigned blocks_of(long long n) { return (unsigned)((n + kT - 1) / kT); }
 template <typename R>
 cudaError_t step3(lbm3d_t* h, double* fields) {
     const R* fin = (const R*)h->f[h->cur];
-    const dim3 grid((h->d.nx + kT - 1) / kT, h->d.ny, h->d.nz);
-    density3_kernel<R><<<grid, kT, 0, h->stream>>>(fin, h->links, (R*)h->rho, h->d, h->dprm);
+    if (fields) solid_density3_kernel<R><<<blocks_of(h->d.n), kT, 0, h->stream>>>(h->links, nullptr, h->d, h->dprm, fields);
+    // one block at least: without fluid the collide pass still closes the
+    // step's observables
+    const unsigned grid = std::max(1u, blocks_of(h->nfluid));
+    if (h->nfluid > 0)
+        density3_kernel<R><<<grid, kT, 0, h->stream>>>(fin, h->links, (R*)h->rho, h->d, h->fluid, h->nfluid);
     collide3_kernel<R><<<grid, kT, 0, h->stream>>>(fin, (R*)h->f[1 - h->cur], h->links, (const R*)h->rho, h->d,
-                                                   h->dprm, h->dacc, h->dobs, fields);
+                                                   h->dprm, h->dacc, h->dobs, fields, h->fluid, h->nfluid);
+    return cudaGetLastError();
+}
+
+cudaError_t init_solid_density(lbm3d_t* h) {
+    if (h->p.precision == LBM_FP64)
+        solid_density3_kernel<double><<<blocks_of(h->d.n), kT, 0, h->stream>>>(h->links, (double*)h->rho, h->d, h->dprm, nullptr);
+    else
+        solid_density3_kernel<float><<<blocks_of(h->d.n), kT, 0, h->stream>>>(h->links, (float*)h->rho, h->d, h->dprm, nullptr);
     return cudaGetLastError();
 }
 
@@ -348,7 +381,8 @@ int lbm3d_create(const uint8_t* mask, const double* rho_init, const lbm3d_params
     *out = nullptr;
     if (!mask || !rho_init || !p) return fail3(nullptr, LBM_EINVAL, "NULL argument");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail3(nullptr, LBM_EINVAL, "nx, ny, nz must be >= 1");
-    if (p->ny > 65535 || p->nz > 65535) return fail3(nullptr, LBM_EINVAL, "ny and nz must be <= 65535");
+    if (p->nx > (1 << 21) || p->ny > (1 << 21) || p->nz > (1 << 21))
+        return fail3(nullptr, LBM_EINVAL, "nx, ny, nz must be <= 2^21");
     const long long n = (long long)p->nx * p->ny * p->nz;
     if (n * 2 * kQ >= (1LL << 40)) return fail3(nullptr, LBM_EINVAL, "grid too large");
     if (p->precision != LBM_FP64 && p->precision != LBM_FP32)
@@ -412,6 +446,22 @@ int lbm3d_create(const uint8_t* mask, const double* rho_init, const lbm3d_params
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->dprm, &hp, sizeof hp, cudaMemcpyHostToDevice, h->stream);
+    // the fluid list (x fastest) and the wall potentials of the solid nodes
+    std::vector<unsigned long long> fl;
+    for (long long k = 0; k < n; k++)
+        if (!mask[k]) {
+            const unsigned long long x = (unsigned long long)(k % p->nx), y = (unsigned long long)((k / p->nx) % p->ny),
+                                     z = (unsigned long long)(k / ((long long)p->nx * p->ny));
+            fl.push_back(x | (y << 21) | (z << 42));
+        }
+    h->nfluid = (long long)fl.size();
+    if (e == cudaSuccess && h->nfluid > 0) {
+        e = cudaMalloc((void**)&h->fluid, fl.size() * sizeof(unsigned long long));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->fluid, fl.data(), fl.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                                h->stream);
+    }
+    if (e == cudaSuccess) e = init_solid_density(h);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dacc, 0, sizeof(ObsAccum), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dobs, 0, sizeof(ObsState), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -514,6 +564,7 @@ void lbm3d_destroy(lbm3d_t* h) {
     cudaFree(h->f[1]);
     cudaFree(h->links);
     cudaFree(h->rho);
+    cudaFree(h->fluid);
     cudaFree(h->dprm);
     cudaFree(h->dacc);
     cudaFree(h->dobs);
