@@ -411,9 +411,10 @@ def native_arm(args):
 
 
 def small_grids_arm(steps=2000):
-    """The small configurations, each 2000 steps (CUDA graphs of 32
-    steps) after 64 warm-up steps; their state fits in the 129 MB L2, so they
-    show launch and graph overhead, not the HBM roofline: the static droplet
+    """The small configurations, each 2000 steps after 256 warm-up steps (in
+    which the library also times its persistent launch against CUDA graphs of
+    32 steps and keeps the faster); their state fits in the 129 MB L2, so they
+    show launch and grid-barrier overhead, not the HBM roofline: the static droplet
     (128 x 128 periodic, R = 20, FP64), the layered channel (256 x 66, FP32)
     and the sinusoidal channel with a slug (1024 x 146) in FP32, FP16- and
     BF16-shifted storage."""
@@ -433,8 +434,8 @@ def small_grids_arm(steps=2000):
     for name, w, prec, kw in cases:
         sim = lbm.Simulation(w.mask, w.rho, precision=prec, periodic=w.periodic, **kw)
         try:
+            sim.step(256)
             kinfo = sim.kernel_info()
-            sim.step(64)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)

@@ -85,6 +85,12 @@ typedef struct {
                                        3 = pipelined (TMA rows, warps march independently),
                                        4 = private (each warp stages its own row windows,
                                        densities exchanged by shuffles, no CTA barrier);
+                                       5 = persistent (many steps per cooperative launch, a
+                                       grid-wide barrier between steps; for small grids:
+                                       with 0 the library times it, with tiles of 1, 2, 4 and
+                                       8 rows, against the graph path on the first lbm_step
+                                       of 160 steps or more when the grid has at most 2^21
+                                       fluid nodes and keeps the fastest);
                                        results agree to rounding */
     int32_t collision;              /* non-equilibrium part f' of Eq. (LBM_BGK): 0 = f - f^eq
                                        (plain BGK); 1 = regularised, Eq. (Regualize): the
@@ -158,7 +164,9 @@ int lbm_save(lbm_t *h, double *f);
 int lbm_load(lbm_t *h, const double *f);
 
 /* Launch configuration the autotuner chose for the step kernel:
- * info[0] = variant (1 simple, 2 staged, 3 pipelined, 4 private); info[1] =
+ * info[0] = variant (1 simple, 2 staged, 3 pipelined, 4 private, 5
+ * persistent: then info[2] = rows per tile, info[3] = CTAs of the
+ * cooperative launch); info[1] =
  * rows in flight (variants 2..4); info[2] = rows per CTA strip (variant 1)
  * or columns per CTA (2..4); info[3] = strips per column block (2..4);
  * info[4] = 1 when the staged kernel's strips sit at the same absolute rows

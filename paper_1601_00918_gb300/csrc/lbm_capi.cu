@@ -88,6 +88,10 @@ struct lbm_t {
     Tuned tune;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t fluid_nodes = 0;
+    // persistent multi-step launches (small grids): 0 undecided, 1 used, -1 not used
+    int persist = 0;
+    int persist_rpb = 8;          // rows per tile of the persistent march
+    int persist_ctas = 0;         // resident CTAs of one cooperative launch
     std::string err;
 };
 
@@ -457,7 +461,9 @@ std::vector<Tuned> candidates(const lbm_t* h) {
     const int sms = sms_of_device();
     const int ny = h->p.ny;
     const int req = h->p.variant;
-    if (req == 0 || req == 1) {
+    // the persistent variant (5) keeps a simple-kernel configuration for the
+    // single launches the library still makes
+    if (req == 0 || req == 1 || req == 5) {
         for (int ctas_per_sm : {4, 8, 16}) {
             Tuned t;
             t.variant = 1;
@@ -625,7 +631,7 @@ int validate(const lbm_params* p, const uint8_t* mask) {
     if (p->nx < 1 || p->ny < 1) return fail(nullptr, LBM_EINVAL, "nx, ny must be >= 1");
     if (elem_size(p->precision) == 0) return fail(nullptr, LBM_EINVAL, "unknown precision %d", p->precision);
     if (p->eq_order != 2 && p->eq_order != 3) return fail(nullptr, LBM_EINVAL, "eq_order must be 2 or 3");
-    if (p->variant < 0 || p->variant > 4) return fail(nullptr, LBM_EINVAL, "variant must be 0, 1, 2, 3 or 4");
+    if (p->variant < 0 || p->variant > 5) return fail(nullptr, LBM_EINVAL, "variant must be 0, 1, 2, 3, 4 or 5");
     if (p->collision != 0 && p->collision != 1) return fail(nullptr, LBM_EINVAL, "collision must be 0 or 1");
     for (int a = 0; a < 2; a++)
         if (!(p->tau[a] > 0.5) || !std::isfinite(p->tau[a]))
@@ -703,6 +709,133 @@ __global__ void wait_selftest_kernel(int* out) {
     fence_mbar_init();
     out[0] = mbar_wait(&bar, 0u) ? 0 : 1;
 }
+
+namespace {
+
+constexpr int64_t kPersistMaxFluid = int64_t(1) << 21;   // grids the persistent path is tried on
+constexpr int kPersistChunk = 4096;                      // steps per cooperative launch
+
+template <typename S>
+cudaError_t launch_persist_t(lbm_t* h, int nsteps) {
+    Grid g = make_grid(h, 0, h->p.ny);
+    g.rows_per_block = h->persist_rpb;
+    S* f0 = at_col0<S>(h->fbase[0]);
+    S* f1 = at_col0<S>(h->fbase[1]);
+    const uint16_t* lk = h->links + kGhost;
+    int parity = h->cur;
+    void* args[] = {(void*)&f0, (void*)&f1, (void*)&lk, (void*)&h->dprm, (void*)&h->dacc, (void*)&h->dobs,
+                    (void*)&g, (void*)&nsteps, (void*)&parity};
+    return cudaLaunchCooperativeKernel((const void*)step_persist_kernel<S, kBX>, dim3(h->persist_ctas), dim3(kBX),
+                                       args, 0, h->stream);
+}
+
+cudaError_t launch_persist(lbm_t* h, int nsteps) {
+    switch (h->p.precision) {
+        case LBM_FP64: return launch_persist_t<double>(h, nsteps);
+        case LBM_FP32: return launch_persist_t<float>(h, nsteps);
+        case LBM_FP32C: return launch_persist_t<f32c>(h, nsteps);
+        case LBM_FP16S: return launch_persist_t<__half>(h, nsteps);
+        default: return launch_persist_t<__nv_bfloat16>(h, nsteps);
+    }
+}
+
+template <typename S>
+int persist_occupancy() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_persist_kernel<S, kBX>, kBX, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+int persist_occupancy_of(int prec) {
+    switch (prec) {
+        case LBM_FP64: return persist_occupancy<double>();
+        case LBM_FP32: return persist_occupancy<float>();
+        case LBM_FP32C: return persist_occupancy<f32c>();
+        case LBM_FP16S: return persist_occupancy<__half>();
+        default: return persist_occupancy<__nv_bfloat16>();
+    }
+}
+
+// Tiles of `rpb` rows for the persistent march, and a cooperative grid no
+// larger than what is resident.
+void set_persist_tiles(lbm_t* h, int rpb, int resident) {
+    h->persist_rpb = std::max(1, std::min(rpb, h->p.ny));
+    const int ntiles = h->ncb * ((h->p.ny + h->persist_rpb - 1) / h->persist_rpb);
+    h->persist_ctas = std::min(ntiles, resident);
+}
+
+// Whether this handle steps with the persistent launch, and with which tile
+// height.  With enough steps at hand, after one untimed launch of each path
+// (the graph's upload and the lazy loading of the cooperative kernel's
+// module are not part of a step), it times 32 steps through the captured
+// graph (unless variant 5 forces the persistent launch) and 16 steps of the
+// persistent launch for tiles of 1, 2, 4 and 8 rows, and keeps the fastest;
+// every timed launch advances the simulation by an even number of steps (the
+// marches give the same bits up to the order of a few sums).  Otherwise
+// (variant 5 and fewer steps) it takes 4-row tiles, or enough rows for one
+// wave of resident CTAs.  *left is reduced by the steps taken.
+int decide_persist(lbm_t* h, int64_t* left) {
+    int dev = 0, coop = 0, sms = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int occ = persist_occupancy_of(h->p.precision);
+    cudaGetLastError();
+    const bool forced = h->p.variant == 5;
+    if (!coop || occ < 1) {
+        if (forced) return fail(h, LBM_ECUDA, "cooperative launches are not available");
+        h->persist = -1;
+        return LBM_OK;
+    }
+    const int resident = occ * sms;
+    const int64_t rows = (int64_t)h->ncb * h->p.ny;
+    const int rpb_wave = (int)std::max<int64_t>(4, (rows + resident - 1) / resident);
+    constexpr int kCand[4] = {1, 2, 4, 8};
+    constexpr int kTimed = 16;
+    const int64_t need = (forced ? 0 : 2 * kGraphSteps) + 2 + 4 * kTimed;
+    if (forced && *left < need) {
+        set_persist_tiles(h, rpb_wave, resident);
+        h->persist = 1;
+        return LBM_OK;
+    }
+    if (!forced && !h->graph[h->cur]) {
+        int rc = build_graph(h, h->cur);
+        if (rc) return rc;
+    }
+    if (!forced) CUDA_TRY(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+    set_persist_tiles(h, kCand[0], resident);
+    CUDA_TRY(h, launch_persist(h, 2));
+    cudaEvent_t ev[6];
+    for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
+    CUDA_TRY(h, cudaEventRecord(ev[0], h->stream));
+    if (!forced) CUDA_TRY(h, cudaGraphLaunch(h->graph[h->cur], h->stream));   // 32 steps: the parity is unchanged
+    CUDA_TRY(h, cudaEventRecord(ev[1], h->stream));
+    for (int c = 0; c < 4; c++) {
+        set_persist_tiles(h, kCand[c], resident);
+        CUDA_TRY(h, launch_persist(h, kTimed));
+        CUDA_TRY(h, cudaEventRecord(ev[2 + c], h->stream));
+    }
+    CUDA_TRY(h, cudaEventSynchronize(ev[5]));
+    float t_graph = 0.f;
+    CUDA_TRY(h, cudaEventElapsedTime(&t_graph, ev[0], ev[1]));
+    float best = 0.f;
+    int best_rpb = kCand[0];
+    for (int c = 0; c < 4; c++) {
+        float t = 0.f;
+        CUDA_TRY(h, cudaEventElapsedTime(&t, ev[1 + c], ev[2 + c]));
+        if (c == 0 || t < best) {
+            best = t;
+            best_rpb = kCand[c];
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    *left -= need;
+    set_persist_tiles(h, best_rpb, resident);
+    h->persist = (forced || best / kTimed < t_graph / kGraphSteps) ? 1 : -1;
+    return LBM_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -849,6 +982,23 @@ int lbm_step(lbm_t* h, int64_t nsteps) {
     if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
     if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps < 0");
     int64_t left = nsteps;
+    // small grids: many steps per cooperative launch, when that beats one
+    // graph node per step (decided once per handle by timing both: 130
+    // steps in all)
+    if (h->persist == 0 && ((h->p.variant == 0 && left >= 160 && h->fluid_nodes <= kPersistMaxFluid) ||
+                            h->p.variant == 5)) {
+        int rc = decide_persist(h, &left);
+        if (rc) return rc;
+    }
+    if (h->persist == 1) {
+        while (left > 0) {
+            const int n = (int)std::min<int64_t>(left, kPersistChunk);
+            CUDA_TRY(h, launch_persist(h, n));
+            if (n & 1) h->cur = 1 - h->cur;
+            left -= n;
+        }
+        return LBM_OK;
+    }
     if (left >= kGraphSteps) {
         if (!h->graph[h->cur]) {
             int rc = build_graph(h, h->cur);
@@ -1001,6 +1151,14 @@ int lbm_load(lbm_t* h, const double* f) {
 
 int lbm_kernel_info(const lbm_t* h, int32_t info[5]) {
     if (!h || !info) return fail(nullptr, LBM_EINVAL, "NULL argument");
+    if (h->persist == 1) {
+        info[0] = 5;
+        info[1] = 0;
+        info[2] = h->persist_rpb;
+        info[3] = h->persist_ctas;
+        info[4] = 0;
+        return LBM_OK;
+    }
     info[0] = h->tune.variant;
     info[1] = h->tune.variant >= 2 ? h->tune.depth : 0;
     info[2] = h->tune.variant == 1 ? h->tune.rpb : h->tune.bx;

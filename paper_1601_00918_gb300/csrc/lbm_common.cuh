@@ -76,7 +76,19 @@ struct f32c {
 static_assert(sizeof(f32c) == 4 && alignof(f32c) == 4, "f32c must be laid out as a float");
 
 using ::__ldg;
+using ::__ldcg;
 __device__ __forceinline__ f32c __ldg(const f32c* p) { return f32c(::__ldg(reinterpret_cast<const float*>(p))); }
+__device__ __forceinline__ f32c __ldcg(const f32c* p) { return f32c(::__ldcg(reinterpret_cast<const float*>(p))); }
+
+// Population load of a march: through the read-only cache (kCoherent =
+// false: the buffer is not written during the launch), or cached in L2 only
+// (kCoherent = true: a persistent launch writes in one step the buffer it
+// reads in the next, and L1 is not kept coherent with other SMs' writes).
+template <bool kCoherent, typename S>
+__device__ __forceinline__ S load_pop(const S* p) {
+    if constexpr (kCoherent) return __ldcg(p);
+    else return __ldg(p);
+}
 
 // ---------------------------------------------------------------------------
 // storage codecs

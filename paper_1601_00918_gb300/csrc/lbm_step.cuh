@@ -27,6 +27,8 @@
 // This variant also computes the macroscopic fields (FIELDS = true).
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "lbm_common.cuh"
 
 namespace gb300lbm {
@@ -39,7 +41,9 @@ namespace gb300lbm {
 // fin, fout and links point at logical column 0 of row 0.  periodic_x only
 // controls the ghost images written for the staged kernel's row windows
 // (pass 0 for a layout without ghost columns); pulls wrap in x and y.
-template <typename S, int BX, bool FIELDS>
+// kCoherent: populations are loaded through L2 only (load_pop), for a
+// persistent launch that reads what it wrote in the previous step.
+template <typename S, int BX, bool FIELDS, bool kCoherent = false>
 __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __restrict__ fout,
                                              const uint16_t* __restrict__ links,
                                              const NodeParams<typename Codec<S>::R>& P,
@@ -102,11 +106,11 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
             // weight for i and opp(i))
             R r0s = R(0), r1s = R(0);
             if (C::kNodeShift) {
-                r0s = C::rho_value(__ldg(fin + 18 * plane + nd[i]));
-                r1s = C::rho_value(__ldg(fin + 19 * plane + nd[i]));
+                r0s = C::rho_value(load_pop<kCoherent>(fin + 18 * plane + nd[i]));
+                r1s = C::rho_value(load_pop<kCoherent>(fin + 19 * plane + nd[i]));
             }
-            f[0][i] = C::decode(__ldg(fin + pl[i] * plane + nd[i]), wgt<R>(i), r0s);
-            f[1][i] = C::decode(__ldg(fin + (9 + pl[i]) * plane + nd[i]), wgt<R>(i), r1s);
+            f[0][i] = C::decode(load_pop<kCoherent>(fin + pl[i] * plane + nd[i]), wgt<R>(i), r0s);
+            f[1][i] = C::decode(load_pop<kCoherent>(fin + (9 + pl[i]) * plane + nd[i]), wgt<R>(i), r1s);
         }
         density_of<C>(f[0], r0, l0);
         density_of<C>(f[1], r1, l1);
@@ -132,8 +136,8 @@ __device__ __forceinline__ void march_simple(const S* __restrict__ fin, S* __res
             const int node = bb ? y * pitch + hx : syp * pitch + sxp;
             const int pln = bb ? d2q9_opp(i) : i;
             R rs = R(0);
-            if (C::kNodeShift) rs = C::rho_value(__ldg(fin + (18 + sp) * plane + node));
-            v = C::decode(__ldg(fin + (sp * 9 + pln) * plane + node), wgt<R>(i), rs);
+            if (C::kNodeShift) rs = C::rho_value(load_pop<kCoherent>(fin + (18 + sp) * plane + node));
+            v = C::decode(load_pop<kCoherent>(fin + (sp * 9 + pln) * plane + node), wgt<R>(i), rs);
         }
         v = halfwarp_density<C>(v);
         if ((lane & 15) == 0) {
@@ -245,6 +249,44 @@ __global__ void __launch_bounds__(BX) step_simple_kernel(const S* __restrict__ f
                                 x0, y0, y1, grid.row_begin, grid.row_end - grid.row_begin, ob, s_rho);
     if (FIELDS) return;
     reduce_observables<R, BX>(ob, acc, obs, false);
+}
+
+// Many steps of one small grid in one launch: a cooperative grid of
+// resident CTAs, each marching its share of the (128-column block, row
+// strip) tiles of a step, then a grid-wide barrier before the next step
+// (steps alternate between f0 and f1 starting from `parity`).  Populations
+// are loaded through L2 (the buffer read in step s + 1 is written in step
+// s); every CTA reduces its observables once per step.  For grids whose
+// steps are a few microseconds of work, this replaces one launch (or graph
+// node) per step.
+template <typename S, int BX>
+__global__ void __launch_bounds__(BX) step_persist_kernel(S* f0, S* f1, const uint16_t* __restrict__ links,
+                                                          const StepParams* __restrict__ prm, ObsAccum* __restrict__ acc,
+                                                          ObsState* __restrict__ obs, Grid grid, int nsteps, int parity) {
+    using R = typename Codec<S>::R;
+    __shared__ pair_t<R> s_rho[4][BX + 2];
+    NodeParams<R> P;
+    P.load(prm);
+    const int ncb = (grid.nx + BX - 1) / BX;
+    const int nstrip = (grid.ny + grid.rows_per_block - 1) / grid.rows_per_block;
+    const int ntiles = ncb * nstrip;
+    cooperative_groups::grid_group gg = cooperative_groups::this_grid();
+    for (int s = 0; s < nsteps; s++) {
+        const bool odd = ((parity + s) & 1) != 0;
+        const S* fin = odd ? f1 : f0;
+        S* fout = odd ? f0 : f1;
+        ObsLocal<R> ob;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int x0 = (tile % ncb) * BX;
+            const int y0 = (tile / ncb) * grid.rows_per_block;
+            const int y1 = min(y0 + grid.rows_per_block, grid.ny);
+            march_simple<S, BX, false, true>(fin, fout, links, P, nullptr, grid.nx, grid.ny, grid.pitch,
+                                             grid.periodic_x, x0, y0, y1, 0, 0, ob, s_rho);
+            __syncthreads();   // the next tile's prologue reuses the density ring
+        }
+        reduce_observables<R, BX>(ob, acc, obs, false, gridDim.x);
+        gg.sync();
+    }
 }
 
 }  // namespace gb300lbm

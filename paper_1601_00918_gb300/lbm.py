@@ -239,7 +239,7 @@ def _check(rc, handle=None):
     return rc
 
 
-VARIANTS = {"auto": 0, "simple": 1, "staged": 2, "pipelined": 3, "private": 4}
+VARIANTS = {"auto": 0, "simple": 1, "staged": 2, "pipelined": 3, "private": 4, "persistent": 5}
 COLLISIONS = {"bgk": 0, "regularized": 1}
 
 
@@ -328,6 +328,8 @@ def lbm_kernel_info(h) -> dict:
     _check(library().lbm_kernel_info(h, info), h)
     if info[0] == 1:
         return {"variant": "simple", "rows_per_cta": info[2]}
+    if info[0] == 5:
+        return {"variant": "persistent", "rows_per_tile": info[2], "ctas": info[3]}
     d = {"variant": {2: "staged", 3: "pipelined", 4: "private"}[info[0]], "depth": info[1], "cols_per_cta": info[2],
          "strips": info[3]}
     if info[0] == 2:

@@ -69,7 +69,7 @@ def test_too_large_grid_rejected(lib):
     dict(eq_order=4),
     dict(precision=9),
     dict(periodic=(True, False)),            # open in y without solid rows
-    dict(variant=5),
+    dict(variant=6),                         # 5 = persistent is the last kernel
     dict(collision=2),
 ])
 def test_create_rejects_bad_parameters(lib, bad):

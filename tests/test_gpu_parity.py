@@ -387,6 +387,28 @@ def test_shifted_16bit_storage_error(lbm, precision, bound):
     assert obs["nan_flag"] == 0
 
 
+@pytest.mark.parametrize("precision,rho_bound,u_bound", [("fp16s", 5e-4, 8e-3), ("bf16s", 2.5e-2, 1.2e-1)])
+@pytest.mark.parametrize("case", ["channel", "droplet"])
+def test_shifted_16bit_storage_error_1000_steps(lbm, precision, rho_bound, u_bound, case):
+    """The 16-bit shifted storage over 1000 steps (the FP32 contract's
+    horizon), channel and droplet, against the FP64 oracle: the paper fixes
+    no bound for it, so the test states the measured error with a factor-2
+    margin (relative L-infinity: FP16-shifted rho 2.4e-4 / 3.4e-4, u 3.8e-3 /
+    3.1e-3; BF16-shifted rho 1.2e-2 / 3.2e-3, u 6e-2 / 3e-2), and the masses
+    to the rounding of the stored populations."""
+    mask, rho, kw = channel() if case == "channel" else droplet_case()
+    _, obs, (rho_g, u_g, _) = gpu_run(lbm, mask, rho, 1000, precision, **kw)
+    P = oracle.Problem(mask, **kw)
+    f_ref, hist = P.run(P.init(rho), 1000, history=True)
+    rho_r, u_r, _ = P.fields(f_ref)
+    err_rho = np.max(np.abs(rho_g - rho_r)) / np.max(rho_r)
+    err_u = np.max(np.abs(u_g - u_r)) / np.max(np.abs(u_r))
+    assert err_rho < rho_bound, err_rho
+    assert err_u < u_bound, err_u
+    np.testing.assert_allclose(obs["mass"], hist[-1, :2], rtol=1e-4 if precision == "fp16s" else 1e-3)
+    assert obs["nan_flag"] == 0
+
+
 # ----------------------------------------------------------------------------
 # full size: 8192 x 1170 sinusoidal channel, the benchmark's launch shape
 # ----------------------------------------------------------------------------
@@ -464,3 +486,55 @@ def test_fp32_regularized_channel_1000_steps(lbm, prec):
     assert err_u <= U_BOUND[prec], err_u
     np.testing.assert_allclose(obs["mass"], hist[-1, :2], rtol=1e-6)
 
+
+
+# ----------------------------------------------------------------------------
+# the persistent multi-step launch (small grids)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,atol", [("fp64", 1e-12), ("fp32", 5e-6), ("fp32c", 5e-6)])
+@pytest.mark.parametrize("steps", [1, 33, 250])
+def test_persistent_launch_matches_oracle(lbm, precision, atol, steps):
+    """variant 5: many steps per cooperative launch with a grid-wide barrier
+    between them (populations loaded through L2, since each step reads what
+    the previous one wrote), on the channel (ragged column blocks, walls,
+    potentials), odd step counts included: the populations after 1, 33 and
+    250 steps agree with the FP64 oracle (FP64 to 1e-12; FP32 after 250 steps
+    to the FP32 step's own bound), the observables count every step, and the
+    FP32 result equals the simple kernel's bit for bit (the same march)."""
+    mask, rho, kw = channel()
+    f_p, obs, _ = gpu_run(lbm, mask, rho, steps, precision, "persistent", **kw)
+    P = oracle.Problem(mask, **kw)
+    f_ref, hist = P.run(P.init(rho), steps, history=True)
+    tol = atol if steps < 100 or precision == "fp64" else 2e-5
+    np.testing.assert_allclose(f_p, f_ref, rtol=0, atol=tol)
+    assert obs["step"] == steps and obs["nan_flag"] == 0 and obs["timeout_flag"] == 0
+    np.testing.assert_allclose(obs["mass"], hist[-1, :2], rtol=1e-12 if precision == "fp64" else 1e-6)
+    # the displacement is a ratio of small momenta to masses summed from
+    # FP32 populations: the FP32 observables' bound of the 1000-step test
+    disp_tol = dict(rtol=1e-9, atol=1e-14) if precision == "fp64" else dict(rtol=1e-3, atol=1e-7)
+    np.testing.assert_allclose(obs["oil_disp_x"], np.sum(hist[:, 2] / hist[:, 0]), **disp_tol)
+    if precision != "fp64":
+        f_s, _, _ = gpu_run(lbm, mask, rho, steps, precision, "simple", **kw)
+        np.testing.assert_array_equal(f_p, f_s)
+
+
+def test_persistent_launch_is_chosen_only_when_faster(lbm):
+    """With the automatic variant the library times the persistent launch
+    against the graph path on a small grid; whichever it keeps, 200 steps
+    give the populations of the explicit simple kernel (to a few FP32
+    rounding units: a tuned kernel may sum halo densities in another order)
+    and the kernel info names the choice."""
+    mask, rho = wl.periodic_box(128, 128), wl.droplet(128, 128, 20.0, 64.0, 64.0)
+    kw = dict(tau=(1.0, 1.0), G=G)
+    sim = lbm.Simulation(mask, rho, precision="fp32", **kw)
+    try:
+        sim.step(200)
+        f_a = sim.save()
+        info = sim.kernel_info()
+        obs = sim.observables()
+    finally:
+        sim.close()
+    f_s, _, _ = gpu_run(lbm, mask, rho, 200, "fp32", "simple", **kw)
+    np.testing.assert_allclose(f_a, f_s, rtol=0, atol=5e-6)
+    assert obs["step"] == 200
+    assert info["variant"] in ("persistent", "simple", "staged", "pipelined", "private")
