@@ -33,67 +33,12 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "lbm_handle.cuh"
 #include "lbm_step.cuh"
-#include "lbm_step_tma.cuh"
-#include "lbm_step_warp.cuh"
 #include "lbm_step_private.cuh"
 #include "lbm_setup.cuh"
 
 using namespace gb300lbm;
-
-namespace {
-
-constexpr int kBX = 128;         // columns per CTA of the simple kernel
-constexpr int kRowBlock = 64;    // column granularity of the fluid-row table
-constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity is kept)
-
-struct Tuned {
-    int variant = 1;   // 1 simple, 2 staged, 3 pipelined, 4 private
-    int depth = 2;     // staged: rows in flight
-    int rpb = 16;      // simple: rows per CTA strip
-    int strips = 1;    // staged: strips per column block
-    int bx = 128;      // staged: columns per CTA (64 or 128)
-    int strip_abs = 0; // staged: strips at absolute rows (Grid::strip_rows)
-};
-
-}  // namespace
-
-struct lbm_t {
-    lbm_params p{};
-    int pitch = 0;
-    int ncb = 0;                  // 128-column blocks
-    int nrb = 0;                  // 64-column blocks of the fluid-row table
-    size_t elem = 0;              // bytes per stored population
-    size_t buf_bytes = 0;         // one population buffer
-    void* arena = nullptr;
-    bool own_arena = false;
-    char* fbase[2] = {nullptr, nullptr};   // buffer starts (storage column 0)
-    int cur = 0;                  // fbase[cur] holds the current stored state
-    uint16_t* links = nullptr;    // storage column 0 of row 0
-    int2* rows = nullptr;
-    StepParams* dprm = nullptr;
-    ObsAccum* dacc = nullptr;
-    ObsState* dobs = nullptr;
-    ObsAccum* tacc = nullptr;     // autotuning scratch
-    ObsState* tobs = nullptr;
-    StepParams hprm{};
-    cudaStream_t stream = nullptr;
-    cudaStream_t capture = nullptr;       // private stream for graph capture
-    CUtensorMap fmap[2][2];       // [buffer][box width 64 + 16 or 128 + 16] (pipelined kernel)
-    CUtensorMap lmap[2];          // link words, box width 64 + 16 or 128 + 16
-    CUtensorMap smap[2][2];       // [buffer][64 or 128 columns] windows of the staged kernel
-    CUtensorMap pmap[2];          // [buffer] per-warp windows of the private kernel
-    CUtensorMap plmap;
-    bool maps_ok = false;
-    Tuned tune;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int64_t fluid_nodes = 0;
-    // persistent multi-step launches (small grids): 0 undecided, 1 used, -1 not used
-    int persist = 0;
-    int persist_rpb = 8;          // rows per tile of the persistent march
-    int persist_ctas = 0;         // resident CTAs of one cooperative launch
-    std::string err;
-};
 
 namespace {
 
@@ -165,147 +110,12 @@ bool layout_of(const lbm_params* p, Layout* L) {
 // ---------------------------------------------------------------------------
 // launches
 // ---------------------------------------------------------------------------
-Grid make_grid(const lbm_t* h, int row_begin, int row_end) {
-    Grid g;
-    g.nx = h->p.nx;
-    g.ny = h->p.ny;
-    g.pitch = h->pitch;
-    g.periodic_x = h->p.periodic_x;
-    g.rows_per_block = h->tune.rpb;
-    g.row_begin = row_begin;
-    g.row_end = row_end;
-    g.strips = h->tune.strips;
-    g.strip_rows = 0;
-    return g;
-}
-
-template <typename S>
-S* at_col0(char* base) {
-    return (S*)base + kGhost;
-}
-
-template <typename S, int BX, int D>
-cudaError_t launch_staged(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs,
-                          cudaStream_t st) {
-    using Plan = StagedPlan<S, BX, D>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(step_staged_kernel<S, BX, D>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Plan::kBytes);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
-    Grid g = make_grid(h, 0, h->p.ny);
-    g.strips = tn.strips;
-    g.strip_rows = tn.strip_abs ? (h->p.ny + tn.strips - 1) / tn.strips : 0;
-    dim3 grid((h->p.nx + BX - 1) / BX, tn.strips);
-    step_staged_kernel<S, BX, D><<<grid, BX, Plan::kBytes, st>>>(
-        h->smap[src][BX == 64 ? 0 : 1], h->lmap[BX == 64 ? 0 : 1], at_col0<S>(h->fbase[1 - src]), h->rows,
-        h->dprm, acc, obs, g);
-    return cudaGetLastError();
-}
-
-template <typename S, int BX, int D>
-cudaError_t launch_pipelined(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs,
-                             cudaStream_t st) {
-    using Plan = WarpPlan<S, BX, D>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(step_warp_kernel<S, BX, D>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Plan::kBytes);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
-    Grid g = make_grid(h, 0, h->p.ny);
-    g.strips = tn.strips;
-    dim3 grid((h->p.nx + BX - 1) / BX, tn.strips);
-    step_warp_kernel<S, BX, D><<<grid, BX, Plan::kBytes, st>>>(
-        h->fmap[src][BX == 64 ? 0 : 1], h->lmap[BX == 64 ? 0 : 1], at_col0<S>(h->fbase[1 - src]), h->rows,
-        h->dprm, acc, obs, g);
-    return cudaGetLastError();
-}
-
-template <typename S, int BX, int D>
-cudaError_t launch_private(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs,
-                           cudaStream_t st) {
-    using Plan = PrivatePlan<S, BX / 32, D>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(step_private_kernel<S, BX, D>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Plan::kBytes);
-        if (e != cudaSuccess) return e;
-        attr_done = true;
-    }
-    Grid g = make_grid(h, 0, h->p.ny);
-    g.strips = tn.strips;
-    dim3 grid((h->p.nx + BX - 1) / BX, tn.strips);
-    step_private_kernel<S, BX, D><<<grid, BX, Plan::kBytes, st>>>(
-        h->pmap[src], h->plmap, at_col0<S>(h->fbase[1 - src]), h->rows, h->dprm, acc, obs, g);
-    return cudaGetLastError();
-}
-
-template <typename S>
-cudaError_t launch_one(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs, cudaStream_t st) {
-    if (tn.variant == 4) {
-        if (tn.bx == 64) {
-            if (tn.depth >= 2) return launch_private<S, 64, 2>(h, src, tn, acc, obs, st);
-            return launch_private<S, 64, 1>(h, src, tn, acc, obs, st);
-        }
-        if (tn.depth >= 2) return launch_private<S, 128, 2>(h, src, tn, acc, obs, st);
-        return launch_private<S, 128, 1>(h, src, tn, acc, obs, st);
-    }
-    if (tn.variant == 3) {
-        if (tn.bx == 64) {
-            if (tn.depth >= 2) return launch_pipelined<S, 64, 2>(h, src, tn, acc, obs, st);
-            return launch_pipelined<S, 64, 1>(h, src, tn, acc, obs, st);
-        }
-        if (tn.depth >= 2) return launch_pipelined<S, 128, 2>(h, src, tn, acc, obs, st);
-        return launch_pipelined<S, 128, 1>(h, src, tn, acc, obs, st);
-    }
-    if (tn.variant == 2) {
-        if (tn.bx == 64) {
-            if (tn.depth >= 2) return launch_staged<S, 64, 2>(h, src, tn, acc, obs, st);
-            return launch_staged<S, 64, 1>(h, src, tn, acc, obs, st);
-        }
-        if (tn.depth >= 2) return launch_staged<S, 128, 2>(h, src, tn, acc, obs, st);
-        return launch_staged<S, 128, 1>(h, src, tn, acc, obs, st);
-    }
-    Grid g = make_grid(h, 0, h->p.ny);
-    g.rows_per_block = tn.rpb;
-    dim3 grid(h->ncb, (h->p.ny + tn.rpb - 1) / tn.rpb);
-    step_simple_kernel<S, kBX, false><<<grid, kBX, 0, st>>>(
-        at_col0<S>(h->fbase[src]), at_col0<S>(h->fbase[1 - src]), h->links + kGhost, h->dprm, acc, obs,
-        nullptr, g);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_step(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs, cudaStream_t st) {
-    switch (h->p.precision) {
-        case LBM_FP64: return launch_one<double>(h, src, tn, acc, obs, st);
-        case LBM_FP32: return launch_one<float>(h, src, tn, acc, obs, st);
-        case LBM_FP32C: return launch_one<f32c>(h, src, tn, acc, obs, st);
-        case LBM_FP16S: return launch_one<__half>(h, src, tn, acc, obs, st);
-        default: return launch_one<__nv_bfloat16>(h, src, tn, acc, obs, st);
-    }
-}
-
-template <typename S>
-cudaError_t launch_fields_t(lbm_t* h, double* out, int rb, int re) {
-    Grid g = make_grid(h, rb, re);
-    g.rows_per_block = 8;
-    dim3 grid(h->ncb, (re - rb + 7) / 8);
-    step_simple_kernel<S, kBX, true><<<grid, kBX, 0, h->stream>>>(
-        at_col0<S>(h->fbase[h->cur]), nullptr, h->links + kGhost, h->dprm, h->dacc, h->dobs, out, g);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fields(lbm_t* h, double* out, int rb, int re) {
-    switch (h->p.precision) {
-        case LBM_FP64: return launch_fields_t<double>(h, out, rb, re);
-        case LBM_FP32: return launch_fields_t<float>(h, out, rb, re);
-        case LBM_FP32C: return launch_fields_t<f32c>(h, out, rb, re);
-        case LBM_FP16S: return launch_fields_t<__half>(h, out, rb, re);
-        default: return launch_fields_t<__nv_bfloat16>(h, out, rb, re);
+    switch (tn.variant) {
+        case 2: return launch_staged_any(h, src, tn, acc, obs, st);
+        case 3: return launch_pipelined_any(h, src, tn, acc, obs, st);
+        case 4: return launch_private_any(h, src, tn, acc, obs, st);
+        default: return launch_simple_any(h, src, tn, acc, obs, st);
     }
 }
 
@@ -424,36 +234,10 @@ int sms_of_device() {
     return n > 0 ? n : 152;
 }
 
-// Resident CTAs per SM of one launch configuration (0 if it cannot launch).
-template <typename K>
-int occupancy_of(K kernel, int threads, int smem) {
-    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) return 0;
-    return n;
-}
-
-template <typename S, int BX, int D>
-int occupancy_tma(int var) {
-    if (var == 2) return occupancy_of(step_staged_kernel<S, BX, D>, BX, StagedPlan<S, BX, D>::kBytes);
-    if (var == 3) return occupancy_of(step_warp_kernel<S, BX, D>, BX, WarpPlan<S, BX, D>::kBytes);
-    return occupancy_of(step_private_kernel<S, BX, D>, BX, PrivatePlan<S, BX / 32, D>::kBytes);
-}
-
-template <typename S>
-int occupancy_prec(int var, int bx, int depth) {
-    if (bx == 64) return depth >= 2 ? occupancy_tma<S, 64, 2>(var) : occupancy_tma<S, 64, 1>(var);
-    return depth >= 2 ? occupancy_tma<S, 128, 2>(var) : occupancy_tma<S, 128, 1>(var);
-}
-
 int occupancy(const lbm_t* h, int var, int bx, int depth) {
-    switch (h->p.precision) {
-        case LBM_FP64: return occupancy_prec<double>(var, bx, depth);
-        case LBM_FP32: return occupancy_prec<float>(var, bx, depth);
-        case LBM_FP32C: return occupancy_prec<f32c>(var, bx, depth);
-        case LBM_FP16S: return occupancy_prec<__half>(var, bx, depth);
-        default: return occupancy_prec<__nv_bfloat16>(var, bx, depth);
-    }
+    if (var == 2) return occupancy_staged(h->p.precision, bx, depth);
+    if (var == 3) return occupancy_pipelined(h->p.precision, bx, depth);
+    return occupancy_private(h->p.precision, bx, depth);
 }
 
 std::vector<Tuned> candidates(const lbm_t* h) {
@@ -715,46 +499,6 @@ namespace {
 constexpr int64_t kPersistMaxFluid = int64_t(1) << 21;   // grids the persistent path is tried on
 constexpr int kPersistChunk = 4096;                      // steps per cooperative launch
 
-template <typename S>
-cudaError_t launch_persist_t(lbm_t* h, int nsteps) {
-    Grid g = make_grid(h, 0, h->p.ny);
-    g.rows_per_block = h->persist_rpb;
-    S* f0 = at_col0<S>(h->fbase[0]);
-    S* f1 = at_col0<S>(h->fbase[1]);
-    const uint16_t* lk = h->links + kGhost;
-    int parity = h->cur;
-    void* args[] = {(void*)&f0, (void*)&f1, (void*)&lk, (void*)&h->dprm, (void*)&h->dacc, (void*)&h->dobs,
-                    (void*)&g, (void*)&nsteps, (void*)&parity};
-    return cudaLaunchCooperativeKernel((const void*)step_persist_kernel<S, kBX>, dim3(h->persist_ctas), dim3(kBX),
-                                       args, 0, h->stream);
-}
-
-cudaError_t launch_persist(lbm_t* h, int nsteps) {
-    switch (h->p.precision) {
-        case LBM_FP64: return launch_persist_t<double>(h, nsteps);
-        case LBM_FP32: return launch_persist_t<float>(h, nsteps);
-        case LBM_FP32C: return launch_persist_t<f32c>(h, nsteps);
-        case LBM_FP16S: return launch_persist_t<__half>(h, nsteps);
-        default: return launch_persist_t<__nv_bfloat16>(h, nsteps);
-    }
-}
-
-template <typename S>
-int persist_occupancy() {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_persist_kernel<S, kBX>, kBX, 0) != cudaSuccess) return 0;
-    return n;
-}
-
-int persist_occupancy_of(int prec) {
-    switch (prec) {
-        case LBM_FP64: return persist_occupancy<double>();
-        case LBM_FP32: return persist_occupancy<float>();
-        case LBM_FP32C: return persist_occupancy<f32c>();
-        case LBM_FP16S: return persist_occupancy<__half>();
-        default: return persist_occupancy<__nv_bfloat16>();
-    }
-}
 
 // Tiles of `rpb` rows for the persistent march, and a cooperative grid no
 // larger than what is resident.
