@@ -167,7 +167,8 @@ int lbm_load(lbm_t *h, const double *f);
  * info[0] = variant (1 simple, 2 staged, 3 pipelined, 4 private, 5
  * persistent: then info[2] = rows per tile, info[3] = CTAs of the
  * cooperative launch); info[1] =
- * rows in flight (variants 2..4); info[2] = rows per CTA strip (variant 1)
+ * rows issued ahead of the three a march reads (1 or 2, variants 2..4);
+ * info[2] = rows per CTA strip (variant 1)
  * or columns per CTA (2..4); info[3] = strips per column block (2..4);
  * info[4] = 1 when the staged kernel's strips sit at the same absolute rows
  * in every column block, 0 when each block's fluid rows are split into

@@ -144,7 +144,7 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
 // Staged step of the batch: one CTA per tile.  maps holds three tensor maps
 // per instance (populations of region A, of region B, link words).
 template <typename S>
-__global__ void __launch_bounds__(kTileX, sizeof(S) == 4 ? 5 : 4)
+__global__ void __launch_bounds__(kTileX, sizeof(S) == 8 ? 4 : 5)
     batch_staged_kernel(BatchInst* __restrict__ inst, const BatchTile* __restrict__ tiles, const CUtensorMap* maps,
                         S* __restrict__ fa, S* __restrict__ fb, int parity) {
     using R = typename Codec<S>::R;

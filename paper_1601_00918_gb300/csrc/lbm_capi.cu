@@ -293,7 +293,7 @@ std::vector<Tuned> candidates(const lbm_t* h) {
     return u;
 }
 
-// GB300LBM_TUNE="staged,<cols per CTA>,<rows in flight>,<strips>[,abs]"
+// GB300LBM_TUNE="staged,<cols per CTA>,<rows ahead: 1 or 2>,<strips>[,abs]"
 // (",abs": strips at absolute rows; likewise "pipelined,..." and
 // "private,..." without it) or "simple,<rows per strip>"
 // pins the launch configuration (no timing); used to profile one

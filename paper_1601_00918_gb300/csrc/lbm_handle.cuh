@@ -22,7 +22,7 @@ constexpr int kGraphSteps = 32;  // steps per captured graph (even: parity is ke
 
 struct Tuned {
     int variant = 1;   // 1 simple, 2 staged, 3 pipelined, 4 private
-    int depth = 2;     // staged: rows in flight
+    int depth = 2;     // staged: rows issued ahead of the three in use (1 or 2)
     int rpb = 16;      // simple: rows per CTA strip
     int strips = 1;    // staged: strips per column block
     int bx = 128;      // staged: columns per CTA (64 or 128)

@@ -37,13 +37,16 @@ cudaError_t launch_prec(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsSt
     return launch_staged<S, 128, 1>(h, src, tn, acc, obs, st);
 }
 
+template <typename S, int BX, int D>
+int occupancy_one() {
+    return occupancy_of(step_staged_kernel<S, BX, D>, BX, StagedPlan<S, BX, D>::kBytes);
+}
+
 template <typename S>
 int occupancy_prec(int bx, int depth) {
     if (bx == 64)
-        return depth >= 2 ? occupancy_of(step_staged_kernel<S, 64, 2>, 64, StagedPlan<S, 64, 2>::kBytes)
-                          : occupancy_of(step_staged_kernel<S, 64, 1>, 64, StagedPlan<S, 64, 1>::kBytes);
-    return depth >= 2 ? occupancy_of(step_staged_kernel<S, 128, 2>, 128, StagedPlan<S, 128, 2>::kBytes)
-                      : occupancy_of(step_staged_kernel<S, 128, 1>, 128, StagedPlan<S, 128, 1>::kBytes);
+        return depth >= 2 ? occupancy_one<S, 64, 2>() : occupancy_one<S, 64, 1>();
+    return depth >= 2 ? occupancy_one<S, 128, 2>() : occupancy_one<S, 128, 1>();
 }
 
 }  // namespace

@@ -141,9 +141,11 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
     unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     uint64_t* bars = (uint64_t*)(smem + Plan::kBarOffset);
     pair_t<R>(*s_rho)[BX + 2] = (pair_t<R>(*)[BX + 2])(smem + Plan::kRhoOffset);
-    auto pops = [&](int stage) { return (const S*)(smem + (stage % NS) * Plan::kSlot); };
+    // stage indices are never negative: unsigned arithmetic keeps the ring
+    // index a plain mask (or a multiply-shift for rings of 3 or 5 slots)
+    auto pops = [&](int stage) { return (const S*)(smem + ((unsigned)stage % NS) * Plan::kSlot); };
     auto lnks = [&](int stage) {
-        return (const uint16_t*)(smem + (stage % NS) * Plan::kSlot + Plan::kPopSlot);
+        return (const uint16_t*)(smem + ((unsigned)stage % NS) * Plan::kSlot + Plan::kPopSlot);
     };
 
     const int plane = ny * pitch;
@@ -174,7 +176,7 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
     next_row = next_row < 0 ? next_row + ny : next_row;
     auto issue = [&]() {
         const int j = next_issue++;
-        uint64_t* bar = &bars[j % NS];
+        uint64_t* bar = &bars[(unsigned)j % NS];
         mbar_expect_tx(bar, Plan::kTxBytes);
         tma_load_3d((void*)pops(j), fmap, x0 + kGhost - Plan::kLead, next_row, 0, bar);
         tma_load_2d((void*)lnks(j), lmap, x0 + kGhost - Plan::kLinkLead, next_row, bar);
@@ -183,7 +185,7 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
     };
     // after one wait gave up the data is invalid anyway: skip the others
     auto wait_stage = [&](int j) {
-        if (!timed_out && !mbar_wait(&bars[j % NS], (uint32_t)((j / NS) & 1))) timed_out = true;
+        if (!timed_out && !mbar_wait(&bars[(unsigned)j % NS], ((unsigned)j / NS) & 1u)) timed_out = true;
     };
 
     // Pull the populations of the row held by stage jc (rows above/below in
@@ -306,6 +308,12 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
             s_rho[slot(first - dir)][t + 1] = make_pair_of<R>(a, b);
         }
         halo(below(0), 1, above(0), slot(first - dir));
+        if constexpr (D == 0) {
+            // a ring of three slots: stage 3 goes into the slot of stage 0,
+            // which the pull above has just read
+            __syncthreads();
+            if (t == 0 && !timed_out && next_issue < n_stage) issue();
+        }
         wait_stage(3);
         sa = pull(below(1), 2, above(1), wi, li, fa, rc0, rc1, lc0, lc1);
         s_rho[slot(first)][t + 1] = make_pair_of<R>(rc0, rc1);
@@ -385,10 +393,18 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
 // of column block bx.  fmap / lmap as in staged_march; rows64[k] = (first,
 // last) row with fluid in columns [64 k, 64 k + 64); a CTA of BX columns
 // merges BX / 64 of them.
+// Resident CTAs per SM the register budget is sized for: FP32 at 128 columns
+// fits five CTAs one row ahead (96 registers without spills, 45.4 KB of
+// shared memory each) and six with no row ahead (80 registers, 34.7 KB); the
+// 16-bit formats five (96 registers; at six they spill and run slower), FP32
+// two rows ahead four, FP64 two.
 template <typename S, int BX, int D>
-// FP32 at 128 columns and one row ahead fits five CTAs per SM (96 registers
-// without spills, 45.4 KB of shared memory each); the others four (or two).
-__global__ void __launch_bounds__(BX, sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : ((sizeof(S) == 4 && D == 1) ? 5 : 4)))
+constexpr int staged_min_ctas() {
+    return sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : (sizeof(S) == 4 ? (D == 0 ? 6 : (D == 1 ? 5 : 4)) : 5));
+}
+
+template <typename S, int BX, int D>
+__global__ void __launch_bounds__(BX, staged_min_ctas<S, BX, D>())
     step_staged_kernel(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap lmap,
                        S* __restrict__ fout, const int2* __restrict__ rows64, const StepParams* __restrict__ prm,
                        ObsAccum* __restrict__ acc, ObsState* __restrict__ obs, Grid grid) {
