@@ -83,17 +83,41 @@ __device__ __forceinline__ long long wrapped(const Dims& d, int x, int y, int z)
     return ((long long)z * d.ny + y) * d.nx + x;
 }
 
-// The 38 pulled populations of node k at (x, y, z) with link word lk.
+// Plane indices of the 3 x 3 x 3 neighbourhood of node (x, y, z), wrapped
+// periodically: node (x + dx, y + dy, z + dz) is at yz[dz + 1][dy + 1] +
+// xs[dx + 1].  A non-periodic direction has solid boundary planes (checked at
+// create), so a fluid node's pulls and force stencil never cross them; the
+// wrap is then never taken there.  Within-plane indices are below n < 2^40 /
+// 38 and kept in 64 bits only where a plane offset is added.
+struct Hood {
+    long long xs[3];
+    long long yz[3][3];
+    __device__ __forceinline__ void init(const Dims& d, int x, int y, int z) {
+        xs[0] = x == 0 ? d.nx - 1 : x - 1;
+        xs[1] = x;
+        xs[2] = x == d.nx - 1 ? 0 : x + 1;
+        const int ys[3] = {y == 0 ? d.ny - 1 : y - 1, y, y == d.ny - 1 ? 0 : y + 1};
+        const int zs[3] = {z == 0 ? d.nz - 1 : z - 1, z, z == d.nz - 1 ? 0 : z + 1};
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) yz[a][b] = ((long long)zs[a] * d.ny + ys[b]) * d.nx;
+    }
+    __device__ __forceinline__ long long at(int dx, int dy, int dz) const { return yz[dz + 1][dy + 1] + xs[dx + 1]; }
+};
+
+// The 38 pulled populations of node k with link word lk and neighbourhood h.
 template <typename R>
-__device__ __forceinline__ void pull3(const R* __restrict__ f, const Dims& d, long long k, int x, int y, int z,
+__device__ __forceinline__ void pull3(const R* __restrict__ f, const Dims& d, long long k, const Hood& h,
                                       unsigned lk, R (&fl)[2][kQ]) {
+    const R* __restrict__ g = f + (long long)kQ * d.n;   // species w
 #pragma unroll
     for (int i = 0; i < kQ; i++) {
         const bool bb = (lk >> i) & 1u;
-        const long long src = bb ? k : wrapped(d, x - cx3(i), y - cy3(i), z - cz3(i));
-        const int pl = bb ? opp3(i) : i;
-        fl[0][i] = __ldg(f + (long long)pl * d.n + src);
-        fl[1][i] = __ldg(f + (long long)(kQ + pl) * d.n + src);
+        // a bounced population is the node's own one of the opposite direction
+        const long long src = bb ? k + (long long)opp3(i) * d.n : h.at(-cx3(i), -cy3(i), -cz3(i)) + (long long)i * d.n;
+        fl[0][i] = __ldg(f + src);
+        fl[1][i] = __ldg(g + src);
     }
 }
 
@@ -124,8 +148,10 @@ __global__ void __launch_bounds__(kT) density3_kernel(const R* __restrict__ f, c
     long long k;
     if (!node_of(d, fluid, nfluid, x, y, z, k)) return;
     const unsigned lk = links[k];
+    Hood hd;
+    hd.init(d, x, y, z);
     R fl[2][kQ];
-    pull3<R>(f, d, k, x, y, z, lk, fl);
+    pull3<R>(f, d, k, hd, lk, fl);
     R a = R(0), b = R(0);
 #pragma unroll
     for (int i = 0; i < kQ; i++) {
@@ -156,8 +182,10 @@ __global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 5 : 3) collide3_kernel(co
     ObsLocal<R> ob;
     if (live) {
         const unsigned lk = links[k];
+        Hood hd;
+        hd.init(d, x, y, z);
         R fl[2][kQ];
-        pull3<R>(f, d, k, x, y, z, lk, fl);
+        pull3<R>(f, d, k, hd, lk, fl);
         R r[2], j[2][3];
 #pragma unroll
         for (int a = 0; a < 2; a++) {
@@ -178,7 +206,7 @@ __global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 5 : 3) collide3_kernel(co
         R sb[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
 #pragma unroll
         for (int i = 1; i < kQ; i++) {
-            const long long nb = wrapped(d, x + cx3(i), y + cy3(i), z + cz3(i));
+            const long long nb = hd.at(cx3(i), cy3(i), cz3(i));
             const R wo = w3<R>(i) * rho[nb], ww = w3<R>(i) * rho[d.n + nb];
             sb[0][0] += R(cx3(i)) * wo;
             sb[0][1] += R(cy3(i)) * wo;
