@@ -162,18 +162,90 @@ __global__ void __launch_bounds__(kT) density3_kernel(const R* __restrict__ f, c
     rho[d.n + k] = b;
 }
 
-// Eq. (feq) deviation from rest, D_i = E_i + O_i with E = -1.5 u^2 +
-// 4.5 (c.u)^2 and O = (c.u) (3 - k3 u^2 + k3 (c.u)^2) (T0 = 1/3).
+// The sums of the collision written out over the nonzero terms of the
+// velocity set (a product with a zero velocity component is not an exact
+// no-op in IEEE arithmetic, so the compiler keeps it; these forms skip them).
+// Opposite directions 2k - 1 and 2k share the even part of the equilibrium.
+
+// Moments of one species: density and momentum, sum_i c_i f_i.
 template <typename R>
-__device__ __forceinline__ R dev3(int i, R ux, R uy, R uz, R uu, R k3) {
-    const R cu = R(cx3(i)) * ux + R(cy3(i)) * uy + R(cz3(i)) * uz;
-    return R(-1.5) * uu + R(4.5) * cu * cu + cu * (R(3) - k3 * uu + k3 * cu * cu);
+__host__ __device__ __forceinline__ void moments3(const R (&f)[kQ], R& rho, R& jx, R& jy, R& jz) {
+    R s = f[0];
+#pragma unroll
+    for (int i = 1; i < kQ; i++) s += f[i];
+    rho = s;
+    jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
+    jy = (f[3] - f[4]) + (f[7] - f[8]) + (f[10] - f[9]) + (f[15] - f[16]) + (f[17] - f[18]);
+    jz = (f[5] - f[6]) + (f[11] - f[12]) + (f[14] - f[13]) + (f[15] - f[16]) + (f[18] - f[17]);
 }
+
+// sum_i w_i c_i r_i over the eighteen moving directions (r_i = rho^b at
+// x + c_i, index i - 1 in nb).
+template <typename R>
+__host__ __device__ __forceinline__ void stencil3(const R (&nb)[kQ - 1], R& sx, R& sy, R& sz) {
+    auto r = [&](int i) { return nb[i - 1]; };
+    const R w1 = R(1.0 / 18.0), w2 = R(1.0 / 36.0);
+    sx = w1 * (r(1) - r(2)) + w2 * ((r(7) - r(8)) + (r(9) - r(10)) + (r(11) - r(12)) + (r(13) - r(14)));
+    sy = w1 * (r(3) - r(4)) + w2 * ((r(7) - r(8)) + (r(10) - r(9)) + (r(15) - r(16)) + (r(17) - r(18)));
+    sz = w1 * (r(5) - r(6)) + w2 * ((r(11) - r(12)) + (r(14) - r(13)) + (r(15) - r(16)) + (r(18) - r(17)));
+}
+
+// Eq. (feq) deviation from rest, D_i = E_i + O_i with E = -1.5 u^2 +
+// 4.5 (c.u)^2 and O = (c.u) (3 - k3 u^2 + k3 (c.u)^2) (T0 = 1/3), for all
+// nineteen directions.
+template <typename R>
+__host__ __device__ __forceinline__ void dev3_all(R ux, R uy, R uz, R k3, R (&D)[kQ]) {
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R m = R(-1.5) * uu;
+    const R B = R(3) - k3 * uu;
+    D[0] = m;
+    const R cu[9] = {ux, uy, uz, ux + uy, ux - uy, ux + uz, ux - uz, uy + uz, uy - uz};
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const R c = cu[k], c2 = c * c;
+        const R e = R(4.5) * c2 + m;
+        const R o = c * (B + k3 * c2);
+        D[2 * k + 1] = e + o;
+        D[2 * k + 2] = e - o;
+    }
+}
+
+// Eq. (Regualize) on D3Q19: f'_i = w_i / (2 T0^2) Q_i : Pi with Q_i = c_i c_i -
+// T0 I and Pi = sum_j c_j c_j f'_j, over the nonzero entries of c_j c_j.
+template <typename R>
+__host__ __device__ __forceinline__ void regularize3(R (&fn)[kQ]) {
+    const R pxx = (fn[1] + fn[2]) + ((fn[7] + fn[8]) + (fn[9] + fn[10])) + ((fn[11] + fn[12]) + (fn[13] + fn[14]));
+    const R pyy = (fn[3] + fn[4]) + ((fn[7] + fn[8]) + (fn[9] + fn[10])) + ((fn[15] + fn[16]) + (fn[17] + fn[18]));
+    const R pzz = (fn[5] + fn[6]) + ((fn[11] + fn[12]) + (fn[13] + fn[14])) + ((fn[15] + fn[16]) + (fn[17] + fn[18]));
+    const R pxy = (fn[7] + fn[8]) - (fn[9] + fn[10]);
+    const R pxz = (fn[11] + fn[12]) - (fn[13] + fn[14]);
+    const R pyz = (fn[15] + fn[16]) - (fn[17] + fn[18]);
+    const R t3 = R(1.0 / 3.0) * (pxx + pyy + pzz);
+    const R a1 = R(4.5) * w3<R>(1), a7 = R(4.5) * w3<R>(7);
+    fn[0] = R(4.5) * w3<R>(0) * (-t3);
+    fn[1] = fn[2] = a1 * (pxx - t3);
+    fn[3] = fn[4] = a1 * (pyy - t3);
+    fn[5] = fn[6] = a1 * (pzz - t3);
+    fn[7] = fn[8] = a7 * (pxx + pyy + R(2) * pxy - t3);
+    fn[9] = fn[10] = a7 * (pxx + pyy - R(2) * pxy - t3);
+    fn[11] = fn[12] = a7 * (pxx + pzz + R(2) * pxz - t3);
+    fn[13] = fn[14] = a7 * (pxx + pzz - R(2) * pxz - t3);
+    fn[15] = fn[16] = a7 * (pyy + pzz + R(2) * pyz - t3);
+    fn[17] = fn[18] = a7 * (pyy + pzz - R(2) * pyz - t3);
+}
+
+// Launch parameters in the arithmetic type (the FP64 block converted once at
+// set-up, so that no thread converts them).
+template <typename R>
+struct Coef3 {
+    R nu[2], G, g[3], k3;
+    int reg;
+};
 
 template <typename R>
 __global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 5 : 3) collide3_kernel(const R* __restrict__ f, R* __restrict__ fo,
                                                       const unsigned* __restrict__ links, const R* __restrict__ rho,
-                                                      Dims d, const Params3* __restrict__ p, ObsAccum* __restrict__ acc,
+                                                      Dims d, const Coef3<R> cf, ObsAccum* __restrict__ acc,
                                                       ObsState* __restrict__ obs, double* __restrict__ fields,
                                                       const unsigned long long* __restrict__ fluid, long long nfluid) {
     int x, y, z;
@@ -188,39 +260,25 @@ __global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 5 : 3) collide3_kernel(co
         pull3<R>(f, d, k, hd, lk, fl);
         R r[2], j[2][3];
 #pragma unroll
-        for (int a = 0; a < 2; a++) {
-            R s = R(0), jx = R(0), jy = R(0), jz = R(0);
-#pragma unroll
-            for (int i = 0; i < kQ; i++) {
-                s += fl[a][i];
-                jx += R(cx3(i)) * fl[a][i];
-                jy += R(cy3(i)) * fl[a][i];
-                jz += R(cz3(i)) * fl[a][i];
-            }
-            r[a] = s;
-            j[a][0] = jx;
-            j[a][1] = jy;
-            j[a][2] = jz;
-        }
+        for (int a = 0; a < 2; a++) moments3<R>(fl[a], r[a], j[a][0], j[a][1], j[a][2]);
         // F^a/rho^a = G sum_i w_i c_i rho^b(x + c_i) + g
-        R sb[2][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
+        R sb[2][3];
+        {
+            R nbo[kQ - 1], nbw[kQ - 1];
 #pragma unroll
-        for (int i = 1; i < kQ; i++) {
-            const long long nb = hd.at(cx3(i), cy3(i), cz3(i));
-            const R wo = w3<R>(i) * rho[nb], ww = w3<R>(i) * rho[d.n + nb];
-            sb[0][0] += R(cx3(i)) * wo;
-            sb[0][1] += R(cy3(i)) * wo;
-            sb[0][2] += R(cz3(i)) * wo;
-            sb[1][0] += R(cx3(i)) * ww;
-            sb[1][1] += R(cy3(i)) * ww;
-            sb[1][2] += R(cz3(i)) * ww;
+            for (int i = 1; i < kQ; i++) {
+                const long long nb = hd.at(cx3(i), cy3(i), cz3(i));
+                nbo[i - 1] = rho[nb];
+                nbw[i - 1] = rho[d.n + nb];
+            }
+            stencil3<R>(nbo, sb[0][0], sb[0][1], sb[0][2]);
+            stencil3<R>(nbw, sb[1][0], sb[1][1], sb[1][2]);
         }
-        const R G = R(p->G);
         R acc3[2][3];
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            acc3[0][q] = G * sb[1][q] + R(p->g[q]);   // species o feels rho^w
-            acc3[1][q] = G * sb[0][q] + R(p->g[q]);   // species w feels rho^o
+            acc3[0][q] = cf.G * sb[1][q] + cf.g[q];   // species o feels rho^w
+            acc3[1][q] = cf.G * sb[0][q] + cf.g[q];   // species w feels rho^o
         }
         const R rt = r[0] + r[1];
         const R inv = R(1) / rt;
@@ -235,49 +293,28 @@ __global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 5 : 3) collide3_kernel(co
             for (int q = 0; q < 3; q++)
                 fields[(2 + q) * n + k] = double(u[q] + R(0.5) * (r[0] * acc3[0][q] + r[1] * acc3[1][q]) * inv);
         } else {
-            const R nu_mix = (r[0] * R(p->nu[0]) + r[1] * R(p->nu[1])) * inv;
+            const R nu_mix = (r[0] * cf.nu[0] + r[1] * cf.nu[1]) * inv;
             const R om1 = R(1) - R(1) / (R(3) * nu_mix + R(0.5));
-            const R k3 = R(p->k3);
-            const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            R Du[kQ];
+            dev3_all<R>(u[0], u[1], u[2], cf.k3, Du);
 #pragma unroll
             for (int a = 0; a < 2; a++) {
                 const R rho_a = r[a];
-                const R us[3] = {u[0] + acc3[a][0], u[1] + acc3[a][1], u[2] + acc3[a][2]};
-                const R uus = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
                 R fn[kQ];
 #pragma unroll
                 for (int i = 0; i < kQ; i++) {
                     const R wr = w3<R>(i) * rho_a;
-                    fn[i] = (fl[a][i] - wr) - wr * dev3<R>(i, u[0], u[1], u[2], uu, k3);
+                    fn[i] = (fl[a][i] - wr) - wr * Du[i];
                 }
-                if (p->reg != 0.0) {
-                    // Eq. (Regualize): f'_i = w_i/(2 T0^2) Q_i : Pi, Q_i = c_i c_i - T0 I
-                    R P[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};   // xx yy zz xy xz yz
-#pragma unroll
-                    for (int i = 1; i < kQ; i++) {
-                        const R cx = R(cx3(i)), cy = R(cy3(i)), cz = R(cz3(i));
-                        P[0] += cx * cx * fn[i];
-                        P[1] += cy * cy * fn[i];
-                        P[2] += cz * cz * fn[i];
-                        P[3] += cx * cy * fn[i];
-                        P[4] += cx * cz * fn[i];
-                        P[5] += cy * cz * fn[i];
-                    }
-                    const R tr = P[0] + P[1] + P[2];
-#pragma unroll
-                    for (int i = 0; i < kQ; i++) {
-                        const R cx = R(cx3(i)), cy = R(cy3(i)), cz = R(cz3(i));
-                        const R qp = cx * cx * P[0] + cy * cy * P[1] + cz * cz * P[2] +
-                                     R(2) * (cx * cy * P[3] + cx * cz * P[4] + cy * cz * P[5]) - R(1.0 / 3.0) * tr;
-                        fn[i] = R(4.5) * w3<R>(i) * qp;
-                    }
-                }
+                if (cf.reg) regularize3<R>(fn);
+                R Ds[kQ];
+                dev3_all<R>(u[0] + acc3[a][0], u[1] + acc3[a][1], u[2] + acc3[a][2], cf.k3, Ds);
                 R out[kQ];
                 R rest = rho_a;
 #pragma unroll
                 for (int i = 1; i < kQ; i++) {
                     const R wr = w3<R>(i) * rho_a;
-                    out[i] = wr + (wr * dev3<R>(i, us[0], us[1], us[2], uus, k3) + om1 * fn[i]);
+                    out[i] = wr + (wr * Ds[i] + om1 * fn[i]);
                     rest -= out[i];
                 }
                 out[0] = rest;   // the f*_i of a node sum to rho for both forms of f'
@@ -346,6 +383,7 @@ struct lbm3d_t {
     unsigned long long* fluid = nullptr;   // packed coordinates of the fluid nodes, x fastest
     long long nfluid = 0;
     Params3* dprm = nullptr;
+    Params3 hp{};                          // host copy of the parameter block
     ObsAccum* dacc = nullptr;
     ObsState* dobs = nullptr;
     std::vector<uint8_t> mask;
@@ -375,6 +413,17 @@ int fail3(lbm3d_t* h, int code, const char* fmt, ...) {
 unsigned blocks_of(long long n) { return (unsigned)((n + kT - 1) / kT); }
 
 template <typename R>
+Coef3<R> coef_of(const Params3& p) {
+    Coef3<R> c;
+    for (int a = 0; a < 2; a++) c.nu[a] = R(p.nu[a]);
+    c.G = R(p.G);
+    for (int q = 0; q < 3; q++) c.g[q] = R(p.g[q]);
+    c.k3 = R(p.k3);
+    c.reg = p.reg != 0.0;
+    return c;
+}
+
+template <typename R>
 cudaError_t step3(lbm3d_t* h, double* fields) {
     const R* fin = (const R*)h->f[h->cur];
     if (fields) solid_density3_kernel<R><<<blocks_of(h->d.n), kT, 0, h->stream>>>(h->links, nullptr, h->d, h->dprm, fields);
@@ -384,7 +433,7 @@ cudaError_t step3(lbm3d_t* h, double* fields) {
     if (h->nfluid > 0)
         density3_kernel<R><<<grid, kT, 0, h->stream>>>(fin, h->links, (R*)h->rho, h->d, h->fluid, h->nfluid);
     collide3_kernel<R><<<grid, kT, 0, h->stream>>>(fin, (R*)h->f[1 - h->cur], h->links, (const R*)h->rho, h->d,
-                                                   h->dprm, h->dacc, h->dobs, fields, h->fluid, h->nfluid);
+                                                   coef_of<R>(h->hp), h->dacc, h->dobs, fields, h->fluid, h->nfluid);
     return cudaGetLastError();
 }
 
@@ -473,6 +522,7 @@ int lbm3d_create(const uint8_t* mask, const double* rho_init, const lbm3d_params
         links3_kernel<<<blocks_of(n), kT, 0, h->stream>>>(dmask, h->links, h->d);
         e = cudaGetLastError();
     }
+    h->hp = hp;
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->dprm, &hp, sizeof hp, cudaMemcpyHostToDevice, h->stream);
     // the fluid list (x fastest) and the wall potentials of the solid nodes
     std::vector<unsigned long long> fl;
