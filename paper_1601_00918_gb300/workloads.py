@@ -166,6 +166,115 @@ def random_perturbed(nx: int, ny: int, seed: int, rho_o: float = 0.6, rho_w: flo
     return out
 
 
+@dataclass
+class BypassSpec:
+    """Two channels with joined ends (the paper's outlook on bypass
+    channels): in the branch section an upper branch of one sinusoidal
+    wavelength (bulge - neck - bulge, mean half-width 0.1875 lam, amplitude
+    amp_ratio of it) followed by a straight part `ext` long at the bulge
+    width, holds the oil slug at its neck; a straight lower branch `hl` rows
+    wide runs beside it, separated by an island `island` rows thick.  Two
+    full-height chambers `chamber` long join both branches to a straight pipe
+    `wm` rows wide and `lm` long, which closes the periodic loop (the
+    chambers are wide enough that their own resistance, the flow turning
+    from the pipe into the lower branch, is a few per cent of the
+    branches').  With blocked = True the lower branch is solid, so all flow
+    must pass the slug."""
+    lam: int = 128
+    amp_ratio: float = 0.5
+    slug_len_over_lambda: float = 0.6
+    hl: int = 12
+    island: int = 4
+    ext: int = 96
+    chamber: int = 32
+    wm: int = 12
+    lm: int = 224
+    blocked: bool = False
+
+    @property
+    def h0(self) -> float:
+        return 0.1875 * self.lam
+
+    @property
+    def amp(self) -> float:
+        return self.amp_ratio * self.h0
+
+    @property
+    def branch_len(self) -> int:
+        return self.lam + self.ext
+
+    @property
+    def nx(self) -> int:
+        return self.lm + 2 * self.chamber + self.branch_len
+
+    @property
+    def upper_height(self) -> int:
+        return 2 * int(math.ceil(self.h0 + self.amp))
+
+    @property
+    def ny(self) -> int:
+        return self.hl + self.island + self.upper_height + 2
+
+    @property
+    def x_neck(self) -> float:
+        """Column of the upper branch's neck (the slug's centre)."""
+        return float(self.lm + self.chamber + self.lam // 2)
+
+
+def bypass_channel(spec: BypassSpec) -> Workload:
+    """Mask and slug fill of a bypass geometry (BypassSpec); periodic in x,
+    solid rows 0 and ny - 1.  Row ranges (fluid): lower branch 1 .. hl,
+    island hl + 1 .. hl + island (solid in the branch section), upper branch
+    above it; the pipe's wm rows are centred in the channel; chambers are
+    fluid over the full height.  The slug spans slug_len_over_lambda * lam
+    columns about the neck and only the upper branch's rows."""
+    nx, ny = spec.nx, spec.ny
+    mask = np.ones((ny, nx), dtype=np.uint8)
+    x = np.arange(nx)
+    y = np.arange(ny)[:, None]
+    x_pipe_end = spec.lm
+    xb0 = spec.lm + spec.chamber                      # branch section [xb0, xb1)
+    xb1 = xb0 + spec.branch_len
+    # pipe
+    yp0 = 1 + (ny - 2 - spec.wm) // 2
+    mask[yp0:yp0 + spec.wm, :x_pipe_end] = 0
+    # chambers
+    mask[1:ny - 1, x_pipe_end:xb0] = 0
+    mask[1:ny - 1, xb1:nx] = 0
+    # lower branch
+    if not spec.blocked:
+        mask[1:1 + spec.hl, xb0:xb1] = 0
+    # upper branch: one sinusoidal wavelength from xb0 (bulge), then straight at the bulge width
+    yu0 = 1 + spec.hl + spec.island                   # first row of the upper branch
+    yc = yu0 + 0.5 * (spec.upper_height - 1)
+    xs = x[xb0:xb1] - xb0
+    h = np.where(xs < spec.lam, spec.h0 + spec.amp * np.cos(2.0 * np.pi * xs / spec.lam), spec.h0 + spec.amp)
+    fluid_u = (np.abs(y - yc) <= h[None, :]) & (y >= yu0) & (y <= ny - 2)
+    sub = mask[:, xb0:xb1]
+    sub[fluid_u] = 0
+    # slug: oil over the neck's columns, upper-branch rows only
+    half = 0.5 * spec.slug_len_over_lambda * spec.lam
+    xx = x[None, :] + np.zeros((ny, 1))
+    s = (_step(xx - (spec.x_neck - half)) - _step(xx - (spec.x_neck + half))) * (y >= yu0)
+    ro = RHO_LO + (RHO_HI - RHO_LO) * s
+    rho = np.stack([ro, RHO_HI + RHO_LO - ro])
+    name = f"bypass_{nx}x{ny}" + ("_blocked" if spec.blocked else "")
+    return Workload(name, mask, rho, (True, False))
+
+
+def bypass_resistance_ratio(spec: BypassSpec) -> float:
+    """(R_lower + R_pipe) / R_lower for plane Poiseuille flow (resistance
+    12 mu length / width^3 per unit depth, walls halfway between the last
+    fluid and the first solid row, the chambers' resistance neglected).  With
+    the body force on every node and the slug blocking the upper branch, the
+    loop's flow Q satisfies rho g L = (R_lower + R_pipe) Q, and the slug holds
+    the lower branch's viscous drop R_lower Q = rho g L R_lower / (R_lower +
+    R_pipe): its critical force is the blocked one times this ratio."""
+    r_lower = spec.branch_len / spec.hl ** 3
+    r_pipe = spec.lm / spec.wm ** 3
+    return (r_lower + r_pipe) / r_lower
+
+
 # ----------------------------------------------------------------------------
 # named workloads
 # ----------------------------------------------------------------------------
