@@ -31,6 +31,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -87,11 +88,13 @@ __device__ __forceinline__ long long wrapped(const Dims& d, int x, int y, int z)
 // periodically: node (x + dx, y + dy, z + dz) is at yz[dz + 1][dy + 1] +
 // xs[dx + 1].  A non-periodic direction has solid boundary planes (checked at
 // create), so a fluid node's pulls and force stencil never cross them; the
-// wrap is then never taken there.  Within-plane indices are below n < 2^40 /
-// 38 and kept in 64 bits only where a plane offset is added.
+// wrap is then never taken there.  Index type I: 32-bit unsigned when every
+// offset into the population buffers (2 x 19 planes) stays below 2^32, so
+// that an address is one multiply-add; 64-bit otherwise.
+template <typename I>
 struct Hood {
-    long long xs[3];
-    long long yz[3][3];
+    I xs[3];
+    I yz[3][3];
     __device__ __forceinline__ void init(const Dims& d, int x, int y, int z) {
         xs[0] = x == 0 ? d.nx - 1 : x - 1;
         xs[1] = x;
@@ -101,21 +104,21 @@ struct Hood {
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
-            for (int b = 0; b < 3; b++) yz[a][b] = ((long long)zs[a] * d.ny + ys[b]) * d.nx;
+            for (int b = 0; b < 3; b++) yz[a][b] = ((I)zs[a] * (I)d.ny + (I)ys[b]) * (I)d.nx;
     }
-    __device__ __forceinline__ long long at(int dx, int dy, int dz) const { return yz[dz + 1][dy + 1] + xs[dx + 1]; }
+    __device__ __forceinline__ I at(int dx, int dy, int dz) const { return yz[dz + 1][dy + 1] + xs[dx + 1]; }
 };
 
 // The 38 pulled populations of node k with link word lk and neighbourhood h.
-template <typename R>
-__device__ __forceinline__ void pull3(const R* __restrict__ f, const Dims& d, long long k, const Hood& h,
-                                      unsigned lk, R (&fl)[2][kQ]) {
-    const R* __restrict__ g = f + (long long)kQ * d.n;   // species w
+template <typename R, typename I>
+__device__ __forceinline__ void pull3(const R* __restrict__ f, I n, I k, const Hood<I>& h, unsigned lk,
+                                      R (&fl)[2][kQ]) {
+    const R* __restrict__ g = f + (size_t)kQ * n;   // species w
 #pragma unroll
     for (int i = 0; i < kQ; i++) {
         const bool bb = (lk >> i) & 1u;
         // a bounced population is the node's own one of the opposite direction
-        const long long src = bb ? k + (long long)opp3(i) * d.n : h.at(-cx3(i), -cy3(i), -cz3(i)) + (long long)i * d.n;
+        const I src = bb ? k + (I)opp3(i) * n : h.at(-cx3(i), -cy3(i), -cz3(i)) + (I)i * n;
         fl[0][i] = __ldg(f + src);
         fl[1][i] = __ldg(g + src);
     }
@@ -126,32 +129,34 @@ __device__ __forceinline__ void pull3(const R* __restrict__ f, const Dims& d, lo
 // every population plane is still read and written coalesced); a node's
 // coordinates are packed as x | y << 16 | z << 32 ... in 64 bits:
 // x in bits 0..20, y in 21..41, z in 42..62.
+template <typename I>
 __device__ __forceinline__ bool node_of(const Dims& d, const unsigned long long* __restrict__ fluid,
-                                        long long nfluid, int& x, int& y, int& z, long long& k) {
+                                        long long nfluid, int& x, int& y, int& z, I& k) {
     const long long t = (long long)blockIdx.x * kT + threadIdx.x;
     if (t >= nfluid) return false;
     const unsigned long long c = fluid[t];
     x = (int)(c & 0x1FFFFFull);
     y = (int)((c >> 21) & 0x1FFFFFull);
     z = (int)((c >> 42) & 0x1FFFFFull);
-    k = ((long long)z * d.ny + y) * d.nx + x;
+    k = ((I)z * (I)d.ny + (I)y) * (I)d.nx + (I)x;
     return true;
 }
 
 // Densities of the fluid nodes (the solid nodes' entries hold the wall
 // potentials, written once at set-up).
-template <typename R>
+template <typename R, typename I>
 __global__ void __launch_bounds__(kT) density3_kernel(const R* __restrict__ f, const unsigned* __restrict__ links,
                                                       R* __restrict__ rho, Dims d,
                                                       const unsigned long long* __restrict__ fluid, long long nfluid) {
     int x, y, z;
-    long long k;
+    I k;
     if (!node_of(d, fluid, nfluid, x, y, z, k)) return;
+    const I n = (I)d.n;
     const unsigned lk = links[k];
-    Hood hd;
+    Hood<I> hd;
     hd.init(d, x, y, z);
     R fl[2][kQ];
-    pull3<R>(f, d, k, hd, lk, fl);
+    pull3<R, I>(f, n, k, hd, lk, fl);
     R a = R(0), b = R(0);
 #pragma unroll
     for (int i = 0; i < kQ; i++) {
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(kT) density3_kernel(const R* __restrict__ f, c
         b += fl[1][i];
     }
     rho[k] = a;
-    rho[d.n + k] = b;
+    rho[n + k] = b;
 }
 
 // The sums of the collision written out over the nonzero terms of the
@@ -242,22 +247,23 @@ struct Coef3 {
     int reg;
 };
 
-template <typename R>
+template <typename R, typename I>
 __global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 5 : 3) collide3_kernel(const R* __restrict__ f, R* __restrict__ fo,
                                                       const unsigned* __restrict__ links, const R* __restrict__ rho,
                                                       Dims d, const Coef3<R> cf, ObsAccum* __restrict__ acc,
                                                       ObsState* __restrict__ obs, double* __restrict__ fields,
                                                       const unsigned long long* __restrict__ fluid, long long nfluid) {
     int x, y, z;
-    long long k;
+    I k;
     const bool live = node_of(d, fluid, nfluid, x, y, z, k);
+    const I n = (I)d.n;
     ObsLocal<R> ob;
     if (live) {
         const unsigned lk = links[k];
-        Hood hd;
+        Hood<I> hd;
         hd.init(d, x, y, z);
         R fl[2][kQ];
-        pull3<R>(f, d, k, hd, lk, fl);
+        pull3<R, I>(f, n, k, hd, lk, fl);
         R r[2], j[2][3];
 #pragma unroll
         for (int a = 0; a < 2; a++) moments3<R>(fl[a], r[a], j[a][0], j[a][1], j[a][2]);
@@ -267,9 +273,9 @@ __global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 5 : 3) collide3_kernel(co
             R nbo[kQ - 1], nbw[kQ - 1];
 #pragma unroll
             for (int i = 1; i < kQ; i++) {
-                const long long nb = hd.at(cx3(i), cy3(i), cz3(i));
+                const I nb = hd.at(cx3(i), cy3(i), cz3(i));
                 nbo[i - 1] = rho[nb];
-                nbw[i - 1] = rho[d.n + nb];
+                nbw[i - 1] = rho[n + nb];
             }
             stencil3<R>(nbo, sb[0][0], sb[0][1], sb[0][2]);
             stencil3<R>(nbw, sb[1][0], sb[1][1], sb[1][2]);
@@ -286,7 +292,6 @@ __global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 5 : 3) collide3_kernel(co
 #pragma unroll
         for (int q = 0; q < 3; q++) u[q] = (j[0][q] + j[1][q]) * inv;
         if (fields) {
-            const long long n = d.n;
             fields[k] = double(r[0]);
             fields[n + k] = double(r[1]);
 #pragma unroll
@@ -319,7 +324,7 @@ __global__ void __launch_bounds__(kT, sizeof(R) == 4 ? 5 : 3) collide3_kernel(co
                 }
                 out[0] = rest;   // the f*_i of a node sum to rho for both forms of f'
 #pragma unroll
-                for (int i = 0; i < kQ; i++) fo[(long long)(a * kQ + i) * d.n + k] = out[i];
+                for (int i = 0; i < kQ; i++) fo[(I)(a * kQ + i) * n + k] = out[i];
             }
             ob.m0 += r[0];
             ob.m1 += r[1];
@@ -423,18 +428,31 @@ Coef3<R> coef_of(const Params3& p) {
     return c;
 }
 
-template <typename R>
-cudaError_t step3(lbm3d_t* h, double* fields) {
+template <typename R, typename I>
+cudaError_t step3_idx(lbm3d_t* h, double* fields) {
     const R* fin = (const R*)h->f[h->cur];
     if (fields) solid_density3_kernel<R><<<blocks_of(h->d.n), kT, 0, h->stream>>>(h->links, nullptr, h->d, h->dprm, fields);
     // one block at least: without fluid the collide pass still closes the
     // step's observables
     const unsigned grid = std::max(1u, blocks_of(h->nfluid));
     if (h->nfluid > 0)
-        density3_kernel<R><<<grid, kT, 0, h->stream>>>(fin, h->links, (R*)h->rho, h->d, h->fluid, h->nfluid);
-    collide3_kernel<R><<<grid, kT, 0, h->stream>>>(fin, (R*)h->f[1 - h->cur], h->links, (const R*)h->rho, h->d,
-                                                   coef_of<R>(h->hp), h->dacc, h->dobs, fields, h->fluid, h->nfluid);
+        density3_kernel<R, I><<<grid, kT, 0, h->stream>>>(fin, h->links, (R*)h->rho, h->d, h->fluid, h->nfluid);
+    collide3_kernel<R, I><<<grid, kT, 0, h->stream>>>(fin, (R*)h->f[1 - h->cur], h->links, (const R*)h->rho, h->d,
+                                                      coef_of<R>(h->hp), h->dacc, h->dobs, fields, h->fluid,
+                                                      h->nfluid);
     return cudaGetLastError();
+}
+
+// 32-bit offsets when all 2 x 19 population planes plus one more (the
+// density field's second plane, the fields' five) stay below 2^32 elements;
+// GB300LBM_INDEX64=1 takes the 64-bit kernels on any grid (the tests compare
+// both).
+template <typename R>
+cudaError_t step3(lbm3d_t* h, double* fields) {
+    const char* e = getenv("GB300LBM_INDEX64");
+    const bool force64 = e && e[0] == '1';
+    if (!force64 && (unsigned long long)h->d.n * (2 * kQ + 1) < (1ull << 32)) return step3_idx<R, unsigned>(h, fields);
+    return step3_idx<R, unsigned long long>(h, fields);
 }
 
 cudaError_t init_solid_density(lbm3d_t* h) {
