@@ -503,6 +503,18 @@ int lbm_meniscus_angles(const double *rho, int32_t nx, int32_t ny, double h0, do
 int lbm_contact_angle(const double *rho, int32_t nx, int32_t ny, int32_t y_lo, int32_t y_hi, int32_t right,
                       double *theta);
 
+/* Oil area of a slug (the planar analogue of the slug volume of Section
+ * 3.4) from host densities rho [2][ny][nx] and the mask [ny][nx] (1 =
+ * solid), both host arrays the caller owns.  out[0]: fluid nodes whose oil
+ * fraction rho^o / (rho^o + rho^w) exceeds 1/2.  out[1]: the paper's volume
+ * detection, in which the slug splits into a bulk region, summed whole, and
+ * interface regions, summed only where the oil density exceeds 90 % of the
+ * total: a column whose fluid nodes are all oil-rich (fraction above 1/2)
+ * is bulk and counts every fluid node; a column that an interface crosses
+ * (some fluid nodes above 1/2, some not) counts the nodes above 9/10.
+ * LBM_EINVAL for NULL pointers or nx, ny < 1. */
+int lbm_slug_area(const double *rho, const uint8_t *mask, int32_t nx, int32_t ny, double *out);
+
 /* Wall potentials (rho_s^o, rho_s^w) whose calibrated contact angle is
  * theta_deg, from a table r[n] (ascending) -> theta[n] (descending): linear
  * interpolation of r in theta, clipped to the table's range, then r > 0 ->

@@ -802,6 +802,33 @@ int lbm_contact_angle(const double* rho, int32_t nx, int32_t ny, int32_t y_lo, i
     return LBM_OK;
 }
 
+int lbm_slug_area(const double* rho, const uint8_t* mask, int32_t nx, int32_t ny, double* out) {
+    if (!rho || !mask || !out || nx < 1 || ny < 1) return cfail(LBM_EINVAL, "bad argument");
+    const size_t n = (size_t)nx * ny;
+    auto frac = [&](size_t k) {
+        const double t = rho[k] + rho[n + k];
+        return t > 0.0 ? rho[k] / t : 0.0;
+    };
+    double half = 0.0, paper = 0.0;
+    for (int x = 0; x < nx; x++) {
+        int fluid = 0, rich = 0, above90 = 0;
+        for (int y = 0; y < ny; y++) {
+            const size_t k = (size_t)y * nx + x;
+            if (mask[k]) continue;
+            const double q = frac(k);
+            fluid++;
+            rich += q > 0.5;
+            above90 += q > 0.9;
+        }
+        half += rich;
+        if (rich == fluid && fluid > 0) paper += fluid;     // bulk column
+        else if (rich > 0) paper += above90;                // a meniscus crosses it
+    }
+    out[0] = half;
+    out[1] = paper;
+    return LBM_OK;
+}
+
 int lbm_wall_potentials(const double* r, const double* theta, int32_t n, double theta_deg, double* rho_wall) {
     if (!r || !theta || !rho_wall || n < 2) return cfail(LBM_EINVAL, "bad argument");
     Calib c;

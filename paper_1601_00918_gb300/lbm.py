@@ -33,7 +33,7 @@ EXPORTS = ("lbm_workspace_size", "lbm_create", "lbm_step", "lbm_observables", "l
            "lbm_mlp_last_error", "lbm_step_noalloc", "lbm_wait_selftest", "lbm_batch_kernel_info",
            "lbm_channel_shape", "lbm_channel_geometry", "lbm_wetting_calibrate", "lbm_surface_tension",
            "lbm_planar_critical_balance", "lbm_planar_critical_balance_hysteresis", "lbm_contact_angle",
-           "lbm_wall_potentials", "lbm_meniscus_angles", "lbm_critical_pressure_channels", "lbm_channel_last_error", "lbm3d_create", "lbm3d_step",
+           "lbm_slug_area", "lbm_wall_potentials", "lbm_meniscus_angles", "lbm_critical_pressure_channels", "lbm_channel_last_error", "lbm3d_create", "lbm3d_step",
            "lbm3d_observables", "lbm3d_get_fields", "lbm3d_save", "lbm3d_load", "lbm3d_destroy",
            "lbm3d_last_error")
 
@@ -189,6 +189,8 @@ def library(path: str | None = None) -> ctypes.CDLL:
     lib.lbm_meniscus_angles.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, dp]
     lib.lbm_meniscus_angles.restype = ctypes.c_int
+    lib.lbm_slug_area.argtypes = [dp, P(ctypes.c_uint8), ctypes.c_int32, ctypes.c_int32, dp]
+    lib.lbm_slug_area.restype = ctypes.c_int
     lib.lbm_contact_angle.argtypes = [dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_int32, dp]
     lib.lbm_wall_potentials.argtypes = [dp, dp, ctypes.c_int32, ctypes.c_double, dp]
@@ -687,6 +689,17 @@ def lbm_contact_angle(rho, y_lo, y_hi, right=True):
     _ccheck(library().lbm_contact_angle(_dptr(rho), nx, ny, int(y_lo), int(y_hi), int(bool(right)),
                                         ctypes.byref(out)))
     return out.value
+
+
+def lbm_slug_area(rho, mask):
+    """(oil-rich nodes, the paper's bulk + 90 % interface count) of a slug."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+    _, ny, nx = rho.shape
+    assert mask.shape == (ny, nx)
+    out = (ctypes.c_double * 2)()
+    _ccheck(library().lbm_slug_area(_dptr(rho), mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nx, ny, out))
+    return out[0], out[1]
 
 
 def lbm_wall_potentials(r, theta, theta_deg):

@@ -161,3 +161,37 @@ def test_hysteresis_balance(theta):
     assert lbm.lbm_planar_critical_balance_hysteresis(theta, theta, *args) == b0
     assert lbm.lbm_planar_critical_balance_hysteresis(theta - 4.0, theta + 4.0, *args) > b0
     assert lbm.lbm_planar_critical_balance_hysteresis(theta + 4.0, theta - 4.0, *args) < b0
+
+
+def test_slug_area_rules():
+    """lbm_slug_area on planar-model slugs between two necks of a lambda =
+    128 channel (rear meniscus at x = 128, front at 256, 60 degrees): the
+    oil-rich count equals the model's oil area (channel area between the
+    contact points plus the two circular segments, oracle/capillary.py) to
+    1.5 %; with sharp interfaces (width 0.05) the paper's bulk + 90 % rule
+    gives the same count but for the few nodes within 0.06 of a meniscus;
+    with tanh interfaces of width 2 it leaves out the band between the
+    1/2 and 9/10 oil-fraction levels, 2 atanh(0.8) = 2.197 nodes thick along
+    each meniscus, whose arc at a neck (wall slope zero) is 2 h (pi/2 -
+    theta) / cos(theta) long (within 25 %).  A flat meniscus (90 degrees at a
+    neck) crosses no column, so the two rules agree."""
+    from paper_1601_00918_gb300 import lbm
+    from paper_1601_00918_gb300 import workloads as wl
+    lam, h0, amp, th = 128, 24.0, 12.0, 60.0
+    ny = 2 * int(math.ceil(h0 + amp)) + 2
+    mask = wl.sinusoidal_channel(4 * lam, ny, h0, amp, float(lam))
+    sharp = _synthetic_slug(lam, h0, amp, 128.0, 256.0, th, th, w=0.05)
+    smooth = _synthetic_slug(lam, h0, amp, 128.0, 256.0, th, th, w=2.0)
+    a_sharp = lbm.lbm_slug_area(sharp, mask)
+    a_smooth = lbm.lbm_slug_area(smooth, mask)
+    model = cap.oil_area(128.0, 256.0, math.radians(th), h0, amp, float(lam))
+    assert a_sharp[0] == pytest.approx(model, rel=0.015), (a_sharp, model)
+    assert a_smooth[0] == pytest.approx(model, rel=0.015), (a_smooth, model)
+    assert 0 <= a_sharp[0] - a_sharp[1] <= 10
+    neck = h0 - amp
+    arc = 2.0 * neck * (0.5 * math.pi - math.radians(th)) / math.cos(math.radians(th))
+    band = 2.0 * math.atanh(0.8) * 2.0 * arc
+    assert a_smooth[0] - a_smooth[1] == pytest.approx(band, rel=0.25), (a_smooth, band)
+    flat = _synthetic_slug(lam, h0, amp, 128.0, 256.0, 90.0, 90.0, w=2.0)
+    a_flat = lbm.lbm_slug_area(flat, mask)
+    assert a_flat[0] == a_flat[1]
