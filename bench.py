@@ -344,15 +344,22 @@ def native_arm(args):
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # the K timed steps in up to five consecutive windows, an event between
+    # them: the line's value is the whole region; best and median window
+    # are reported beside it
+    nwin = max(1, min(5, args.steps))
+    sizes = [args.steps // nwin + (1 if k < args.steps % nwin else 0) for k in range(nwin)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(nwin + 1)]
     t_start = time.time()
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
+    ev[0].record(stream)
+    for k, n in enumerate(sizes):
+        sim.step(n)
+        ev[k + 1].record(stream)
     torch.cuda.synchronize()
     t_end = time.time()
-    ms = e0.elapsed_time(e1)
+    ms = ev[0].elapsed_time(ev[-1])
+    win_glups = sorted(ws * n_fluid * n / (ev[k].elapsed_time(ev[k + 1]) * 1e-3) / 1e9
+                       for k, n in enumerate(sizes))
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop(t_start, t_end)
@@ -383,6 +390,7 @@ def native_arm(args):
     bstep = batched_step_arm(args, peak) if rank == 0 and args.batch_n > 0 else None
     small = small_grids_arm() if rank == 0 and not args.no_small else None
     d3 = d3q19_arm(args, peak) if rank == 0 and args.d3_steps > 0 else None
+    forms = forms_arm(args, w, peak, local, n_fluid) if rank == 0 and args.forms_steps > 0 else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -394,6 +402,8 @@ def native_arm(args):
                            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                            "l2": "state 2 x %.2f GB ping-pong > 129 MB L2: no flush needed" %
                                  (nx * ny * 18 * BYTES_PER_POP[prec] / 1e9)},
+                "windows": {"n": nwin, "steps": sizes, "best": win_glups[-1],
+                            "median": statistics.median(win_glups), "unit": UNIT},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic,
                              "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
@@ -403,7 +413,7 @@ def native_arm(args):
                              "traffic_gbs": traffic / per_launch_s / 1e9 if traffic else None},
                 "all_nodes_value": value * nx * ny / n_fluid,
                 "e2e": e2e, "gpu_launches": args.steps, "clocks": clk, "cpu_baseline": cpu,
-                "critical_pressure": crit, "batched_step": bstep, "small_grids": small, "d3q19_tube": d3}
+                "critical_pressure": crit, "batched_step": bstep, "small_grids": small, "d3q19_tube": d3, "storage_forms": forms}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -690,6 +700,41 @@ def critical_pressure_arm(args):
             "speedup_seeded_with_training_vs_plain": (ok_s / (t_s + t_train)) / max(rate_p, 1e-30)}
 
 
+def forms_arm(args, w, peak, device, n_fluid):
+    """The same workload in the other storage forms, each timed over
+    args.forms_steps steps after 50 warm-up steps (the tuned kernel of each):
+    FP32 with the compensated arithmetic (the form that meets the 1e-5
+    velocity tolerance after 1000 steps), FP16- and BF16-shifted storage.
+    GLUPS and the fraction of the measured copy rate at the form's own
+    algorithmic bytes (144 B per fluid node for FP32, 72 B for the 16-bit
+    forms)."""
+    import torch
+    from paper_1601_00918_gb300 import lbm
+    stream = torch.cuda.current_stream()
+    out = {}
+    for prec in ("fp32c", "fp16s", "bf16s"):
+        sim = lbm.Simulation(w.mask, w.rho, precision=prec, periodic=w.periodic, device=device, **PHYS)
+        try:
+            sim.step(50)
+            kinfo = sim.kernel_info()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(args.forms_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            assert sim.observables()["nan_flag"] == 0
+        finally:
+            sim.close()
+        glups = n_fluid * args.forms_steps / (ms * 1e-3) / 1e9
+        gbs = glups * 18 * 2 * BYTES_PER_POP[prec]
+        out[prec] = {"value": glups, "unit": UNIT, "steps": args.forms_steps, "kernel": kinfo,
+                     "achieved_gbs": gbs, "frac": gbs / peak, "dtype": DTYPE_NAME[prec]}
+    return out
+
+
 def e2e_arm(args, w, prec, device, n_fluid):
     """GLUPS through the C ABI with host buffers: lbm_create from pinned host
     arrays (H2D of mask and densities), then every step lbm_step(1) and
@@ -750,6 +795,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=160, help="timed steps of the batched-step measurement")
     ap.add_argument("--no-small", action="store_true", help="skip the small-grid latency lines")
     ap.add_argument("--d3-steps", type=int, default=200, help="timed steps of the D3Q19 tube line (0: skip)")
+    ap.add_argument("--forms-steps", type=int, default=1000, help="timed steps of the other storage forms (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
