@@ -158,8 +158,14 @@ __global__ void __launch_bounds__(kTileX, sizeof(S) == 8 ? 4 : 5)
     }
     S* fout = (parity ? fa : fb) + I->off + kGhost;
     ObsLocal<R> ob;
-    const bool timed_out = staged_march<S, kTileX, 1>(m + parity, m + 2, fout, &I->prm, I->nx, I->ny, I->pitch,
-                                                      I->periodic_x, tl.x0, tl.y0, tl.y1, tl.dir, ob);
+    // the instance's collision, uniform over the CTA: one march without the
+    // other collision's branch for each
+    const bool timed_out =
+        I->prm.reg != 0.0
+            ? staged_march<S, kTileX, 1, 1>(m + parity, m + 2, fout, &I->prm, I->nx, I->ny, I->pitch, I->periodic_x,
+                                            tl.x0, tl.y0, tl.y1, tl.dir, ob)
+            : staged_march<S, kTileX, 1, 0>(m + parity, m + 2, fout, &I->prm, I->nx, I->ny, I->pitch, I->periodic_x,
+                                            tl.x0, tl.y0, tl.y1, tl.dir, ob);
     reduce_observables<R, kTileX>(ob, &I->acc, &I->obs, timed_out, (unsigned)I->ntiles);
 }
 

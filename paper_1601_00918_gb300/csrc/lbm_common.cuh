@@ -403,7 +403,10 @@ struct ObsLocal {
 //   nb[b][k]  rho^b at the 8 neighbours x + c_k (k = 1..8 in index k-1)
 //   dst       pointer to element (x, y) of plane (species 0, direction 0)
 //   x, nx     the node's column and the grid width (ghost images when periodic)
-template <typename S, typename R>
+//   kReg      the collision: -1 as P.reg says (read at run time), 0 plain
+//             BGK, 1 regularised (fixed at compile time: the other branch is
+//             left out of the kernel)
+template <typename S, typename R, int kReg = -1>
 __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1, R rl0, R rl1, const R (&nb)[2][8],
                                               const NodeParams<R>& P, S* __restrict__ dst, int plane,
                                               int x, int nx, int periodic, ObsLocal<R>& ob) {
@@ -472,7 +475,7 @@ __device__ __forceinline__ void collide_store(const R (&f)[2][9], R rho0, R rho1
             else
                 fn[i] = xfma(-w, Du[i], xsub(f[a][i], w));
         }
-        if (P.reg) {
+        if (kReg < 0 ? P.reg : kReg == 1) {
             // Eq. (Regualize): f'_i = w_i / (2 T0^2) Q_i : Pi with Q_i = c_i c_i - T0 I
             // and Pi = sum_j c_j c_j f'_j; on D2Q9 with T0 = 1/3 the
             // coefficients reduce to the combinations below (f'_0 is not

@@ -6,13 +6,13 @@
 namespace gb300lbm {
 namespace {
 
-template <typename S, int BX, int D>
-cudaError_t launch_staged(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs,
-                          cudaStream_t st) {
+template <typename S, int BX, int D, int kReg>
+cudaError_t launch_staged_reg(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs,
+                              cudaStream_t st) {
     using Plan = StagedPlan<S, BX, D>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(step_staged_kernel<S, BX, D>,
+        cudaError_t e = cudaFuncSetAttribute(step_staged_kernel<S, BX, D, kReg>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Plan::kBytes);
         if (e != cudaSuccess) return e;
         attr_done = true;
@@ -21,10 +21,19 @@ cudaError_t launch_staged(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, Obs
     g.strips = tn.strips;
     g.strip_rows = tn.strip_abs ? (h->p.ny + tn.strips - 1) / tn.strips : 0;
     dim3 grid((h->p.nx + BX - 1) / BX, tn.strips);
-    step_staged_kernel<S, BX, D><<<grid, BX, Plan::kBytes, st>>>(
+    step_staged_kernel<S, BX, D, kReg><<<grid, BX, Plan::kBytes, st>>>(
         h->smap[src][BX == 64 ? 0 : 1], h->lmap[BX == 64 ? 0 : 1], at_col0<S>(h->fbase[1 - src]), h->rows,
         h->dprm, acc, obs, g);
     return cudaGetLastError();
+}
+
+// The collision is fixed per handle (lbm_params.collision): one kernel per
+// collision, without the other's branch.
+template <typename S, int BX, int D>
+cudaError_t launch_staged(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsState* obs,
+                          cudaStream_t st) {
+    if (h->p.collision == 1) return launch_staged_reg<S, BX, D, 1>(h, src, tn, acc, obs, st);
+    return launch_staged_reg<S, BX, D, 0>(h, src, tn, acc, obs, st);
 }
 
 template <typename S>
@@ -39,7 +48,7 @@ cudaError_t launch_prec(lbm_t* h, int src, const Tuned& tn, ObsAccum* acc, ObsSt
 
 template <typename S, int BX, int D>
 int occupancy_one() {
-    return occupancy_of(step_staged_kernel<S, BX, D>, BX, StagedPlan<S, BX, D>::kBytes);
+    return occupancy_of(step_staged_kernel<S, BX, D, 0>, BX, StagedPlan<S, BX, D>::kBytes);
 }
 
 template <typename S>

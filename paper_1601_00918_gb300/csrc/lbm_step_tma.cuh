@@ -123,7 +123,7 @@ struct StagedPlan {
 // points at logical column 0 of row 0.  y0 >= y1: nothing to do.  Returns
 // (uniformly over the CTA) whether a bounded wait gave up; the caller
 // reduces the observables gathered in ob.
-template <typename S, int BX, int D>
+template <typename S, int BX, int D, int kReg = -1>
 __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUtensorMap* lmap,
                                              S* __restrict__ fout, const StepParams* __restrict__ prm, int nx,
                                              int ny, int pitch, int periodic_x, int x0, int y0, int y1, int dir,
@@ -360,7 +360,7 @@ __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUte
                     nb[0][6] = sw.x; nb[1][6] = sw.y;
                     nb[0][7] = se.x; nb[1][7] = se.y;
                 }
-                collide_store<S, R>(cur, rc0, rc1, lc0, lc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx,
+                collide_store<S, R, kReg>(cur, rc0, rc1, lc0, lc1, nb, P, fout + r * pitch + gxc, plane, gxc, nx,
                                     periodic_x, ob);
             }
             rc0 = rn0;
@@ -403,7 +403,8 @@ constexpr int staged_min_ctas() {
     return sizeof(S) == 8 ? 2 : (BX == 64 ? 8 : (sizeof(S) == 4 ? (D == 0 ? 6 : (D == 1 ? 5 : 4)) : 5));
 }
 
-template <typename S, int BX, int D>
+// kReg: the collision, fixed at compile time (0 plain BGK, 1 regularised).
+template <typename S, int BX, int D, int kReg>
 __global__ void __launch_bounds__(BX, staged_min_ctas<S, BX, D>())
     step_staged_kernel(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap lmap,
                        S* __restrict__ fout, const int2* __restrict__ rows64, const StepParams* __restrict__ prm,
@@ -441,8 +442,8 @@ __global__ void __launch_bounds__(BX, staged_min_ctas<S, BX, D>())
     // second time.
     const int dir = (blockIdx.y & 1) ? -1 : 1;
     ObsLocal<R> ob;
-    const bool any_timeout = staged_march<S, BX, D>(&fmap, &lmap, fout, prm, nx, ny, grid.pitch, grid.periodic_x,
-                                                    x0, y0, y1, dir, ob);
+    const bool any_timeout = staged_march<S, BX, D, kReg>(&fmap, &lmap, fout, prm, nx, ny, grid.pitch,
+                                                          grid.periodic_x, x0, y0, y1, dir, ob);
     reduce_observables<R, BX>(ob, acc, obs, any_timeout);
 }
 
