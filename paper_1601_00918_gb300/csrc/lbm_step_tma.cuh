@@ -122,7 +122,8 @@ struct StagedPlan {
 // space or in global memory (written before the launch).  fout
 // points at logical column 0 of row 0.  y0 >= y1: nothing to do.  Returns
 // (uniformly over the CTA) whether a bounded wait gave up; the caller
-// reduces the observables gathered in ob.
+// reduces the observables gathered in ob.  kReg picks the collision as in
+// collide_store (-1: at run time from prm).
 template <typename S, int BX, int D, int kReg = -1>
 __device__ __forceinline__ bool staged_march(const CUtensorMap* fmap, const CUtensorMap* lmap,
                                              S* __restrict__ fout, const StepParams* __restrict__ prm, int nx,
