@@ -134,13 +134,17 @@ int lbm_create(const uint8_t *mask, const double *rho_init, const lbm_params *p,
 
 /* Advance nsteps >= 0 time steps (Eq. basic_LBM_eq with the collision of
  * Eq. LBM_BGK, its non-equilibrium part as lbm_params.collision says),
- * asynchronously on the handle's stream.  Returns the launch status;
- * instability is reported by lbm_observables. */
+ * asynchronously on the handle's stream.  Returns the launch status:
+ * LBM_EINVAL for a NULL handle or nsteps < 0, LBM_ECUDA when a launch (or
+ * the capture of the 32-step graph) fails; instability and a bounded wait
+ * that gave up are reported by lbm_observables. */
 int lbm_step(lbm_t *h, int64_t nsteps);
 
-/* Synchronise the stream and copy the observables of the latest step.
- * Returns LBM_ETIMEOUT once timeout_flag is set, else LBM_EUNSTABLE once
- * nan_flag is set (*out is filled in both cases). */
+/* Synchronise the stream and copy the observables of the latest step
+ * (Section 3.4 tracks the slug by its centre of oil mass; the sums are the
+ * lbm_obs fields above).  Returns LBM_EINVAL for a NULL argument,
+ * LBM_ETIMEOUT once timeout_flag is set, else LBM_EUNSTABLE once nan_flag is
+ * set (*out is filled in both cases), LBM_ECUDA when the copy fails. */
 int lbm_observables(lbm_t *h, lbm_obs *out);
 
 /* Macroscopic fields of the current state (the state a next step would pull
@@ -153,13 +157,19 @@ int lbm_observables(lbm_t *h, lbm_obs *out);
  * are in pinned memory); the call returns when they are complete. */
 int lbm_get_fields(lbm_t *h, double *rho, double *u, double *p);
 
-/* Change the body-force acceleration used by the following steps. */
+/* Change the body-force acceleration (Section 3.4's homogeneous driving
+ * force) used by the following steps; synchronises the stream.  LBM_EINVAL
+ * for a NULL handle or a value that is not finite. */
 int lbm_set_body_force(lbm_t *h, double gx, double gy);
 
-/* Copy the stored post-collision populations to / from a host FP64 array
- * f[2][9][ny][nx] (species, direction, y, x; directions c_0 = (0,0),
- * c_1..c_4 = (1,0),(0,1),(-1,0),(0,-1), c_5..c_8 = (1,1),(-1,1),(-1,-1),(1,-1)).
- * lbm_load also resets the observables (step count, displacement, NaN flag). */
+/* Copy the stored post-collision populations f*_i^a (Eq. basic_LBM_eq) to /
+ * from a host FP64 array f[2][9][ny][nx] (species, direction, y, x;
+ * directions c_0 = (0,0), c_1..c_4 = (1,0),(0,1),(-1,0),(0,-1),
+ * c_5..c_8 = (1,1),(-1,1),(-1,-1),(1,-1)), synchronously.  lbm_save writes 0
+ * at solid nodes; lbm_load ignores them and stores each value in the
+ * handle's format (rounded for FP32 and the 16-bit forms).  lbm_load also
+ * resets the observables (step count, displacement, NaN flag).  LBM_EINVAL
+ * for a NULL argument, LBM_ECUDA when a copy fails. */
 int lbm_save(lbm_t *h, double *f);
 int lbm_load(lbm_t *h, const double *f);
 
@@ -257,18 +267,29 @@ typedef struct {
  * direction whose boundary planes hold fluid, densities at fluid nodes not
  * finite, negative or both zero), LBM_ENOMEM, LBM_ECUDA. */
 int lbm3d_create(const uint8_t *mask, const double *rho_init, const lbm3d_params *p, lbm3d_t **out);
-/* Advance nsteps (asynchronous). */
+/* Advance nsteps >= 0 steps (asynchronous on the handle's stream).
+ * LBM_EINVAL for a NULL handle or nsteps < 0, LBM_ECUDA when a launch fails. */
 int lbm3d_step(lbm3d_t *h, int64_t nsteps);
-/* Observables of the latest step (as lbm_observables; oil_mom_x along x). */
+/* Observables of the latest step (as lbm_observables; oil_mom_x along x);
+ * synchronises the stream.  LBM_EUNSTABLE once nan_flag is set (*out
+ * filled).  The two D3Q19 passes hold no device-side wait, so timeout_flag
+ * stays 0. */
 int lbm3d_observables(lbm3d_t *h, lbm_obs *out);
 /* Densities rho [2][nz][ny][nx] and mixture velocity u [3][nz][ny][nx]
  * (with half the force) of the current state; either may be NULL.
- * Allocates a temporary device buffer of 40 bytes per node. */
+ * Allocates a temporary device buffer of 40 bytes per node (LBM_ECUDA when
+ * that fails) and returns when the host arrays are written. */
 int lbm3d_get_fields(lbm3d_t *h, double *rho, double *u);
-/* Stored populations to / from a host array f[2][19][nz][ny][nx]. */
+/* Stored populations to / from a host array f[2][19][nz][ny][nx]
+ * (synchronous; 0 at solid nodes on save, ignored there on load; load
+ * resets the observables).  LBM_EINVAL for a NULL argument. */
 int lbm3d_save(lbm3d_t *h, double *f);
 int lbm3d_load(lbm3d_t *h, const double *f);
+/* Free the handle and its device memory (after its stream's work); NULL is
+ * ignored. */
 void lbm3d_destroy(lbm3d_t *h);
+/* Text of the last error of h, or of the calling thread's last
+ * lbm3d_create when h is NULL. */
 const char *lbm3d_last_error(const lbm3d_t *h);
 
 /* Free the handle and the device memory it owns.  NULL is ignored. */
@@ -317,7 +338,9 @@ typedef struct {
 int lbm_batch_create(const lbm_instance *inst, int32_t n, int32_t precision, int32_t eq_order,
                      void *cuda_stream, lbm_batch_t **out);
 
-/* Advance every active instance by nsteps (asynchronous). */
+/* Advance every active instance by nsteps >= 0 (asynchronous; runs of 16
+ * steps replay a captured CUDA graph).  LBM_EINVAL for a NULL batch or
+ * nsteps < 0, LBM_ECUDA when a launch fails. */
 int lbm_batch_step(lbm_batch_t *b, int64_t nsteps);
 
 /* Observables of every instance (out[n]); LBM_EUNSTABLE if any NaN flag,
@@ -330,10 +353,14 @@ int lbm_batch_observables(lbm_batch_t *b, lbm_obs *out);
  * library's tiling. */
 int lbm_batch_kernel_info(const lbm_batch_t *b, int32_t info[3]);
 
-/* Set the x body force of every instance (gx[n]). */
+/* Set the x body force (Section 3.4) of every instance from the host
+ * array gx[n]; synchronises the stream.  LBM_EINVAL for a NULL argument or
+ * a value that is not finite. */
 int lbm_batch_set_body_force(lbm_batch_t *b, const double *gx);
 
-/* Stored populations of instance i as lbm_save does for a single grid. */
+/* Stored populations of instance i as lbm_save does for a single grid
+ * (f[2][9][ny_i][nx_i], synchronous).  LBM_EINVAL for a NULL argument or
+ * i outside [0, n). */
 int lbm_batch_save(lbm_batch_t *b, int32_t i, double *f);
 
 typedef struct {
@@ -361,7 +388,11 @@ typedef struct {
 int lbm_critical_pressure_batch(lbm_batch_t *b, const double *g_lo, const double *g_hi,
                                 const lbm_bisect_opts *o, lbm_crit_result *out);
 
+/* Free the batch and its device memory (after its stream's work); NULL is
+ * ignored. */
 void lbm_batch_destroy(lbm_batch_t *b);
+/* Text of the last error of b, or of the calling thread's last
+ * lbm_batch_create when b is NULL. */
 const char *lbm_batch_last_error(const lbm_batch_t *b);
 
 /* ---------------------------------------------------------------------------

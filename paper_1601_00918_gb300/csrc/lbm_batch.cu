@@ -809,6 +809,8 @@ int lbm_batch_kernel_info(const lbm_batch_t* b, int32_t info[3]) {
 
 int lbm_batch_set_body_force(lbm_batch_t* b, const double* gx) {
     if (!b || !gx) return batch_fail(b, LBM_EINVAL, "NULL argument");
+    for (int i = 0; i < b->n; i++)
+        if (!std::isfinite(gx[i])) return batch_fail(b, LBM_EINVAL, "g of instance %d is not finite", i);
     // patch the g[0] field of every record (a small host round trip)
     std::vector<BatchInst> h(b->n);
     BTRY(b, cudaMemcpyAsync(h.data(), b->dinst, sizeof(BatchInst) * b->n, cudaMemcpyDeviceToHost, b->stream));
