@@ -133,6 +133,45 @@ def test_null_handle_calls_fail_cleanly(lib):
     lib.lbm_destroy(None)
 
 
+def test_every_handle_call_rejects_a_null_handle(lib):
+    """Each call that takes a handle returns LBM_EINVAL for NULL (as the
+    header states) before it touches a device, and every destroy ignores
+    NULL; the error text of the NULL handle is readable afterwards."""
+    d = ctypes.c_double
+    calls = [
+        lambda: lib.lbm_get_fields(None, None, None, None),
+        lambda: lib.lbm_set_body_force(None, d(0.0), d(0.0)),
+        lambda: lib.lbm_save(None, None),
+        lambda: lib.lbm_load(None, None),
+        lambda: lib.lbm_kernel_info(None, None),
+        lambda: lib.lbm_batch_step(None, ctypes.c_int64(1)),
+        lambda: lib.lbm_batch_observables(None, None),
+        lambda: lib.lbm_batch_kernel_info(None, None),
+        lambda: lib.lbm_batch_set_body_force(None, None),
+        lambda: lib.lbm_batch_save(None, 0, None),
+        lambda: lib.lbm_critical_pressure_batch(None, None, None, None, None),
+        lambda: lib.lbm3d_step(None, ctypes.c_int64(1)),
+        lambda: lib.lbm3d_observables(None, None),
+        lambda: lib.lbm3d_get_fields(None, None, None),
+        lambda: lib.lbm3d_save(None, None),
+        lambda: lib.lbm3d_load(None, None),
+        lambda: lib.lbm_mlp_params(None, None, None),
+        lambda: lib.lbm_mlp_forward(None, None, 1, None),
+        lambda: lib.lbm_mlp_loss_grad(None, None, None, 1, None, None),
+        lambda: lib.lbm_mlp_adam(None, ctypes.c_float(1e-3)),
+        lambda: lib.lbm_critical_pressure_channels(None, 1, None, None),
+        lambda: lib.lbm_step_noalloc(None, None, None, None, None),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == lbm.LBM_EINVAL, k
+    lib.lbm_batch_destroy(None)
+    lib.lbm3d_destroy(None)
+    lib.lbm_mlp_destroy(None)
+    for fn in (lib.lbm_last_error, lib.lbm_batch_last_error, lib.lbm3d_last_error):
+        fn.restype = ctypes.c_char_p
+        assert isinstance(fn(None), bytes)
+
+
 # ----------------------------------------------------------------------------
 # input generators
 # ----------------------------------------------------------------------------
