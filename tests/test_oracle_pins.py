@@ -578,6 +578,49 @@ def test_oracle_rejects_open_boundary_without_walls():
 
 
 # ----------------------------------------------------------------------------
+# observables (Section 3.4 tracks the slug by its centre of oil mass)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("tau", [(1.0, 1.0), (0.7, 1.4)])
+def test_observables_of_a_uniformly_accelerated_mixture(tau):
+    """A uniform mixture at rest in a periodic box under a body force: the
+    interaction force vanishes (sum_i w_i c_i = 0), both species relax
+    towards the same shifted velocity, so the fluid moves as one body whose
+    stored velocity grows by g per step.  The state pulled in step s
+    (0-based) carries velocity s g, and the physical velocity adds half a
+    step of force: the oil momentum observable is M^o (s + 1/2) g_x, max|u|
+    is (s + 1/2)|g|, and the oil displacement summed over N steps is
+    g_x N^2 / 2, the distance a body accelerated from rest covers."""
+    n, steps = 6, 40
+    g = np.array([3e-5, -4e-5])
+    P = oracle.Problem(wl.periodic_box(n, n), tau=tau, G=G_REPULSIVE, g=tuple(g))
+    f0 = P.init(wl.uniform(n, n, 0.7, 0.4))
+    mo = 0.7 * n * n
+    _, hist = P.run(f0, steps, history=True)
+    s = np.arange(steps)
+    np.testing.assert_allclose(hist[:, 0], mo, rtol=1e-14)
+    np.testing.assert_allclose(hist[:, 2], mo * (s + 0.5) * g[0], rtol=1e-9)
+    np.testing.assert_allclose(hist[:, 3], (s + 0.5) * np.hypot(*g), rtol=1e-9)
+    assert np.sum(hist[:, 2] / hist[:, 0]) == pytest.approx(0.5 * g[0] * steps ** 2, rel=1e-9)
+    assert not hist[:, 4].any()
+
+
+@pytest.mark.parametrize("species", [0, 1])
+def test_instability_flag_for_either_species(species):
+    """The instability flag rises when the pulled density of either species
+    is negative (or NaN) at some fluid node, and only then: a 3 x 3 block of
+    the rest state at density `bad` gives its centre node the pulled density
+    bad (all nine pulls come from the block, weights summing to 1)."""
+    n = 5
+    rho = wl.uniform(n, n, 0.6, 0.3)
+    P = oracle.Problem(wl.periodic_box(n, n), tau=(1.0, 1.0), G=G_REPULSIVE)
+    assert P.step(P.init(rho))[1][4] == 0.0
+    for bad in (-0.05, np.nan):
+        r = rho.copy()
+        r[species, 1:4, 2:5] = bad
+        assert P.step(P.init(r))[1][4] == 1.0, bad
+
+
+# ----------------------------------------------------------------------------
 # bisection protocol of the critical body force
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("g_true,lo,hi", [(1.3e-4, 1e-4, 4e-4), (5e-4, 1e-4, 2e-4), (3e-5, 1e-4, 4e-4)])
