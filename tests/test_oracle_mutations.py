@@ -5,7 +5,9 @@ index or species, a transposed operand) in a copy of oracle/lbm_oracle.c,
 compiles the copy into a temporary directory with the oracle's own gcc
 flags, points the oracle package at it for the duration of the test, and
 runs the fast pins of tests/test_oracle_pins.py (and, for the equation of
-state, the Laplace law): at least one of them has to fail.  A control case
+state, the Laplace law): at least one of them has to fail.  The D3Q19
+oracle (oracle/lbm3d_oracle.c) is treated the same way with the pins of
+tests/test_oracle_d3q19.py.  A control case
 compiles the unchanged source the same way and checks that every pin of the
 battery passes, so a failure under a mutation is the mistake's doing and not
 the harness's.
@@ -21,20 +23,22 @@ import subprocess
 import pytest
 
 import oracle
+from oracle import d3q19
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "lbm_oracle.c")
+SRC3 = os.path.join(ROOT, "oracle", "lbm3d_oracle.c")
 
 
-def _pins():
-    spec = importlib.util.spec_from_file_location("oracle_pins_for_mutations",
-                                                  os.path.join(ROOT, "tests", "test_oracle_pins.py"))
+def _pins(name):
+    spec = importlib.util.spec_from_file_location(f"{name}_for_mutations", os.path.join(ROOT, "tests", f"{name}.py"))
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     return mod
 
 
-PINS = _pins()
+PINS = _pins("test_oracle_pins")
+PINS3 = _pins("test_oracle_d3q19")
 
 
 def _battery():
@@ -148,12 +152,13 @@ def _compile(source, out_dir, name):
     return so
 
 
-def _run_battery(monkeypatch, so, stop_at_first=True):
-    """Point the oracle at `so`, run the battery, return the names that failed."""
-    monkeypatch.setattr(oracle, "_lib", None)
-    monkeypatch.setattr(oracle, "build", lambda force=False: so)
+def _run_battery(monkeypatch, so, stop_at_first=True, module=oracle, battery=None):
+    """Point the oracle module `module` at `so`, run the battery, return the
+    names of the pins that failed."""
+    monkeypatch.setattr(module, "_lib", None)
+    monkeypatch.setattr(module, "build", lambda force=False: so)
     failed = []
-    for name, call in _battery():
+    for name, call in (battery or _battery)():
         try:
             call()
         except Exception:   # an assertion, or the oracle refusing the run
@@ -185,4 +190,77 @@ def test_a_planted_mistake_fails_a_pin(tmp_path, monkeypatch, mid, what, old, ne
             pin()
         except Exception:
             failed.append(name)
+    assert failed, f"no pin caught: {what}"
+
+
+# ----------------------------------------------------------------------------
+# the D3Q19 oracle
+# ----------------------------------------------------------------------------
+def _battery3():
+    """(name, call) of every D3Q19 pin (about 2 s in all)."""
+    p = PINS3
+    return [
+        ("lattice moments", p.test_lattice_moments),
+        ("feq moments", lambda: [p.test_feq_moments(o, r, u) for o in (2, 3)
+                                 for (r, u) in ((0.7, (0.11, -0.04, 0.07)), (1.3, (0.02, 0.2, -0.12)))]),
+        ("axis permutation", p.test_axis_permutation_commutes_with_the_step),
+        ("momentum balance", p.test_total_momentum_grows_by_mass_times_g),
+        ("Hermite projection", p.test_regularized_part_is_the_hermite_projection),
+        ("z-uniform flow = D2Q9", lambda: [p.test_z_uniform_flow_reproduces_the_d2q9_oracle(o) for o in (2, 3)]),
+        ("mass in the tube", p.test_mass_conservation_in_the_sinusoidal_tube),
+        ("uniformly accelerated mixture", p.test_uniformly_accelerated_mixture),
+    ]
+
+
+MUTATIONS3 = [
+    ("weight_z_faces", "the two z faces weighted 1/36 instead of 1/18",
+     "(i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0)", "(i <= 4 ? 1.0 / 18.0 : 1.0 / 36.0)"),
+    ("feq_cubic_sign", "sign of the -(c.u) u^2 / (2 T0^2) term of Eq. (feq)",
+     "- cu * uu / (2.0 * T0 * T0)", "+ cu * uu / (2.0 * T0 * T0)"),
+    ("feq_uz_dropped", "u_z left out of u^2 in Eq. (feq)",
+     "double uu = ux * ux + uy * uy + uz * uz;", "double uu = ux * ux + uy * uy;"),
+    ("force_z_transposed", "c_y in place of c_z in the z force sum",
+     "s[2] += weight(i) * CZ[i] * rb;", "s[2] += weight(i) * CY[i] * rb;"),
+    ("momentum_z_transposed", "c_y in place of c_z in the z momentum",
+     "j[a][2] += CZ[i] * fl[a][i];", "j[a][2] += CY[i] * fl[a][i];"),
+    ("pull_z_sign", "streaming source z + c_z instead of z - c_z",
+     "node(p, x - CX[i], y - CY[i], z - CZ[i]);", "node(p, x - CX[i], y - CY[i], z + CZ[i]);"),
+    ("bounce_own_direction", "bounce-back returns the direction itself, not its opposite",
+     "return fs[fidx(p, a, opposite(i), node(p, x, y, z))];", "return fs[fidx(p, a, i, node(p, x, y, z))];"),
+    ("hermite_trace_2d", "Q_i = c_i c_i - T0 I with the T0 dropped along z",
+     "(r == s ? T0 : 0.0)", "(r == s && r < 2 ? T0 : 0.0)"),
+    ("force_own_species", "the force of a species from its own density, not the other's",
+     "for (int a = 0; a < 2; a++) accel_at(p, rho + (size_t)(1 - a) * n, x, y, z, acc[a]);",
+     "for (int a = 0; a < 2; a++) accel_at(p, rho + (size_t)a * n, x, y, z, acc[a]);"),
+    ("force_shift_z_dropped", "the equilibrium velocity shift dropped along z",
+     "u[2] + acc[a][2], feq_s", "u[2], feq_s"),
+    ("mixture_viscosity_swapped", "the viscosities of the two species swapped in nu_mix",
+     "(rho[0] * nu0 + rho[1] * nu1) / rt", "(rho[0] * nu1 + rho[1] * nu0) / rt"),
+    ("wall_potential_species", "the other species' wall potential at a solid node",
+     "if (solid[k]) return p->rho_wall[a];", "if (solid[k]) return p->rho_wall[1 - a];"),
+    ("oil_momentum_half_force", "half the force left out of the oil momentum observable",
+     "px += mac[2] + 0.5 * r0 * acc[0][0];", "px += mac[2];"),
+    ("fields_half_force", "half the force left out of the physical velocity of the fields",
+     "u[d] = (jx[d] + 0.5 * (r0 * acc[0][d] + r1 * acc[1][d])) / (r0 + r1);", "u[d] = jx[d] / (r0 + r1);"),
+    ("max_u_without_z", "max|u| over u_x and u_y only",
+     "for (int d = 0; d < 3; d++) {\n                    double ud", "for (int d = 0; d < 2; d++) {\n                    double ud"),
+]
+
+
+@pytest.mark.slow
+def test_control_unchanged_d3q19_source_passes_the_battery(tmp_path, monkeypatch):
+    with open(SRC3) as fh:
+        src = fh.read()
+    so = _compile(src, str(tmp_path), "control3")
+    assert _run_battery(monkeypatch, so, stop_at_first=False, module=d3q19, battery=_battery3) == []
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mid,what,old,new", MUTATIONS3, ids=[m[0] for m in MUTATIONS3])
+def test_a_planted_mistake_in_the_d3q19_oracle_fails_a_pin(tmp_path, monkeypatch, mid, what, old, new):
+    with open(SRC3) as fh:
+        src = fh.read()
+    assert src.count(old) == 1, f"mutation {mid}: the text to replace must occur exactly once"
+    so = _compile(src.replace(old, new), str(tmp_path), mid + "3")
+    failed = _run_battery(monkeypatch, so, module=d3q19, battery=_battery3)
     assert failed, f"no pin caught: {what}"
