@@ -140,6 +140,41 @@ def test_water_wet_slug_on_a_neck_rests_symmetrically_and_needs_a_push():
     assert g > 0 and smax > s0
 
 
+def _constructed_balance(points, lam):
+    """Periodic piecewise-linear balance through (s / lam, value) points."""
+    xs = np.array([p[0] for p in points] + [1.0]) * lam
+    ys = np.array([p[1] for p in points] + [points[0][1]])
+    return lambda s: np.interp(np.mod(s, lam), xs, ys)
+
+
+def test_loading_path_on_a_constructed_balance():
+    """The loading rule of the critical force on balances built by hand
+    (the geometry replaced by a known periodic curve with its rest zero at
+    s = 0): a first peak of 1.0 at 0.15 lam, a dip, a second peak of 1.5 at
+    0.8 lam.  Loaded from rest the slug climbs to the first peak and jumps to
+    where the balance is 1.0 again.  With a deep dip (to -0.5 at 0.3 lam)
+    that point lies 0.525 lam ahead: longer than lam / 2, so the slug counts
+    as moving at the first peak (1.0); with a shallow dip (0.6) it lies
+    0.35 lam ahead, so the slug only moves on and escapes past the second
+    peak (1.5), whose next equal value is a full period ahead.  With the
+    threshold raised to 0.6 lam the deep-dip slug escapes at 1.5 too."""
+    lam = 100.0
+    deep = _constructed_balance([(0.0, 0.0), (0.15, 1.0), (0.3, -0.5), (0.8, 1.5), (0.9, -1.0)], lam)
+    shallow = _constructed_balance([(0.0, 0.0), (0.15, 1.0), (0.3, 0.6), (0.8, 1.5), (0.9, -1.0)], lam)
+    glb = cap.critical_force.__globals__     # the module the function reads its helpers from
+    saved = glb["front_for"], glb["capillary_balance"]
+    try:
+        glb["front_for"] = lambda s, *a, **k: s + 1.0
+        for bal, jump, expected in ((deep, None, 1.0), (shallow, None, 1.5), (deep, 0.6 * lam, 1.5)):
+            glb["capillary_balance"] = lambda s, xf, *a, bal=bal: bal(np.asarray(s))
+            g, s0, smax, _ = cap.critical_force(1.0, 50.0, 10.0, 5.0, lam, x_rest=0.0, jump=jump)
+            assert s0 == pytest.approx(0.0, abs=1e-9)
+            assert g == pytest.approx(expected, rel=1e-9), (jump, expected)
+            assert smax == pytest.approx(0.15 * lam if expected == 1.0 else 0.8 * lam, abs=1e-6)
+    finally:
+        glb["front_for"], glb["capillary_balance"] = saved
+
+
 # ----------------------------------------------------------------------------
 # Section 3.3: contact angle
 # ----------------------------------------------------------------------------

@@ -5,20 +5,24 @@ index or species, a transposed operand) in a copy of oracle/lbm_oracle.c,
 compiles the copy into a temporary directory with the oracle's own gcc
 flags, points the oracle package at it for the duration of the test, and
 runs the fast pins of tests/test_oracle_pins.py: at least one of them has
-to fail.  The D3Q19
-oracle (oracle/lbm3d_oracle.c) is treated the same way with the pins of
-tests/test_oracle_d3q19.py.  A control case
-compiles the unchanged source the same way and checks that every pin of the
-battery passes, so a failure under a mutation is the mistake's doing and not
-the harness's.
+to fail.  The D3Q19 oracle (oracle/lbm3d_oracle.c) is treated the same way
+with the pins of tests/test_oracle_d3q19.py, and the Python modules of the
+oracle (the planar critical force and the contact angle, the closed forms
+and fits, the bisection protocol, the surrogate's FP64 reference) by
+replacing their functions with those of a mutated copy of the source.
+Control cases compile the unchanged C sources the same way and check that
+every pin of their battery passes, so a failure under a mutation is the
+mistake's doing and not the harness's.
 
 Every planted mistake keeps all memory accesses inside their arrays (index
 tables stay permutations of 0..8, wrapped indices stay in [0, n)), so a
 mutated oracle can give wrong numbers but cannot crash the test process.
 """
+import importlib
 import importlib.util
 import os
 import subprocess
+import types
 
 import pytest
 
@@ -254,4 +258,127 @@ def test_a_planted_mistake_in_the_d3q19_oracle_fails_a_pin(tmp_path, monkeypatch
     assert src.count(old) == 1, f"mutation {mid}: the text to replace must occur exactly once"
     so = _compile(src.replace(old, new), str(tmp_path), mid + "3")
     failed = _run_battery(monkeypatch, so, module=d3q19, battery=_battery3)
+    assert failed, f"no pin caught: {what}"
+
+
+# ----------------------------------------------------------------------------
+# the Python parts of the oracle: closed forms, the planar critical force,
+# the contact angle, the bisection protocol and the surrogate's reference
+# ----------------------------------------------------------------------------
+CAP = _pins("test_oracle_capillary")
+
+
+def _python_battery():
+    """(name, call) of the pins of the Python oracle modules, cheapest first;
+    the Laplace law (about 45 s) and the contact-angle symmetry run (about
+    15 s) come last, so only mistakes the others miss pay for them.  The
+    unchanged modules pass all of these pins in the regular suite."""
+    p, c = PINS, CAP
+    return [
+        ("worked numbers", p.test_worked_numbers_section_3_4),
+        ("bisection brackets", lambda: [p.test_bisection_brackets_a_sharp_threshold(*a) for a in
+                                        ((1.3e-4, 1e-4, 4e-4), (5e-4, 1e-4, 2e-4), (3e-5, 1e-4, 4e-4))]),
+        ("bisection status", p.test_bisection_status_codes),
+        ("MLP layout", p.test_mlp_parameter_count_and_layout),
+        ("MLP gradient", p.test_mlp_gradient_matches_central_differences),
+        ("MLP closed forms", p.test_mlp_closed_forms),
+        ("Adam first step", p.test_adam_first_step_is_lr_times_sign),
+        ("meniscus", lambda: [c.test_front_meniscus_against_constructed_circle(*a) for a in
+                              ((30, 0, 8.0), (55, 20, 6.0), (120, -15, 10.0), (150, 10, 12.0))]),
+        ("channel area", c.test_channel_area_is_the_integral_of_twice_the_half_width),
+        ("circle fit", c.test_circle_fit_recovers_a_circle),
+        ("synthetic contact angle", lambda: [c.test_contact_angle_of_a_synthetic_circular_interface(t)
+                                             for t in (35.0, 115.0)]),
+        ("droplet radius", lambda: p.test_droplet_radius_of_a_synthetic_tanh_disc(17.3, 64.0, 64.0)),
+        ("straight channel / symmetric slug",
+         lambda: c.test_balance_vanishes_in_a_straight_channel_and_for_symmetric_slugs(60)),
+        ("long-wavelength limit", lambda: c.test_long_wavelength_limit_is_the_curvature_difference(50)),
+        ("small-amplitude limit", lambda: c.test_small_amplitude_limit_is_the_wall_slope_term(40)),
+        ("water-wet slug on a neck", c.test_water_wet_slug_on_a_neck_rests_symmetrically_and_needs_a_push),
+        ("loading path", c.test_loading_path_on_a_constructed_balance),
+        ("layered Poiseuille", p.test_layered_poiseuille_reduces_to_parabola),
+        ("layered Poiseuille, two components", lambda: p.test_layered_poiseuille_two_components(1.5, 1.0)),
+        ("shear wave", p.test_shear_wave_viscosity_single_species),
+        ("Laplace law", p.test_laplace_law_droplets),
+        ("contact-angle symmetries", c.test_oracle_contact_angle_symmetries),
+    ]
+
+
+# (module, id, what the mistake is, unique text in the module, its replacement)
+PY_MUTATIONS = [
+    ("capillary", "wall_slope", "h'(x) without its 2 pi / lam",
+     "return np.arctan(amp * k * np.sin(k * np.asarray(x, dtype=np.float64)))",
+     "return np.arctan(amp * np.sin(k * np.asarray(x, dtype=np.float64)))"),
+    ("capillary", "meniscus_phi_sign", "the wall angle entering the front and rear menisci swapped",
+     "alpha = 0.5 * math.pi + (phi if front else -phi) - theta",
+     "alpha = 0.5 * math.pi + (-phi if front else phi) - theta"),
+    ("capillary", "segment_area", "the circular segment without its chord triangle",
+     "(a - np.sin(a) * np.cos(a))", "(a - np.sin(a))"),
+    ("capillary", "channel_area_k", "the integral of the cosine with k in place of 1 / k",
+     "return 2.0 * (h0 * (b - a) - amp / k * (math.sin(k * b) - math.sin(k * a)))",
+     "return 2.0 * (h0 * (b - a) - amp * k * (math.sin(k * b) - math.sin(k * a)))"),
+    ("capillary", "oil_area_rear_segment", "the rear segment subtracted from the oil area",
+     "return between + sr + sf", "return between - sr + sf"),
+    ("capillary", "balance_sign", "rear minus front curvature",
+     "return kf - kr", "return kr - kf"),
+    ("capillary", "jump_length", "a slug counted as moving only after a jump of a whole wavelength",
+     "jump = 0.5 * lam if jump is None else jump", "jump = lam if jump is None else jump"),
+    ("capillary", "contact_half_width", "the half width between the outermost fluid rows, not the walls",
+     "y0 = 0.5 * (y_hi - y_lo + 1)", "y0 = 0.5 * (y_hi - y_lo)"),
+    ("capillary", "contact_side", "the angle taken through oil instead of water",
+     "return acute if centre_on_oil else 180.0 - acute", "return 180.0 - acute if centre_on_oil else acute"),
+    ("analytic", "layered_core_continuity", "the wall layer's velocity at the interface with the core viscosity",
+     "+ f * (a * a - b * b) / (2.0 * mu_out)\n", "+ f * (a * a - b * b) / (2.0 * mu_core)\n"),
+    ("analytic", "bond_without_d", "the Bond number without the neck half-width",
+     "return rho * g * length * d / sigma", "return rho * g * length / sigma"),
+    ("analytic", "droplet_diameter", "the droplet's diameter taken for its radius",
+     "radii.append(0.5 * (pos[1] - pos[0]))", "radii.append(pos[1] - pos[0])"),
+    ("analytic", "tanh_shift_sign", "the interface position entering Eq. (den-fitting) with the wrong sign",
+     "return c1 * np.tanh(c2 * (x - c3)) + c4", "return c1 * np.tanh(c2 * (x + c3)) + c4"),
+    ("analytic", "laplace_inverse_diameter", "dP fitted against 2 / R",
+     "inv_r = 1.0 / np.asarray(radii, dtype=np.float64)", "inv_r = 2.0 / np.asarray(radii, dtype=np.float64)"),
+    ("bisect", "arithmetic_first_probe", "the bracket check skipped: the first probe bisects",
+     'state = "hi" if check_bracket else "bisect"', 'state = "bisect"'),
+    ("bisect", "stop_rule", "the stopping rule relative to g_lo",
+     "if state == \"bisect\" and g_hi - g_lo <= rel * g_hi:", "if state == \"bisect\" and g_hi - g_lo <= rel:"),
+    ("bisect", "widening", "a failed upper bracket not widened",
+     "g_lo, g_hi = g_hi, 2.0 * g_hi", "g_lo, g_hi = g_hi, g_hi"),
+    ("mlp", "dsilu", "the SiLU derivative without the z s (1 - s) term",
+     "return s * (1.0 + z * (1.0 - s))", "return s * (1.0 + z * s)"),
+    ("mlp", "dloss_ds", "dL/ds without its 1/2",
+     "d[:, 1] = 0.5 * (1.0 - e * r * r) / B", "d[:, 1] = (1.0 - e * r * r) / B"),
+    ("mlp", "adam_bias_correction", "Adam's second moment without its bias correction",
+     "vh = v / (1 - b2 ** t)", "vh = v"),
+    ("mlp", "unpack_transposed", "weights read as [fan_in, fan_out]",
+     "W = theta[o:o + fan_out * fan_in].reshape(fan_out, fan_in)",
+     "W = theta[o:o + fan_out * fan_in].reshape(fan_in, fan_out).T"),
+]
+
+
+def _mutate_python(monkeypatch, modname, old, new):
+    """Replace every function of oracle.<modname> by its counterpart from a
+    copy of the module's source with `old` replaced by `new`."""
+    real = importlib.import_module(f"oracle.{modname}")
+    with open(real.__file__) as fh:
+        src = fh.read()
+    assert src.count(old) == 1, f"{modname}: the text to replace must occur exactly once"
+    mut = types.ModuleType(f"oracle.{modname}_mutated")
+    mut.__file__ = real.__file__
+    exec(compile(src.replace(old, new), real.__file__, "exec"), mut.__dict__)
+    for name, value in vars(mut).items():
+        if callable(value) and getattr(value, "__module__", None) == mut.__name__:
+            monkeypatch.setattr(real, name, value)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("modname,mid,what,old,new", PY_MUTATIONS, ids=[m[1] for m in PY_MUTATIONS])
+def test_a_planted_mistake_in_the_python_oracle_fails_a_pin(monkeypatch, modname, mid, what, old, new):
+    _mutate_python(monkeypatch, modname, old, new)
+    failed = []
+    for name, call in _python_battery():
+        try:
+            call()
+        except Exception:
+            failed.append(name)
+            break
     assert failed, f"no pin caught: {what}"
