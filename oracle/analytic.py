@@ -9,7 +9,8 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 * the layered two-component Hagen-Poiseuille profile (Section 3.2);
 * the Bond number Bo = rho g L D / sigma, Eq. (Bo_number), and the hydrostatic
   term rho g x of Eq. (plot_value) (Section 3.4);
-* the Taylor-Green shear-wave decay of a BGK fluid with nu = T0 (tau - 1/2).
+* the kinematic viscosity of a BGK fluid, nu = T0 (tau - 1/2) (Section 2),
+  against which the shear-wave pins measure the decay rate nu k^2.
 """
 from __future__ import annotations
 
@@ -105,18 +106,3 @@ def bond_number(rho: float, g: float, length: float, d: float, sigma: float) -> 
 def hydrostatic(rho: float, g: float, x: float) -> float:
     """The rho g x term removed in Eq. (plot_value)."""
     return rho * g * x
-
-
-# ----------------------------------------------------------------------------
-# Taylor-Green shear wave (G = 0 limit)
-# ----------------------------------------------------------------------------
-def shear_wave_amplitude(u0: float, nu: float, k: float, t):
-    """u(t) = u0 exp(-nu k^2 t) for a shear wave u_x(y) = u0 sin(k y)."""
-    return u0 * np.exp(-nu * k * k * np.asarray(t, dtype=np.float64))
-
-
-def taylor_green_factor(nu: float, k: float, t):
-    """Decay factor exp(-2 nu k^2 t) of the 2-D Taylor-Green vortex with
-    equal wavenumbers k in x and y."""
-    return np.exp(-2.0 * nu * k * k * np.asarray(t, dtype=np.float64))
-
