@@ -9,8 +9,9 @@ collision_term), written so that the precision of each stage can be chosen:
 
 * "store":   the stored populations f* (float32 or float64);
 * "density": rho^a = sum_i f_i, either summed in the working precision or
-             exactly (the float32 pulls summed in float64) and then rounded
-             once;
+             exactly (the float32 pulls summed in float64), the exact sum
+             kept for the composition ("exact") or rounded once to the
+             working precision everywhere ("exact_rounded");
 * "dev":     the deviation of Eq. (feq) from its rest value,
              dev_i = 3 (c.v) + 4.5 (c.v)^2 - 1.5 v^2 + 4.5 (c.v)^3
                      - 4.5 (c.v) v^2  (T0 = 1/3: every constant exact in
@@ -56,7 +57,7 @@ def weights(work, kind="nearest"):
 def step(f, G, g=(0.0, 0.0), work=np.float32, density="work", dev="exact_constants", compose="work",
          weight_kind="nearest"):
     """One step at tau = 1 in working precision `work`; `f` keeps its dtype
-    (the storage).  density: "work" | "exact"; dev: "exact_constants" |
+    (the storage).  density: "work" | "exact" | "exact_rounded"; dev: "exact_constants" |
     "rounded_t0"; compose: "work" | "single_rounding"; weight_kind: as in
     weights()."""
     store = f.dtype
@@ -65,9 +66,11 @@ def step(f, G, g=(0.0, 0.0), work=np.float32, density="work", dev="exact_constan
     # pull (streaming): f_i(x) = f*_i(x - c_i)
     fl = np.stack([np.roll(f[:, i], (CY[i], CX[i]), axis=(-2, -1)) for i in range(9)], axis=1).astype(m)
     # densities
-    if density == "exact":
+    if density in ("exact", "exact_rounded"):
         rho64 = fl.astype(np.float64).sum(axis=1)
         rho = rho64.astype(m)
+        if density == "exact_rounded":          # the low part dropped
+            rho64 = rho.astype(np.float64)
     else:
         rho = fl[:, 0].copy()
         for i in range(1, 9):

@@ -10,8 +10,9 @@ each stage in a chosen precision, and compared with the FP64 oracle:
 | storage only (arithmetic in FP64)               | 8.8e-8  | 3.0e-6  |
 | all, weights rounded to nearest                 | 1.1e-5  | 2.9e-5  |
 | all, 1/36 one ulp low (weights sum to 1)        | 1.4e-6  | 1.8e-5  |
-| all but the density sums and the composition   | 6.9e-8  | 4.5e-6  |
+| all but the density sums and the composition    | 6.9e-8  | 4.5e-6  |
 | the same, deviation divided by a rounded T0     | 4.9e-7  | 1.1e-5  |
+| the same, exact density rounded once everywhere | 3.0e-7  | 8.8e-6  |
 
 So the storage is not the limit; plain FP32 arithmetic is, through the
 density sums and the composition f*_i = w_i rho + w_i rho dev_i (and, for
@@ -93,10 +94,15 @@ def test_exact_density_sums_and_single_rounding_meet_the_contract(droplet):
     """Only the density sums and the composition made exact (rounded once),
     everything else FP32: u within the contract; written with a rounded T0
     instead of exact constants the deviation alone costs more than half
-    again as much."""
+    again as much, and so does dropping the exact density's low part."""
     kw = dict(density="exact", compose="single_rounding")
     err_rho, err_u, drift = errors(droplet, em.run(droplet[0], STEPS, G, **kw))
     assert err_rho < 1e-6 and err_u < 6e-6, (err_rho, err_u)
     assert np.all(drift < 1e-6)
     _, err_u_t0, _ = errors(droplet, em.run(droplet[0], STEPS, G, dev="rounded_t0", **kw))
     assert err_u_t0 > 1.5 * err_u, (err_u_t0, err_u)
+    # the exact density rounded once, its low part never reaching the
+    # stored populations: about twice the error (8.8e-6)
+    _, err_u_hi, _ = errors(droplet, em.run(droplet[0], STEPS, G, density="exact_rounded",
+                                            compose="single_rounding"))
+    assert err_u_hi > 1.5 * err_u, (err_u_hi, err_u)
