@@ -1,0 +1,182 @@
+"""FP32 emulation of the two-component step on a periodic box (numpy).
+
+TEST INFRASTRUCTURE ONLY: tests/test_precision_emulation.py uses it to show where
+the error of an FP32 evaluation of the step against the FP64 oracle comes
+from.  It shares no code with the CUDA library or with the oracle; it is a
+third, vectorised statement of the same step (Section 2 of the paper:
+Eqs. basic_LBM_eq, LBM_BGK at tau = 1, feq, comp_interaction,
+collision_term), written so that the precision of each stage can be chosen:
+
+* "store":   the stored populations f* (float32 or float64);
+* "density": rho^a = sum_i f_i, either summed in the working precision or
+             exactly (the float32 pulls summed in float64), the exact sum
+             kept for the composition ("exact") or rounded once to the
+             working precision everywhere ("exact_rounded");
+* "dev":     the deviation of Eq. (feq) from its rest value,
+             dev_i = 3 (c.v) + 4.5 (c.v)^2 - 1.5 v^2 + 4.5 (c.v)^3
+                     - 4.5 (c.v) v^2  (T0 = 1/3: every constant exact in
+             binary), or the same written with divisions by a rounded T0;
+* "compose": f*_i = w_i rho + w_i rho dev_i, either in the working
+             precision or with w_i rho exact and the sum rounded once;
+* the weights: correctly rounded, or with 1/36 one unit lower so that the
+             nine float32 weights add up to exactly 1.
+
+Only tau = 1 is emulated (f* is then the equilibrium at the force-shifted
+velocity: the non-equilibrium part drops out), on fully periodic boxes: the
+static droplet that the FP32 contract is stated on.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+W = np.array([4 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 36, 1 / 36, 1 / 36, 1 / 36])
+
+
+def initial_state(rho_init, dtype):
+    """f*_i = w_i rho_init (the rest equilibrium), [2, 9, ny, nx]."""
+    return (W[None, :, None, None] * np.asarray(rho_init, dtype=np.float64)[:, None]).astype(dtype)
+
+
+def _shift(a, dx, dy):
+    """a(x + dx, y + dy) on a periodic box (a is [..., ny, nx])."""
+    return np.roll(a, (-dy, -dx), axis=(-2, -1))
+
+
+def weights(work, kind="nearest"):
+    """The nine weights in precision `work`: each correctly rounded
+    ("nearest"), or with 1/36 one unit in the last place lower
+    ("sum_to_one": in float32 the nine then add up to exactly 1)."""
+    w = W.astype(work)
+    if kind == "sum_to_one":
+        w[5:] = np.nextafter(w[5:], work(0))
+    return w
+
+
+def collide(fl, G, g=(0.0, 0.0), work=np.float32, density="work", dev="exact_constants",
+            compose="work", weight_kind="nearest"):
+    """The collision at tau = 1 from the pulled populations fl [2, 9, ny, nx]
+    (already in precision `work`).  Returns (f* [2, 9, ny, nx] in float64
+    holding values of the working precision, unless compose is
+    "single_rounding": then exact sums to be rounded once by the caller,
+    rho [2, ny, nx] in the working precision)."""
+    m = work
+    w = weights(m, weight_kind)
+    # densities
+    if density in ("exact", "exact_rounded"):
+        rho64 = fl.astype(np.float64).sum(axis=1)
+        rho = rho64.astype(m)
+        if density == "exact_rounded":          # the low part dropped
+            rho64 = rho.astype(np.float64)
+    else:
+        rho = fl[:, 0].copy()
+        for i in range(1, 9):
+            rho = rho + fl[:, i]
+        rho64 = rho.astype(np.float64)
+    # momenta (opposite directions paired) and the mixture velocity
+    jx = (fl[:, 1] - fl[:, 3]) + ((fl[:, 5] - fl[:, 7]) + (fl[:, 8] - fl[:, 6]))
+    jy = (fl[:, 2] - fl[:, 4]) + ((fl[:, 5] - fl[:, 7]) + (fl[:, 6] - fl[:, 8]))
+    rt = rho[0] + rho[1]
+    ux = (jx[0] + jx[1]) / rt
+    uy = (jy[0] + jy[1]) / rt
+    out = np.empty(fl.shape, dtype=np.float64)
+    for a in range(2):
+        # Eq. (comp_interaction) / rho^a: G sum_i w_i c_i rho^b(x + c_i)
+        rb = rho[1 - a]
+        d1 = _shift(rb, 1, 1) - _shift(rb, -1, -1)
+        sx = w[1] * (_shift(rb, 1, 0) - _shift(rb, -1, 0)) + w[5] * (d1 + (_shift(rb, 1, -1) - _shift(rb, -1, 1)))
+        sy = w[2] * (_shift(rb, 0, 1) - _shift(rb, 0, -1)) + w[5] * (d1 + (_shift(rb, -1, 1) - _shift(rb, 1, -1)))
+        # Eq. (collision_term): the equilibrium at the force-shifted velocity
+        vx = ux + (m(G) * sx + m(g[0]))
+        vy = uy + (m(G) * sy + m(g[1]))
+        vv = vx * vx + vy * vy
+        t0 = m(1.0 / 3.0)
+        # all nine directions at once (the same operations, element by element)
+        cu = CX.astype(m)[:, None, None] * vx + CY.astype(m)[:, None, None] * vy
+        if dev == "exact_constants":
+            d = cu * (m(3) + cu * (m(4.5) + m(4.5) * cu)) - m(1.5) * vv * (m(1) + m(3) * cu)
+        else:
+            d = (cu / t0 + cu * cu / (m(2) * t0 * t0) - vv / (m(2) * t0)
+                 + cu * cu * cu / (m(6) * t0 * t0 * t0) - cu * vv / (m(2) * t0 * t0))
+        wr = w[:, None, None] * rho[a]
+        if compose == "single_rounding":
+            out[a] = W[:, None, None] * rho64[a] + (wr * d).astype(np.float64)
+        else:
+            out[a] = wr + wr * d
+    return out, rho
+
+
+def pull(f):
+    """Streaming: f_i(x) = f*_i(x - c_i) on the periodic box."""
+    return np.stack([np.roll(f[:, i], (CY[i], CX[i]), axis=(-2, -1)) for i in range(9)], axis=1)
+
+
+def step(f, G, work=np.float32, **kw):
+    """One step at tau = 1 in working precision `work` (keywords as in
+    collide); `f` keeps its dtype (the storage)."""
+    out, _ = collide(pull(f).astype(work), G, work=work, **kw)
+    return out.astype(f.dtype)
+
+
+def run(rho_init, steps, G, store=np.float32, **kw):
+    """`steps` steps from the rest equilibrium of rho_init; returns f*."""
+    f = initial_state(rho_init, store)
+    for _ in range(steps):
+        f = step(f, G, **kw)
+    return f
+
+
+# ----------------------------------------------------------------------------
+# 16-bit storage of the populations, shifted by a reference equilibrium
+# ----------------------------------------------------------------------------
+def to16(x, fmt):
+    """Round float32 values to FP16 or BF16 (nearest, ties to even); the
+    result is float32 holding values of the 16-bit format."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    drop = 13 if fmt == "fp16" else 16          # mantissa bits beyond the format's
+    u = x.view(np.uint32).astype(np.uint64)
+    u = (u + (((u >> drop) & 1) + (1 << (drop - 1)) - 1)) & (0xFFFFFFFF ^ ((1 << drop) - 1))
+    out = u.astype(np.uint32).view(np.float32)
+    if fmt == "fp16":
+        # below 2^-14 FP16 is subnormal: a fixed spacing of 2^-24
+        tiny = np.abs(x) < 2.0 ** -14
+        out = np.where(tiny, np.round(x.astype(np.float64) * 2.0 ** 24) * 2.0 ** -24, out).astype(np.float32)
+    return out
+
+
+def _shifted_w(rh, shift):
+    """w_i times the reference density of each stored population of a node:
+    rh [2, ny, nx] is the node's own ("node") or, for direction i, that of
+    the node x + c_i that will pull it ("destination")."""
+    if shift == "node":
+        return np.stack([W[i] * rh for i in range(9)], axis=1)
+    return np.stack([W[i] * _shift(rh, CX[i], CY[i]) for i in range(9)], axis=1)
+
+
+def run16(rho_init, steps, G, fmt="fp16", shift="node", work=np.float32, **kw):
+    """`steps` steps with the populations stored in 16 bits as
+    s_i = f*_i - w_i rhohat, rhohat the 16-bit density of the storing node
+    ("node"), of the node that pulls the population next ("destination",
+    which knows it as its own previous density), or each species' initial
+    mean ("constant"); rhohat is stored too.  Returns f* decoded (float64)."""
+    rho_init = np.asarray(rho_init, dtype=np.float64)
+    f = W[None, :, None, None] * rho_init[:, None]
+    if shift == "constant":
+        rh = np.broadcast_to(rho_init.mean(axis=(1, 2))[:, None, None], rho_init.shape).astype(np.float32)
+    else:
+        rh = to16(rho_init, fmt)
+    s = to16(f - _shifted_w(rh, "node" if shift == "constant" else shift), fmt)
+    m = work
+    for _ in range(steps):
+        # decode the pulled populations: s_i(x - c_i) + w_i rhohat
+        ps = pull(s).astype(m)
+        if shift == "node":
+            ref = pull(_shifted_w(rh, "node"))
+        else:
+            ref = _shifted_w(rh, "node")        # the pulling node's own rhohat
+        out, rho = collide(ps + ref.astype(m), G, work=m, **kw)
+        if shift != "constant":
+            rh = to16(rho, fmt)
+        s = to16(out.astype(m) - _shifted_w(rh, "node" if shift == "constant" else shift).astype(m), fmt)
+    return s.astype(np.float64) + _shifted_w(rh, "node" if shift == "constant" else shift)
