@@ -55,7 +55,7 @@ def peaks():
         with open(path) as fh:
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
-    except Exception:
+    except (OSError, ValueError, KeyError, TypeError):
         return 6800.0, "fallback"
 
 
@@ -84,8 +84,8 @@ def recorded_traffic(precision, wname, kinfo):
         e = d.get(f"{wname}/{precision}")
         if e and e.get("kernel_info") == kinfo and e.get("kernel_sha") == kernel_hash(kinfo["variant"]):
             return float(e["dram_bytes_per_launch"])
-    except Exception:
-        pass
+    except (OSError, ValueError, KeyError, TypeError, AttributeError):
+        pass                                # no usable record: traffic unknown
     return None
 
 
@@ -111,7 +111,7 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
-        except Exception:
+        except OSError:                     # no nvidia-smi on this machine
             self.proc = None
 
     def _read(self):
@@ -131,7 +131,7 @@ class ClockSampler:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
-            except Exception:
+            except subprocess.TimeoutExpired:
                 self.proc.kill()
         rows = [r for r in self.rows if t0 is not None and r[0] is not None and t0 <= r[0] <= t1]
         inside = bool(rows)
@@ -208,7 +208,7 @@ def host_cores():
             if line.strip().startswith("Model name:"):
                 model = line.split(":", 1)[1].strip()
                 break
-    except Exception:
+    except (OSError, subprocess.SubprocessError):
         pass
     return n, model
 
