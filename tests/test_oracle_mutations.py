@@ -290,6 +290,7 @@ def _python_battery():
         ("synthetic contact angle", lambda: [c.test_contact_angle_of_a_synthetic_circular_interface(t)
                                              for t in (35.0, 115.0)]),
         ("droplet radius", lambda: p.test_droplet_radius_of_a_synthetic_tanh_disc(17.3, 64.0, 64.0)),
+        ("Laplace fit", p.test_laplace_fit_recovers_a_known_line),
         ("straight channel / symmetric slug",
          lambda: c.test_balance_vanishes_in_a_straight_channel_and_for_symmetric_slugs(60)),
         ("long-wavelength limit", lambda: c.test_long_wavelength_limit_is_the_curvature_difference(50)),

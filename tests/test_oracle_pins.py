@@ -536,6 +536,20 @@ def flat_interface_sigma():
     return 0.5 * float(np.sum(p_n.mean() - p_t))
 
 
+def test_laplace_fit_recovers_a_known_line():
+    """Pressure jumps that lie exactly on dP = sigma / R + c give back sigma,
+    c and a coefficient of determination of 1; a jump off the line lowers
+    the coefficient."""
+    radii = np.array([8.5, 11.0, 14.2, 19.0, 26.3])
+    sigma, c = 0.0875, 4e-4
+    s, c_fit, r2 = analytic.laplace_fit(radii, sigma / radii + c)
+    assert s == pytest.approx(sigma, rel=1e-12) and c_fit == pytest.approx(c, rel=1e-9)
+    assert r2 == pytest.approx(1.0, abs=1e-12)
+    off = sigma / radii + c
+    off[2] *= 1.05
+    assert analytic.laplace_fit(radii, off)[2] < 0.999
+
+
 @pytest.mark.parametrize("R,cx,cy", [(17.3, 64.0, 64.0), (9.71, 40.0, 41.0), (24.05, 63.0, 60.0)])
 def test_droplet_radius_of_a_synthetic_tanh_disc(R, cx, cy):
     """droplet_radius on a disc whose density is exactly the tanh profile
