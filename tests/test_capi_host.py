@@ -133,6 +133,33 @@ def test_null_handle_calls_fail_cleanly(lib):
     lib.lbm_destroy(None)
 
 
+@pytest.mark.parametrize("bad,needle", [
+    (dict(precision="fp64"), "LBM_FP32"),
+    (dict(nx=2048, ny=1025), "2097152"),
+    (dict(nx=0, ny=8), "2097152"),
+    (dict(eq_order=4), "eq_order"),
+    (dict(collision=2), "collision"),
+    (dict(tau=(0.5, 1.0)), "tau"),
+    (dict(tau=(1.0, float("inf"))), "tau"),
+    (dict(G=float("nan")), "finite"),
+    (dict(g=(float("inf"), 0.0)), "finite"),
+    (dict(rho_wall=(0.1, float("nan"))), "finite"),
+])
+def test_noalloc_step_checks_its_arguments_on_the_host(lib, bad, needle):
+    """The allocation-free step rejects every argument it cannot step with
+    (LBM_EINVAL and a message naming it) before it touches the device; the
+    pointers here are host buffers it never reads."""
+    kw = dict(nx=16, ny=8)
+    kw.update(bad)
+    p = lbm.make_params(**kw)
+    buf = (ctypes.c_float * 16)()
+    mask = (ctypes.c_uint8 * 16)()
+    rc = lib.lbm_step_noalloc(ctypes.addressof(mask), ctypes.addressof(buf), ctypes.addressof(buf), None,
+                              ctypes.byref(p))
+    assert rc == lbm.LBM_EINVAL
+    assert needle in lbm.lbm_last_error(None)
+
+
 def test_every_handle_call_rejects_a_null_handle(lib):
     """Each call that takes a handle returns LBM_EINVAL for NULL (as the
     header states) before it touches a device, and every destroy ignores
