@@ -249,7 +249,7 @@ int lbm_step_noalloc(const uint8_t *mask, const float *f_in, float *f_out, lbm_o
 typedef struct lbm3d_t lbm3d_t; /* opaque */
 
 typedef struct {
-    int32_t nx, ny, nz;           /* lattice size, each >= 1; ny, nz <= 65535 */
+    int32_t nx, ny, nz;           /* lattice size, each in [1, 2^21], 38 nx ny nz < 2^40 */
     int32_t periodic[3];          /* 1 = periodic along x, y, z (else solid boundary planes) */
     double tau[2];                /* tau^o, tau^w (> 1/2) */
     double G;                     /* Eq. (comp_interaction) */
@@ -263,9 +263,11 @@ typedef struct {
 
 /* Create from a host mask [nz][ny][nx] (1 = solid) and host initial
  * densities [2][nz][ny][nx] (the state starts at f*_i = w_i rho_init).
- * Errors: LBM_EINVAL (sizes, parameters, precision, a non-periodic
- * direction whose boundary planes hold fluid, densities at fluid nodes not
- * finite, negative or both zero), LBM_ENOMEM, LBM_ECUDA. */
+ * Errors: LBM_EINVAL (sizes, parameters: tau > 1/2 and finite, G, g and
+ * rho_wall finite, precision, eq_order, collision; a non-periodic direction
+ * whose boundary planes hold fluid; densities at fluid nodes not finite,
+ * negative or both zero: all checked on the host before any device work),
+ * LBM_ENOMEM, LBM_ECUDA. */
 int lbm3d_create(const uint8_t *mask, const double *rho_init, const lbm3d_params *p, lbm3d_t **out);
 /* Advance nsteps >= 0 steps (asynchronous on the handle's stream).
  * LBM_EINVAL for a NULL handle or nsteps < 0, LBM_ECUDA when a launch fails. */

@@ -238,3 +238,40 @@ def test_sweep_specs_are_seeded():
         assert 0.2 <= s.visc_ratio <= 10
         w = wl.channel_instance(s)
         assert w.mask.shape == (s.ny, s.nx)
+
+
+@pytest.mark.parametrize("bad,needle", [
+    (dict(nz=0), "nx, ny, nz"),
+    (dict(precision=2), "precision"),
+    (dict(eq_order=1), "eq_order"),
+    (dict(collision=3), "collision"),
+    (dict(tau=(1.0, 0.5)), "tau"),
+    (dict(G=float("inf")), "finite"),
+    (dict(g=(0.0, 0.0, float("nan"))), "finite"),
+    (dict(periodic=(1, 1, 0)), "boundary plane"),
+    (dict(rho_bad=-0.1), "rho_init"),
+    (dict(rho_bad=float("nan")), "rho_init"),
+])
+def test_d3q19_create_checks_its_arguments_on_the_host(lib, bad, needle):
+    """lbm3d_create rejects sizes, parameters, an open direction with fluid
+    on its boundary planes and bad initial densities with LBM_EINVAL and a
+    message, on the host, before any device work."""
+    from paper_1601_00918_gb300.lbm import Params3
+    kw = dict(nx=6, ny=5, nz=4, precision=0, eq_order=3, collision=0, tau=(1.0, 1.0), G=-1.79,
+              g=(0.0, 0.0, 0.0), periodic=(1, 1, 1))
+    rho_bad = bad.pop("rho_bad", None)
+    kw.update(bad)
+    n = 6 * 5 * 4
+    mask = np.zeros(n, np.uint8)
+    rho = np.full(2 * n, 0.5)
+    if rho_bad is not None:
+        rho[7] = rho_bad
+    p = Params3(kw["nx"], kw["ny"], kw["nz"], (ctypes.c_int32 * 3)(*kw["periodic"]),
+                (ctypes.c_double * 2)(*kw["tau"]), kw["G"], (ctypes.c_double * 2)(0.0, 0.0),
+                (ctypes.c_double * 3)(*kw["g"]), kw["precision"], kw["eq_order"], kw["collision"], None)
+    h = ctypes.c_void_p()
+    rc = lib.lbm3d_create(mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                          rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(p), ctypes.byref(h))
+    assert rc == lbm.LBM_EINVAL and not h.value
+    lib.lbm3d_last_error.restype = ctypes.c_char_p
+    assert needle in lib.lbm3d_last_error(None).decode()
