@@ -72,13 +72,14 @@ struct Geom {
     double lam, h0, amp, yc, centre, half, spacing;
 };
 
-int periods_of(const lbm_channel_spec& s) { return s.n_periods > 0 ? s.n_periods : 4; }
-int slugs_of(const lbm_channel_spec& s) { return s.n_slugs > 0 ? s.n_slugs : 1; }
+// 0 selects the default; a negative count is out of range (geom_of rejects it)
+int periods_of(const lbm_channel_spec& s) { return s.n_periods != 0 ? s.n_periods : 4; }
+int slugs_of(const lbm_channel_spec& s) { return s.n_slugs != 0 ? s.n_slugs : 1; }
 
 bool geom_of(const lbm_channel_spec& s, Geom* g) {
     const int np = periods_of(s), ns = slugs_of(s);
     if (s.lambda < 8 || s.lambda > (1 << 16) || np < 2 || np > 64) return false;
-    if (ns > np || np % ns != 0) return false;
+    if (ns < 1 || ns > np || np % ns != 0) return false;
     if (!(s.amp_ratio >= 0.0 && s.amp_ratio <= 0.95)) return false;
     if (!(s.slug_len_over_lambda > 0.0 && s.slug_len_over_lambda <= np / ns - (ns > 1 ? 0.25 : 1.0))) return false;
     if (!(s.theta_deg > 0.0 && s.theta_deg < 180.0) || !(s.visc_ratio > 0.0) || !std::isfinite(s.visc_ratio))

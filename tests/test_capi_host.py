@@ -275,3 +275,39 @@ def test_d3q19_create_checks_its_arguments_on_the_host(lib, bad, needle):
     assert rc == lbm.LBM_EINVAL and not h.value
     lib.lbm3d_last_error.restype = ctypes.c_char_p
     assert needle in lib.lbm3d_last_error(None).decode()
+
+
+def _shape(lib, **kw):
+    spec = dict(lam=64, amp_ratio=0.5, slug_len_over_lambda=1.5, theta_deg=60.0, visc_ratio=1.0, n_periods=0,
+                n_slugs=0)
+    spec.update(kw)
+    cs = lbm.ChannelSpec(spec["lam"], spec["amp_ratio"], spec["slug_len_over_lambda"], spec["theta_deg"],
+                         spec["visc_ratio"], spec["n_periods"], spec["n_slugs"])
+    nx, ny = ctypes.c_int32(), ctypes.c_int32()
+    rc = lib.lbm_channel_shape(ctypes.byref(cs), ctypes.byref(nx), ctypes.byref(ny))
+    return rc, nx.value, ny.value
+
+
+@pytest.mark.parametrize("bad", [
+    dict(lam=4), dict(lam=70000), dict(n_periods=1), dict(n_periods=65), dict(n_periods=-2),
+    dict(n_periods=4, n_slugs=3), dict(n_slugs=-1), dict(amp_ratio=-0.1), dict(amp_ratio=0.96),
+    dict(amp_ratio=float("nan")), dict(slug_len_over_lambda=0.0), dict(slug_len_over_lambda=3.01),
+    dict(n_slugs=2, slug_len_over_lambda=1.76), dict(theta_deg=0.0), dict(theta_deg=180.0),
+    dict(visc_ratio=0.0), dict(visc_ratio=float("inf")),
+])
+def test_channel_spec_ranges(lib, bad):
+    """A channel description outside the ranges the header states is
+    rejected with LBM_EINVAL (host, no GPU)."""
+    assert _shape(lib, **bad)[0] == lbm.LBM_EINVAL
+
+
+def test_channel_spec_defaults_and_limits(lib):
+    """0 periods and 0 slugs select 4 and 1; the longest slugs the header
+    admits (n_periods - 1 wavelengths for one slug, n_periods / n_slugs - 1/4
+    for several) are accepted; the lattice is lambda n_periods by
+    2 ceil(h0 + A) + 2 with h0 = 0.1875 lambda."""
+    assert _shape(lib) == (lbm.LBM_OK, 256, 2 * 18 + 2)
+    assert _shape(lib, n_periods=4, n_slugs=1)[1:] == (256, 38)
+    assert _shape(lib, slug_len_over_lambda=3.0)[0] == lbm.LBM_OK
+    assert _shape(lib, n_slugs=2, slug_len_over_lambda=1.75)[0] == lbm.LBM_OK
+    assert _shape(lib, lam=128, n_periods=6, amp_ratio=0.2)[1:] == (768, 2 * 29 + 2)
