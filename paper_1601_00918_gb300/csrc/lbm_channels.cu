@@ -831,10 +831,13 @@ int lbm_slug_area(const double* rho, const uint8_t* mask, int32_t nx, int32_t ny
 }
 
 int lbm_wall_potentials(const double* r, const double* theta, int32_t n, double theta_deg, double* rho_wall) {
-    if (!r || !theta || !rho_wall || n < 2) return cfail(LBM_EINVAL, "bad argument");
+    if (!r || !theta || !rho_wall || n < 2 || !std::isfinite(theta_deg)) return cfail(LBM_EINVAL, "bad argument");
     Calib c;
     c.r.assign(r, r + n);
     c.theta.assign(theta, theta + n);
+    for (int k = 0; k < n; k++)
+        if (!std::isfinite(c.r[k]) || !std::isfinite(c.theta[k]))
+            return cfail(LBM_EINVAL, "calibration table: entry %d is not finite", k);
     for (int k = 0; k + 1 < n; k++)
         if (!(c.r[k] < c.r[k + 1]) || !(c.theta[k] > c.theta[k + 1]))
             return cfail(LBM_EINVAL, "calibration table: r must ascend and theta descend");
@@ -877,6 +880,9 @@ int lbm_critical_pressure_channels(const lbm_channel_spec* specs, int32_t n, con
         if (!o->calib_r || !o->calib_theta || o->calib_n < 2) return cfail(LBM_EINVAL, "bad calibration table");
         cal.r.assign(o->calib_r, o->calib_r + o->calib_n);
         cal.theta.assign(o->calib_theta, o->calib_theta + o->calib_n);
+        for (int k = 0; k < o->calib_n; k++)
+            if (!std::isfinite(cal.r[k]) || !std::isfinite(cal.theta[k]))
+                return cfail(LBM_EINVAL, "calibration table: entry %d is not finite", k);
         for (int k = 0; k + 1 < o->calib_n; k++)
             if (!(cal.r[k] < cal.r[k + 1]) || !(cal.theta[k] > cal.theta[k + 1]))
                 return cfail(LBM_EINVAL, "calibration table: r must ascend and theta descend");

@@ -49,6 +49,25 @@ def test_potentials_for_inverts_the_table():
     assert tab.potentials_for(10.0) == pytest.approx((0.0, 0.4))        # clipped to the table
 
 
+@pytest.mark.parametrize("r,theta,theta_deg", [
+    ([-0.4, 0.0, 0.4], [135.0, 90.0, 45.0], float("nan")),
+    ([-0.4, float("nan"), 0.4], [135.0, 90.0, 45.0], 60.0),
+    ([-float("inf"), 0.0, 0.4], [135.0, 90.0, 45.0], 60.0),
+    ([-0.4, 0.0, 0.4], [135.0, 90.0, -float("inf")], 60.0),
+    ([-0.4, 0.4, 0.0], [135.0, 90.0, 45.0], 60.0),
+    ([-0.4, 0.0, 0.4], [45.0, 90.0, 135.0], 60.0),
+    ([0.0], [90.0], 60.0),
+])
+def test_wall_potentials_reject_bad_tables(r, theta, theta_deg):
+    """The table inversion refuses a contact angle or a table entry that is
+    not finite, and a table that is not ascending in r and descending in
+    theta (LBM_EINVAL), instead of returning interpolated garbage."""
+    from paper_1601_00918_gb300 import lbm
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_wall_potentials(np.array(r), np.array(theta), theta_deg)
+    assert e.value.code == lbm.LBM_EINVAL
+
+
 @pytest.mark.parametrize("theta_deg,area,x_rest", [(40.0, 2612.0, 77.4), (60.0, 2528.0, 80.0),
                                                    (90.0, 2600.0, 79.7), (120.0, 2576.0, 81.3),
                                                    (140.0, 2560.0, 82.4)])
