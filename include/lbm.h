@@ -385,8 +385,9 @@ typedef struct {
 /* Bisect every instance of b on its x body force, starting from the brackets
  * [g_lo[i], g_hi[i]]; all instances probe in lockstep, finished ones drop
  * out of the launches.  Classification and bracket updates run on the
- * device in FP64.  Returns LBM_ETIMEOUT (results filled, status 3) when
- * timeout_s ran out. */
+ * device in FP64.  LBM_EINVAL unless 0 < g_lo[i] < g_hi[i] < infinity for
+ * every instance, rel_bracket > 0, t_obs >= 1, t_eq >= 0 and max_probes >= 1.
+ * Returns LBM_ETIMEOUT (results filled, status 3) when timeout_s ran out. */
 int lbm_critical_pressure_batch(lbm_batch_t *b, const double *g_lo, const double *g_hi,
                                 const lbm_bisect_opts *o, lbm_crit_result *out);
 

@@ -871,8 +871,8 @@ int lbm_critical_pressure_batch(lbm_batch_t* b, const double* g_lo, const double
     if (!(o->rel_bracket > 0.0) || o->t_obs < 1 || o->t_eq < 0 || o->max_probes < 1)
         return batch_fail(b, LBM_EINVAL, "bad bisection options");
     for (int i = 0; i < b->n; i++)
-        if (!(g_lo[i] > 0.0) || !(g_hi[i] > g_lo[i]))
-            return batch_fail(b, LBM_EINVAL, "instance %d: need 0 < g_lo < g_hi", i);
+        if (!(g_lo[i] > 0.0) || !(g_hi[i] > g_lo[i]) || !std::isfinite(g_hi[i]))
+            return batch_fail(b, LBM_EINVAL, "instance %d: need 0 < g_lo < g_hi < infinity", i);
     const auto t_start = std::chrono::steady_clock::now();
     // reset records: bracket, state machine, observables; everyone active
     std::vector<BatchInst> h(b->n);
