@@ -9,14 +9,14 @@ Tolerances (derived from the arithmetic, written here):
   |gpu - oracle| <= 5e-6.
 * FP32 storage after 1000 steps: relative L-infinity <= 1e-5 on rho and u,
   mass drift <= 1e-6 relative, with the compensated arithmetic ("fp32c":
-  error-free density sums and composition of the stored populations).  An
-  FP32 emulation of the step (numpy, every stage in float32 unless promoted)
-  shows why: FP32 storage with exact arithmetic leaves 3-4e-6 on u; plain
-  FP32 arithmetic 1.3e-5 to 2e-5, set by two stages only (the density sums
-  and the composition f* = w rho + t); compensating those two brings it back
-  to 3.5e-6 (droplet) and 4.6e-6 (channel, plain and regularised).  The
-  plain FP32 arithmetic ("fp32") is kept as the fast form and bounded at
-  3e-5 on u.
+  error-free density sums and composition of the stored populations).  The
+  FP32 emulation of tests/precision_emulation.py (numpy, each stage's
+  precision chosen; tests/test_precision_emulation.py) shows why on the
+  droplet: FP32 storage with exact arithmetic leaves 3.0e-6 on u; plain FP32
+  arithmetic 1.8e-5, set by two stages (the density sums and the
+  composition f* = w rho + t); with those two exact it is back at 4.5e-6.
+  The plain FP32 arithmetic ("fp32") is kept as the fast form and bounded
+  at 3e-5 on u.
 * FP16/BF16 shifted storage: parity is not fixed by the paper; the bound comes
   from the storage rounding of |f - w rho_ref| <= w max|rho - rho_ref|
   (2^-11 and 2^-8 relative), amplified over the run; the tests state it.
