@@ -54,13 +54,21 @@ def weights(work, kind="nearest"):
     return w
 
 
+OPP = np.array([0, 3, 4, 1, 2, 7, 8, 5, 6])
+
+
 def collide(fl, G, g=(0.0, 0.0), work=np.float32, density="work", dev="exact_constants",
-            compose="work", weight_kind="nearest"):
-    """The collision at tau = 1 from the pulled populations fl [2, 9, ny, nx]
-    (already in precision `work`).  Returns (f* [2, 9, ny, nx] in float64
-    holding values of the working precision, unless compose is
-    "single_rounding": then exact sums to be rounded once by the caller,
-    rho [2, ny, nx] in the working precision)."""
+            compose="work", weight_kind="nearest", tau=(1.0, 1.0), rho_wall=(0.0, 0.0), mask=None,
+            regularized=False, rest="equilibrium"):
+    """The collision from the pulled populations fl [2, 9, ny, nx] (already in
+    precision `work`), mask [ny, nx] (1 = solid, whose densities the wall
+    potentials rho_wall replace in the force) or None for a fully fluid box.
+    Returns (f* [2, 9, ny, nx] in the working precision, or in float64 the
+    exact sums to be rounded once by the caller when compose is
+    "single_rounding"; rho [2, ny, nx] in the working precision).  With compose "single_rounding" the non-equilibrium part is
+    also taken against the exact w_i rho (so it carries no mass); rest
+    "by_mass" sets the rest population to what the other eight leave of
+    rho (f*_0 = rho - sum_{i>0} f*_i, the same value in exact arithmetic)."""
     m = work
     w = weights(m, weight_kind)
     # densities
@@ -80,50 +88,101 @@ def collide(fl, G, g=(0.0, 0.0), work=np.float32, density="work", dev="exact_con
     rt = rho[0] + rho[1]
     ux = (jx[0] + jx[1]) / rt
     uy = (jy[0] + jy[1]) / rt
-    out = np.empty(fl.shape, dtype=np.float64)
+    # mixture relaxation: nu_mix = (rho^o nu^o + rho^w nu^w) / rho, tau_mix = 3 nu_mix + 1/2
+    relax = tuple(tau) != (1.0, 1.0)
+    if relax:
+        nu = [m((t - 0.5) / 3.0) for t in tau]
+        tau_mix = m(3) * ((rho[0] * nu[0] + rho[1] * nu[1]) / rt) + m(0.5)
+        keep = m(1) - m(1) / tau_mix                  # 1 - 1 / tau_mix
+    cx = CX.astype(m)[:, None, None]
+    cy = CY.astype(m)[:, None, None]
+
+    def deviation(vx, vy):
+        vv = vx * vx + vy * vy
+        cu = cx * vx + cy * vy
+        if dev == "exact_constants":
+            return cu * (m(3) + cu * (m(4.5) + m(4.5) * cu)) - m(1.5) * vv * (m(1) + m(3) * cu)
+        t0 = m(1.0 / 3.0)
+        return (cu / t0 + cu * cu / (m(2) * t0 * t0) - vv / (m(2) * t0)
+                + cu * cu * cu / (m(6) * t0 * t0 * t0) - cu * vv / (m(2) * t0 * t0))
+
+    out = np.empty(fl.shape, dtype=np.float64 if compose == "single_rounding" else m)
     for a in range(2):
-        # Eq. (comp_interaction) / rho^a: G sum_i w_i c_i rho^b(x + c_i)
-        rb = rho[1 - a]
+        # Eq. (comp_interaction) / rho^a: G sum_i w_i c_i rho^b(x + c_i), a
+        # solid neighbour carrying the wall potential
+        rb = rho[1 - a] if mask is None else np.where(mask != 0, m(rho_wall[1 - a]), rho[1 - a])
         d1 = _shift(rb, 1, 1) - _shift(rb, -1, -1)
         sx = w[1] * (_shift(rb, 1, 0) - _shift(rb, -1, 0)) + w[5] * (d1 + (_shift(rb, 1, -1) - _shift(rb, -1, 1)))
         sy = w[2] * (_shift(rb, 0, 1) - _shift(rb, 0, -1)) + w[5] * (d1 + (_shift(rb, -1, 1) - _shift(rb, 1, -1)))
-        # Eq. (collision_term): the equilibrium at the force-shifted velocity
-        vx = ux + (m(G) * sx + m(g[0]))
-        vy = uy + (m(G) * sy + m(g[1]))
-        vv = vx * vx + vy * vy
-        t0 = m(1.0 / 3.0)
-        # all nine directions at once (the same operations, element by element)
-        cu = CX.astype(m)[:, None, None] * vx + CY.astype(m)[:, None, None] * vy
-        if dev == "exact_constants":
-            d = cu * (m(3) + cu * (m(4.5) + m(4.5) * cu)) - m(1.5) * vv * (m(1) + m(3) * cu)
-        else:
-            d = (cu / t0 + cu * cu / (m(2) * t0 * t0) - vv / (m(2) * t0)
-                 + cu * cu * cu / (m(6) * t0 * t0 * t0) - cu * vv / (m(2) * t0 * t0))
         wr = w[:, None, None] * rho[a]
-        if compose == "single_rounding":
-            out[a] = W[:, None, None] * rho64[a] + (wr * d).astype(np.float64)
+        exact = compose == "single_rounding"
+        if exact:
+            wex = W[:, None, None] * rho64[a]             # w_i rho, exact
+            wl = (wex - wr.astype(np.float64)).astype(m)
         else:
-            out[a] = wr + wr * d
+            wl = m(0)
+        # Eq. (collision_term): the equilibrium at the force-shifted velocity
+        ds = deviation(ux + (m(G) * sx + m(g[0])), uy + (m(G) * sy + m(g[1])))
+        t = wr * ds
+        if relax:
+            # Eq. (LBM_BGK): (1 - 1/tau_mix) f', f' = f - f^eq(rho^a, u_mix)
+            fneq = ((fl[a] - wr) - wl) - wr * deviation(ux, uy)
+            if regularized:
+                # Eq. (Regualize): w_i Q_i : Pi / (2 T0^2), Q_i = c_i c_i - T0 I
+                pxx = (cx * cx * fneq).sum(axis=0, dtype=m)
+                pyy = (cy * cy * fneq).sum(axis=0, dtype=m)
+                pxy = (cx * cy * fneq).sum(axis=0, dtype=m)
+                third = m(1.0 / 3.0)
+                fneq = w[:, None, None] * m(4.5) * ((cx * cx - third) * pxx + (cy * cy - third) * pyy
+                                                   + m(2) * (cx * cy) * pxy)
+            t = t + keep * fneq
+        if exact:
+            # (w_i rho)(1 + D_i) + (1 - 1/tau) f'_i with w_i rho exact: its low
+            # part scales with the deviation too, then one rounding
+            out[a] = wex + (t + wl * ds).astype(np.float64)
+        else:
+            out[a] = wr + t
+        if rest == "by_mass":
+            if exact:
+                out[a, 0] = wex[0] - t[1:].sum(axis=0, dtype=m).astype(np.float64)
+            else:
+                out[a, 0] = rho[a] - out[a, 1:].astype(m).sum(axis=0, dtype=m)
     return out, rho
 
 
-def pull(f):
-    """Streaming: f_i(x) = f*_i(x - c_i) on the periodic box."""
-    return np.stack([np.roll(f[:, i], (CY[i], CX[i]), axis=(-2, -1)) for i in range(9)], axis=1)
+def pull(f, mask=None):
+    """Streaming: f_i(x) = f*_i(x - c_i), or f*_opp(i)(x) when x - c_i is
+    solid (halfway bounce-back); indices wrap."""
+    out = np.empty_like(f)
+    for i in range(9):
+        moved = np.roll(f[:, i], (CY[i], CX[i]), axis=(-2, -1))
+        if mask is None:
+            out[:, i] = moved
+        else:
+            src_solid = np.roll(mask, (CY[i], CX[i]), axis=(0, 1)) != 0
+            out[:, i] = np.where(src_solid, f[:, OPP[i]], moved)
+    return out
 
 
-def step(f, G, work=np.float32, **kw):
-    """One step at tau = 1 in working precision `work` (keywords as in
-    collide); `f` keeps its dtype (the storage)."""
-    out, _ = collide(pull(f).astype(work), G, work=work, **kw)
-    return out.astype(f.dtype)
+def step(f, G, work=np.float32, mask=None, **kw):
+    """One step in working precision `work` (keywords as in collide); `f`
+    keeps its dtype (the storage); solid nodes hold zeros."""
+    with np.errstate(invalid="ignore", divide="ignore"):     # solid nodes: 0 / 0, zeroed below
+        out, _ = collide(pull(f, mask).astype(work), G, work=work, mask=mask, **kw)
+    out = out.astype(f.dtype)
+    if mask is not None:
+        out[:, :, mask != 0] = 0
+    return out
 
 
-def run(rho_init, steps, G, store=np.float32, **kw):
-    """`steps` steps from the rest equilibrium of rho_init; returns f*."""
+def run(rho_init, steps, G, store=np.float32, mask=None, **kw):
+    """`steps` steps from the rest equilibrium of rho_init (zero at solid
+    nodes of mask); returns f*."""
     f = initial_state(rho_init, store)
+    if mask is not None:
+        f[:, :, mask != 0] = 0
     for _ in range(steps):
-        f = step(f, G, **kw)
+        f = step(f, G, mask=mask, **kw)
     return f
 
 
