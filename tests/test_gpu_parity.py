@@ -13,8 +13,9 @@ Tolerances (derived from the arithmetic, written here):
   FP32 emulation of tests/precision_emulation.py (numpy, each stage's
   precision chosen; tests/test_precision_emulation.py) shows why on the
   droplet: FP32 storage with exact arithmetic leaves 3.0e-6 on u; plain FP32
-  arithmetic 1.8e-5, set by two stages (the density sums and the
-  composition f* = w rho + t); with those two exact it is back at 4.5e-6.
+  arithmetic 1.7e-5 (2.0e-5 on the channel), set by two stages (the density
+  sums and the composition f* = w rho + t); with those two exact it is back
+  at 3.3e-6 (7.7e-6 on the channel).
   The plain FP32 arithmetic ("fp32") is kept as the fast form and bounded
   at 3e-5 on u.
 * FP16/BF16 shifted storage: parity is not fixed by the paper; the bound comes
