@@ -239,3 +239,31 @@ def run16(rho_init, steps, G, fmt="fp16", shift="node", work=np.float32, **kw):
             rh = to16(rho, fmt)
         s = to16(out.astype(m) - _shifted_w(rh, "node" if shift == "constant" else shift).astype(m), fmt)
     return s.astype(np.float64) + _shifted_w(rh, "node" if shift == "constant" else shift)
+
+
+# ----------------------------------------------------------------------------
+# the cases of tests/test_precision_emulation.py, runnable in a worker process
+# ----------------------------------------------------------------------------
+def case_inputs(case):
+    """(mask or None, rho_init, keywords) of a named case: the static droplet
+    (128 x 128 periodic, R = 20, tau = 1) or the sinusoidal channel of the GPU
+    parity tests (300 x 40, tau = (1, 0.9), wall potentials (0.3, 0.1), body
+    force 2e-5; "channel_bgk" or "channel_reg" for the collision)."""
+    from paper_1601_00918_gb300 import workloads as wl
+    if case == "droplet":
+        return None, wl.droplet(128, 128, 20.0, 64.0, 64.0), {}
+    nx, ny = 300, 40
+    mask = wl.sinusoidal_channel(nx, ny, 12.0, 5.0, 100.0)
+    kw = dict(tau=(1.0, 0.9), rho_wall=(0.3, 0.1), g=(2e-5, 0.0), regularized=case == "channel_reg")
+    return mask, wl.slug(nx, ny, 0.3 * nx, 0.7 * nx), kw
+
+
+def run_case(job):
+    """job = (case, steps, G, options): the state f* after `steps` steps, 16-bit
+    storage when the options name a format ("fmt")."""
+    case, steps, G, opts = job
+    mask, rho, kw = case_inputs(case)
+    opts = dict(opts)
+    if "fmt" in opts:
+        return run16(rho, steps, G, **opts)
+    return run(rho, steps, G, mask=mask, **kw, **opts)

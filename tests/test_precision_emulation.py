@@ -8,56 +8,83 @@ parity tests (300 x 40, walls, wall potentials, body force, tau = (1, 0.9),
 plain BGK and regularised) with each stage in a chosen precision, and is
 compared with the FP64 oracle after 1000 steps (u, relative L-infinity):
 
-| form                                                        | droplet | channel BGK / reg. |
-|-------------------------------------------------------------|---------|--------------------|
+| form                                                         | droplet | channel BGK / reg. |
+|--------------------------------------------------------------|---------|--------------------|
 | FP32 storage, FP64 arithmetic                                | 3.0e-6  |                    |
-| plain FP32 (weights summing to 1, rest population by mass)  | 1.7e-5  | 2.0e-5 / 1.7e-5    |
+| plain FP32 (weights summing to 1, rest population by mass)   | 1.7e-5  | 2.0e-5 / 1.7e-5    |
 | compensated: density sums exact, w_i rho exact, one rounding | 3.3e-6  | 7.7e-6 / 6.3e-6    |
-| the same, deviation written with a rounded T0                | 1.4e-5  |                    |
-| the same, exact density rounded once (its low part dropped)  | 6.3e-6  |                    |
+| density sums exact only                                      | 1.2e-5  | 1.1e-5             |
+| single-rounding composition only                             | 1.2e-5  | 1.5e-5             |
+| compensated, deviation written with a rounded T0             | 1.4e-5  |                    |
+| compensated, exact density rounded once (low part dropped)   | 6.3e-6  |                    |
 
 The GPU's two FP32 forms measure u 1.4e-5 to 2.2e-5 (plain) and 3.5e-6 to
 4.6e-6 (compensated) on the same cases.  So the storage is not the limit;
 plain FP32 arithmetic is, through the density sums and the composition
-f*_i = w_i rho (1 + D_i) + (1 - 1/tau) f'_i; with both exact and the
-deviation D_i written with constants exact in binary, FP32 meets the
+f*_i = w_i rho (1 + D_i) + (1 - 1/tau) f'_i; only with both exact, and the
+deviation D_i written with constants exact in binary, does FP32 meet the
 contract.  Correctly rounded FP32 weights sum to 1 + 2^-27 and create that
 fraction of mass every step unless the rest population closes the mass.
+
+The emulated runs are independent: a module fixture runs them in spawned
+worker processes while this process steps the oracle.
 """
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
+
 import numpy as np
 import pytest
 
 import oracle
-from paper_1601_00918_gb300 import workloads as wl
 
 import precision_emulation as em
 
 pytestmark = pytest.mark.slow
 
 G = -1.79
-N, STEPS = 128, 1000
+STEPS = 1000
 # the two FP32 forms of the CUDA library, as emulation options
 PLAIN = dict(weight_kind="sum_to_one", rest="by_mass")
 COMPENSATED = dict(density="exact", compose="single_rounding", weight_kind="sum_to_one", rest="by_mass")
-CHANNEL = dict(tau=(1.0, 0.9), rho_wall=(0.3, 0.1), g=(2e-5, 0.0))
+# name -> (case, steps, options)
+JOBS = {
+    "storage_only": ("droplet", STEPS, dict(work=np.float64)),
+    "nearest_weights": ("droplet", STEPS, {}),
+    "plain": ("droplet", STEPS, PLAIN),
+    "compensated": ("droplet", STEPS, COMPENSATED),
+    "density_only": ("droplet", STEPS, dict(PLAIN, density="exact")),
+    "compose_only": ("droplet", STEPS, dict(PLAIN, compose="single_rounding")),
+    "rounded_t0": ("droplet", STEPS, dict(COMPENSATED, dev="rounded_t0")),
+    "density_low_part_dropped": ("droplet", STEPS, dict(COMPENSATED, density="exact_rounded")),
+    "bgk_plain": ("channel_bgk", STEPS, PLAIN),
+    "bgk_compensated": ("channel_bgk", STEPS, COMPENSATED),
+    "bgk_density_only": ("channel_bgk", STEPS, dict(PLAIN, density="exact")),
+    "bgk_compose_only": ("channel_bgk", STEPS, dict(PLAIN, compose="single_rounding")),
+    "reg_plain": ("channel_reg", STEPS, PLAIN),
+    "reg_compensated": ("channel_reg", STEPS, COMPENSATED),
+    "fp16_node": ("droplet", STEPS, dict(fmt="fp16", shift="node", weight_kind="sum_to_one")),
+    "fp16_destination": ("droplet", STEPS, dict(fmt="fp16", shift="destination", weight_kind="sum_to_one")),
+    "bf16_node": ("droplet", STEPS, dict(fmt="bf16", shift="node", weight_kind="sum_to_one")),
+    "fp16_constant": ("droplet", 200, dict(fmt="fp16", shift="constant", weight_kind="sum_to_one")),
+}
 
 
-def channel_geometry():
-    nx, ny = 300, 40
-    return wl.sinusoidal_channel(nx, ny, 12.0, 5.0, 100.0), wl.slug(nx, ny, 0.3 * nx, 0.7 * nx)
+def reference(case, steps):
+    """(rho_init, oracle Problem, rho, u) of the FP64 oracle after `steps`."""
+    mask, rho0, kw = em.case_inputs(case)
+    if mask is None:
+        P = oracle.Problem(np.zeros(rho0.shape[1:], np.uint8), tau=(1.0, 1.0), G=G)
+    else:
+        P = oracle.Problem(mask, G=G, periodic=(True, False), tau=kw["tau"], rho_wall=kw["rho_wall"], g=kw["g"],
+                           collision="regularized" if kw["regularized"] else "bgk")
+    rho, u, _ = P.fields(P.run(P.init(rho0), steps))
+    return rho0, P, rho, u
 
 
-@pytest.fixture(scope="module")
-def droplet():
-    rho0 = wl.droplet(N, N, 20.0, N / 2.0, N / 2.0)
-    P = oracle.Problem(wl.periodic_box(N, N), tau=(1.0, 1.0), G=G)
-    rho_r, u_r, _ = P.fields(P.run(P.init(rho0), STEPS))
-    return rho0, P, rho_r, u_r
-
-
-def errors(case, f):
+def errors(ref, f):
     """(rho, u) relative L-infinity errors and the per-species mass drift."""
-    rho0, P, rho_r, u_r = case
+    rho0, P, rho_r, u_r = ref
     rho, u, _ = P.fields(np.asarray(f, dtype=np.float64))
     fluid = P.mask == 0
     m0 = rho0[:, fluid].sum(axis=1)
@@ -66,22 +93,28 @@ def errors(case, f):
             np.max(np.abs(u - u_r)) / np.max(np.abs(u_r)), np.abs(m - m0) / m0)
 
 
+@pytest.fixture(scope="module")
+def results():
+    """name -> (rho error, u error, mass drift) of every job."""
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        futures = {name: ex.submit(em.run_case, (case, steps, G, opts))
+                   for name, (case, steps, opts) in JOBS.items()}
+        refs = {key: reference(*key) for key in {(case, steps) for case, steps, _ in JOBS.values()}}
+        return {name: errors(refs[JOBS[name][:2]], fut.result()) for name, fut in futures.items()}
+
+
 def test_the_emulation_in_fp64_is_the_oracle():
     """The emulation is a statement of the same step: in FP64 it gives the
     oracle's state to rounding on the droplet (100 steps) and on the walled
     channel with wall potentials, body force and mixed tau, plain BGK and
-    regularised (50 steps)."""
-    rho0 = wl.droplet(N, N, 20.0, N / 2.0, N / 2.0)
-    P = oracle.Problem(wl.periodic_box(N, N), tau=(1.0, 1.0), G=G)
-    f = em.run(rho0, 100, G, store=np.float64, work=np.float64)
-    np.testing.assert_allclose(f, P.run(P.init(rho0), 100), rtol=0, atol=1e-13)
-    mask, rho = channel_geometry()
-    for collision in ("bgk", "regularized"):
-        P = oracle.Problem(mask, G=G, periodic=(True, False), collision=collision, **CHANNEL)
+    regularised, with either closure of the rest population (50 steps)."""
+    for case, steps in (("droplet", 100), ("channel_bgk", 50), ("channel_reg", 50)):
+        mask, rho0, kw = em.case_inputs(case)
+        _, P, _, _ = reference(case, 0)
         for rest in ("equilibrium", "by_mass"):
-            f = em.run(rho, 50, G, store=np.float64, work=np.float64, mask=mask, rest=rest,
-                       regularized=collision == "regularized", **CHANNEL)
-            np.testing.assert_allclose(f, P.run(P.init(rho), 50), rtol=0, atol=1e-13)
+            f = em.run(rho0, steps, G, store=np.float64, work=np.float64, mask=mask, rest=rest, **kw)
+            np.testing.assert_allclose(f, P.run(P.init(rho0), steps), rtol=0, atol=1e-13)
 
 
 def test_fp32_weights():
@@ -92,61 +125,49 @@ def test_fp32_weights():
     assert em.weights(np.float32, "sum_to_one").astype(np.float64).sum() == 1.0
 
 
-def test_fp32_storage_alone_meets_the_contract(droplet):
-    err_rho, err_u, drift = errors(droplet, em.run(droplet[0], STEPS, G, work=np.float64))
-    assert err_rho < 1e-6 and err_u < 5e-6, (err_rho, err_u)
-    assert np.all(drift < 1e-6)
+def test_fp32_storage_alone_meets_the_contract(results):
+    err_rho, err_u, drift = results["storage_only"]
+    assert err_rho < 1e-6 and err_u < 5e-6 and np.all(drift < 1e-6), (err_rho, err_u, drift)
 
 
-def test_correctly_rounded_weights_create_mass(droplet):
+def test_correctly_rounded_weights_create_mass(results):
     """All stages in FP32 with correctly rounded weights and the rest
     population from its equilibrium: the mass grows by 2^-27 per step
     (7.5e-6 after 1000 steps), more than the contract allows."""
-    err_rho, _, drift = errors(droplet, em.run(droplet[0], STEPS, G))
+    err_rho, _, drift = results["nearest_weights"]
     assert np.all(np.abs(drift - STEPS * 2.0 ** -27) < 0.1 * STEPS * 2.0 ** -27), drift
     assert err_rho > 1e-5
 
 
-def test_plain_fp32_arithmetic_misses_the_velocity_bound(droplet):
-    """The plain FP32 form (weights summing to 1, the rest population closing
-    the mass): mass and rho within the contract, u not (1.7e-5)."""
-    err_rho, err_u, drift = errors(droplet, em.run(droplet[0], STEPS, G, **PLAIN))
-    assert np.all(drift < 1e-6) and err_rho < 5e-6, (drift, err_rho)
-    assert err_u > 1.2e-5, err_u
-
-
-def test_compensated_fp32_meets_the_contract(droplet):
-    """Density sums and w_i rho exact, each stored population rounded once,
-    everything else FP32: u 3.3e-6.  Written with a rounded T0 instead of
-    exact constants the deviation alone puts u back above the contract
-    (1.4e-5); rounding the exact density once, so that its low part never
-    reaches the stored populations, about doubles the error (6.3e-6)."""
-    err_rho, err_u, drift = errors(droplet, em.run(droplet[0], STEPS, G, **COMPENSATED))
-    assert err_rho < 1e-6 and err_u < 5e-6, (err_rho, err_u)
-    assert np.all(drift < 1e-6)
-    _, err_u_t0, _ = errors(droplet, em.run(droplet[0], STEPS, G, **dict(COMPENSATED, dev="rounded_t0")))
-    assert err_u_t0 > 1e-5, err_u_t0
-    _, err_u_hi, _ = errors(droplet, em.run(droplet[0], STEPS, G, **dict(COMPENSATED, density="exact_rounded")))
-    assert err_u_hi > 1.5 * err_u, (err_u_hi, err_u)
-
-
-@pytest.mark.parametrize("collision", ["bgk", "regularized"])
-def test_the_two_fp32_forms_on_the_channel(collision):
-    """The channel of the GPU parity tests after 1000 steps: the plain form
-    misses the velocity bound (BGK 2.0e-5, regularised 1.7e-5), the
-    compensated one meets it (7.7e-6, 6.3e-6); both keep rho and the mass
-    within the contract."""
-    mask, rho = channel_geometry()
-    P = oracle.Problem(mask, G=G, periodic=(True, False), collision=collision, **CHANNEL)
-    rho_r, u_r, _ = P.fields(P.run(P.init(rho), STEPS))
-    case = (rho, P, rho_r, u_r)
-    reg = collision == "regularized"
-    err_rho, err_u, drift = errors(case, em.run(rho, STEPS, G, mask=mask, regularized=reg, **CHANNEL, **PLAIN))
+@pytest.mark.parametrize("case", ["", "bgk_", "reg_"])
+def test_plain_fp32_misses_and_compensated_fp32_meets_the_velocity_bound(results, case):
+    """The two FP32 forms of the library on the droplet and on the channel
+    (BGK, regularised): both keep rho and the mass within the contract; u
+    exceeds 1e-5 with the plain form (1.7e-5, 2.0e-5, 1.7e-5) and stays
+    below it with the compensated one (3.3e-6, 7.7e-6, 6.3e-6)."""
+    err_rho, err_u, drift = results[case + "plain"]
     assert err_rho < 1e-5 and np.all(drift < 1e-6), (err_rho, drift)
     assert err_u > 1.2e-5, err_u
-    err_rho, err_u, drift = errors(case, em.run(rho, STEPS, G, mask=mask, regularized=reg, **CHANNEL,
-                                                **COMPENSATED))
+    err_rho, err_u, drift = results[case + "compensated"]
     assert err_rho < 5e-6 and err_u < 1e-5 and np.all(drift < 1e-6), (err_rho, err_u, drift)
+
+
+@pytest.mark.parametrize("case", ["", "bgk_"])
+def test_either_compensated_stage_alone_is_not_enough(results, case):
+    """Exact density sums alone (u 1.2e-5 droplet, 1.1e-5 channel) or the
+    single-rounding composition alone (1.2e-5, 1.5e-5) leave u above the
+    contract: the compensated form needs both."""
+    for stage in ("density_only", "compose_only"):
+        assert results[case + stage][1] > 1e-5, (case, stage, results[case + stage][1])
+
+
+def test_what_else_the_compensated_form_needs(results):
+    """Written with divisions by a rounded T0 instead of constants exact in
+    binary, the deviation alone puts u back above the contract (1.4e-5);
+    rounding the exact density once, so that its low part never reaches
+    the stored populations, about doubles the error (6.3e-6)."""
+    assert results["rounded_t0"][1] > 1e-5
+    assert results["density_low_part_dropped"][1] > 1.5 * results["compensated"][1]
 
 
 # ----------------------------------------------------------------------------
@@ -166,47 +187,30 @@ def test_16bit_rounding_is_the_formats_own():
     np.testing.assert_array_equal(em.to16(x, "bf16").view(np.uint32), refb.view(np.uint32))
 
 
-@pytest.fixture(scope="module")
-def shifted16(droplet):
-    """Errors (rho, u) of the droplet after 1000 steps with 16-bit storage,
-    FP32 arithmetic and weights summing to 1, for the node shift (FP16,
-    BF16) and the destination shift (FP16); the constant shift after 200
-    steps."""
-    rho0, P, _, _ = droplet
-    out = {}
-    for fmt, shift in (("fp16", "node"), ("fp16", "destination"), ("bf16", "node")):
-        out[fmt, shift] = errors(droplet, em.run16(rho0, STEPS, G, fmt=fmt, shift=shift,
-                                                   weight_kind="sum_to_one"))[:2]
-    rho_r, u_r, _ = P.fields(P.run(P.init(rho0), 200))
-    rho, u, _ = P.fields(em.run16(rho0, 200, G, fmt="fp16", shift="constant", weight_kind="sum_to_one"))
-    out["fp16", "constant"] = (np.max(np.abs(rho - rho_r)) / np.max(rho_r), np.max(np.abs(u - u_r)) / np.max(np.abs(u_r)))
-    return out
-
-
-def test_node_shifted_16bit_storage_within_the_gpu_bounds(shifted16):
+def test_node_shifted_16bit_storage_within_the_gpu_bounds(results):
     """The node shift the library stores (s_i = f*_i - w_i rhohat of the
     storing node): emulated FP16 rho 2.7e-4, u 3.4e-3 and BF16 rho 2.9e-3,
     u 2.8e-2, the errors the GPU shows on the same droplet (FP16 3.4e-4 /
     3.1e-3, BF16 3.2e-3 / 3e-2) and inside the bounds its 1000-step test
     holds it to."""
-    r, u = shifted16["fp16", "node"]
+    r, u, _ = results["fp16_node"]
     assert r < 5e-4 and u < 8e-3, (r, u)
-    r, u = shifted16["bf16", "node"]
+    r, u, _ = results["bf16_node"]
     assert r < 2.5e-2 and u < 0.12, (r, u)
 
 
-def test_destination_shift_is_no_better(shifted16):
+def test_destination_shift_is_no_better(results):
     """Shifting each stored part by the density of the node that pulls it
     next (which cancels the force-shifted first-order part at a static
     interface in the continuum) gives larger velocity errors (FP16 6.2e-3
     against 3.4e-3; BF16, not run here, 4.0e-2 against 2.8e-2): the
     interfaces are four nodes wide, far from the continuum limit."""
-    assert shifted16["fp16", "destination"][1] > 1.2 * shifted16["fp16", "node"][1]
+    assert results["fp16_destination"][1] > 1.2 * results["fp16_node"][1]
 
 
-def test_constant_shift_fails_at_the_interface(shifted16):
+def test_constant_shift_fails_at_the_interface(results):
     """A shift by each species' mean density leaves the minority species'
     stored part as large as the majority density across the interface:
     percent-level density errors within 200 steps (FP16 1.1 % on rho,
     11 % on u), far above the node shift's after 1000."""
-    assert shifted16["fp16", "constant"][0] > 30 * shifted16["fp16", "node"][0]
+    assert results["fp16_constant"][0] > 30 * results["fp16_node"][0]
