@@ -213,12 +213,44 @@ def _shifted_w(rh, shift):
     return np.stack([W[i] * _shift(rh, CX[i], CY[i]) for i in range(9)], axis=1)
 
 
+def _first_order_ref(rh, ux, uy):
+    """w_i rhohat (1 + 3 c_i . uhat), [2, 9, ny, nx] float32."""
+    return np.stack([W[i] * rh * (1.0 + 3.0 * (CX[i] * ux + CY[i] * uy)) for i in range(9)],
+                    axis=1).astype(np.float32)
+
+
+def _run16_first_order(rho_init, steps, G, fmt, work=np.float32, **kw):
+    """16-bit storage shifted by the storing node's first-order equilibrium,
+    s_i = f*_i - w_i rhohat (1 + 3 c_i . uhat^a), with rhohat and the
+    species' post-collision velocity uhat^a = j*^a / rho^a kept in 16 bits
+    too (six extra planes)."""
+    m = work
+    f = W[None, :, None, None] * np.asarray(rho_init, dtype=np.float64)[:, None]
+    rh = to16(rho_init, fmt)
+    ux = np.zeros_like(rh)
+    uy = np.zeros_like(rh)
+    s = to16(f - _first_order_ref(rh, ux, uy), fmt)
+    for _ in range(steps):
+        full = s.astype(m) + _first_order_ref(rh, ux, uy).astype(m)     # decoded at the storing node
+        out, rho = collide(pull(full).astype(m), G, work=m, **kw)
+        out = out.astype(m)
+        jx = (out[:, 1] - out[:, 3]) + ((out[:, 5] - out[:, 7]) + (out[:, 8] - out[:, 6]))
+        jy = (out[:, 2] - out[:, 4]) + ((out[:, 5] - out[:, 7]) + (out[:, 6] - out[:, 8]))
+        rh, ux, uy = to16(rho, fmt), to16(jx / rho, fmt), to16(jy / rho, fmt)
+        s = to16(out - _first_order_ref(rh, ux, uy), fmt)
+    return s.astype(np.float64) + _first_order_ref(rh, ux, uy)
+
+
 def run16(rho_init, steps, G, fmt="fp16", shift="node", work=np.float32, **kw):
     """`steps` steps with the populations stored in 16 bits as
     s_i = f*_i - w_i rhohat, rhohat the 16-bit density of the storing node
     ("node"), of the node that pulls the population next ("destination",
     which knows it as its own previous density), or each species' initial
-    mean ("constant"); rhohat is stored too.  Returns f* decoded (float64)."""
+    mean ("constant"); rhohat is stored too; "first_order" also removes the
+    storing node's first-order velocity term (see _run16_first_order).
+    Returns f* decoded (float64)."""
+    if shift == "first_order":
+        return _run16_first_order(rho_init, steps, G, fmt, work, **kw)
     rho_init = np.asarray(rho_init, dtype=np.float64)
     f = W[None, :, None, None] * rho_init[:, None]
     if shift == "constant":
