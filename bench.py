@@ -162,6 +162,16 @@ def dist_env():
     return ws, rank, local
 
 
+def workload_config(w, ws):
+    """The `config` of both arms' lines: the workload itself (how each arm
+    runs it goes in the arm's own keys)."""
+    ny, nx = w.mask.shape
+    return {"workload": w.name, "nodes": nx * ny, "fluid_nodes": int(np.count_nonzero(w.mask == 0)),
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "l2": "state >= 2 x %.2f GB ping-pong in every storage form > 129 MB L2: no flush needed"
+                  % (nx * ny * 18 * 2 / 1e9)}
+
+
 # ----------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # ----------------------------------------------------------------------------
@@ -283,7 +293,8 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * slowest / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": w.name, "precision": "fp64", "cols_sampled": cols, "processes": procs},
+            "config": workload_config(w, ws), "precision": "fp64",
+            "sample": {"cols_sampled": cols, "processes": procs},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -397,11 +408,7 @@ def native_arm(args):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[prec],
                 "data": "synthetic",
-                "config": {"workload": w.name, "nodes": nx * ny, "fluid_nodes": n_fluid,
-                           "precision": prec, "kernel": kinfo,
-                           "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                           "l2": "state 2 x %.2f GB ping-pong > 129 MB L2: no flush needed" %
-                                 (nx * ny * 18 * BYTES_PER_POP[prec] / 1e9)},
+                "config": workload_config(w, ws), "precision": prec, "kernel": kinfo,
                 "windows": {"n": nwin, "steps": sizes, "best": win_glups[-1],
                             "median": statistics.median(win_glups), "unit": UNIT},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -65,3 +65,25 @@ def test_oracle_on_several_host_cores():
     assert slowest > 0 and value == 2 * n_fluid * 2 / slowest / 1e9
     n, model = b.host_cores()
     assert n >= 1 and isinstance(model, str)
+
+
+def test_reference_line_has_the_native_config(monkeypatch, capsys):
+    """The reference arm prints its line on the native arm's `config` (the
+    workload; how each arm runs it goes in its own keys) with the contract's
+    keys; the oracle timing itself is replaced by a stub here."""
+    import argparse
+    b = load_bench()
+    w = b.workload()
+
+    class Sample:
+        cols = 64
+
+    monkeypatch.setattr(b, "oracle_sample_for", lambda w, s: Sample())
+    monkeypatch.setattr(b, "oracle_all_cores", lambda w, cols, warmup, steps, procs: (0.04, 2.5, 123))
+    assert b.reference_arm(argparse.Namespace(steps=4, warmup=3)) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["config"] == b.workload_config(w, 1)
+    assert line["impl"] == "reference" and line["metric"] == b.METRIC and line["unit"] == b.UNIT
+    assert line["higher_is_better"] is True and line["steps"] == 4 and line["warmup"] == 3
+    assert line["e2e"]["value"] == line["value"] and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["config"]["fluid_nodes"] == int((w.mask == 0).sum())
