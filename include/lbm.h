@@ -290,8 +290,9 @@ int lbm3d_load(lbm3d_t *h, const double *f);
 /* Free the handle and its device memory (after its stream's work); NULL is
  * ignored. */
 void lbm3d_destroy(lbm3d_t *h);
-/* Text of the last error of h, or of the calling thread's last
- * lbm3d_create when h is NULL. */
+/* Text of the last error of h, or, when h is NULL, of the calling thread's
+ * last 3-D call that failed without a handle (lbm3d_create, or a call given
+ * NULL). */
 const char *lbm3d_last_error(const lbm3d_t *h);
 
 /* Free the handle and the device memory it owns.  NULL is ignored. */
@@ -394,8 +395,9 @@ int lbm_critical_pressure_batch(lbm_batch_t *b, const double *g_lo, const double
 /* Free the batch and its device memory (after its stream's work); NULL is
  * ignored. */
 void lbm_batch_destroy(lbm_batch_t *b);
-/* Text of the last error of b, or of the calling thread's last
- * lbm_batch_create when b is NULL. */
+/* Text of the last error of b, or, when b is NULL, of the calling thread's
+ * last batch call that failed without a batch (lbm_batch_create, or a call
+ * given NULL). */
 const char *lbm_batch_last_error(const lbm_batch_t *b);
 
 /* ---------------------------------------------------------------------------
