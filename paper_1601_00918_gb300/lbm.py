@@ -312,8 +312,12 @@ def lbm_save(h, nx, ny):
     return f
 
 
-def lbm_load(h, f):
+def lbm_load(h, f, nx, ny):
+    """Load populations f [2, 9, ny, nx] (the C call reads exactly that many
+    values, so the shape is checked here)."""
     f = np.ascontiguousarray(f, dtype=np.float64)
+    if f.shape != (2, 9, ny, nx):
+        raise ValueError(f"lbm_load: expected populations of shape {(2, 9, ny, nx)}, got {f.shape}")
     _check(library().lbm_load(h, _dptr(f)), h)
 
 
@@ -394,7 +398,7 @@ class Simulation:
         return lbm_save(self.h, self.nx, self.ny)
 
     def load(self, f):
-        lbm_load(self.h, f)
+        lbm_load(self.h, f, self.nx, self.ny)
 
     def close(self):
         if getattr(self, "h", None):
@@ -432,7 +436,8 @@ def lbm_batch_create(instances, precision="fp32", eq_order=3, stream=None):
         mask = np.ascontiguousarray(d["mask"], dtype=np.uint8)
         rho = np.ascontiguousarray(d["rho_init"], dtype=np.float64)
         ny, nx = mask.shape
-        assert rho.shape == (2, ny, nx)
+        if rho.shape != (2, ny, nx):
+            raise ValueError(f"instance {k}: rho_init must have shape {(2, ny, nx)}, got {rho.shape}")
         keep += [mask, rho]
         per = d.get("periodic", (True, False))
         arr[k] = Instance(nx, ny, int(per[0]), int(per[1]), (ctypes.c_double * 2)(*d.get("tau", (1.0, 1.0))),
@@ -641,7 +646,7 @@ def lbm_channel_geometry(spec):
 
 
 def lbm_wetting_calibrate(r_values, steps=20000, precision="fp32", stream=None):
-    r = np.ascontiguousarray(r_values, dtype=np.float64)
+    r = np.ascontiguousarray(r_values, dtype=np.float64).ravel()
     theta = np.empty_like(r)
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     _ccheck(library().lbm_wetting_calibrate(_dptr(r), len(r), int(steps), prec,
@@ -672,19 +677,26 @@ def lbm_planar_critical_balance_hysteresis(theta_front, theta_rear, area, h0, am
     return out.value
 
 
+def _densities(rho, name):
+    """rho as a C-contiguous float64 [2, ny, nx] array, and (ny, nx): the C
+    calls read both species' planes, so the shape is checked here."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    if rho.ndim != 3 or rho.shape[0] != 2:
+        raise ValueError(f"{name}: densities must have shape (2, ny, nx), got {rho.shape}")
+    return rho, rho.shape[1], rho.shape[2]
+
+
 def lbm_meniscus_angles(rho, h0, amp, lam):
     """{theta_rear, theta_front, x_rear, x_front, r_rear, r_front} of a slug
     in the planar sinusoidal channel (lbm_meniscus_angles)."""
-    rho = np.ascontiguousarray(rho, dtype=np.float64)
-    _, ny, nx = rho.shape
+    rho, ny, nx = _densities(rho, "lbm_meniscus_angles")
     out = np.zeros(6)
     _ccheck(library().lbm_meniscus_angles(_dptr(rho), nx, ny, float(h0), float(amp), float(lam), _dptr(out)))
     return dict(zip(("theta_rear", "theta_front", "x_rear", "x_front", "r_rear", "r_front"), out.tolist()))
 
 
 def lbm_contact_angle(rho, y_lo, y_hi, right=True):
-    rho = np.ascontiguousarray(rho, dtype=np.float64)
-    _, ny, nx = rho.shape
+    rho, ny, nx = _densities(rho, "lbm_contact_angle")
     out = ctypes.c_double()
     _ccheck(library().lbm_contact_angle(_dptr(rho), nx, ny, int(y_lo), int(y_hi), int(bool(right)),
                                         ctypes.byref(out)))
@@ -693,18 +705,20 @@ def lbm_contact_angle(rho, y_lo, y_hi, right=True):
 
 def lbm_slug_area(rho, mask):
     """(oil-rich nodes, the paper's bulk + 90 % interface count) of a slug."""
-    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    rho, ny, nx = _densities(rho, "lbm_slug_area")
     mask = np.ascontiguousarray(mask, dtype=np.uint8)
-    _, ny, nx = rho.shape
-    assert mask.shape == (ny, nx)
+    if mask.shape != (ny, nx):
+        raise ValueError(f"lbm_slug_area: mask must have shape {(ny, nx)}, got {mask.shape}")
     out = (ctypes.c_double * 2)()
     _ccheck(library().lbm_slug_area(_dptr(rho), mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), nx, ny, out))
     return out[0], out[1]
 
 
 def lbm_wall_potentials(r, theta, theta_deg):
-    r = np.ascontiguousarray(r, dtype=np.float64)
-    th = np.ascontiguousarray(theta, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64).ravel()
+    th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+    if th.shape != r.shape:
+        raise ValueError(f"lbm_wall_potentials: {len(r)} potentials but {len(th)} angles")
     out = (ctypes.c_double * 2)()
     _ccheck(library().lbm_wall_potentials(_dptr(r), _dptr(th), len(r), float(theta_deg), out))
     return (out[0], out[1])
@@ -767,7 +781,8 @@ class Simulation3:
         mask = np.ascontiguousarray(mask, dtype=np.uint8)
         rho = np.ascontiguousarray(rho_init, dtype=np.float64)
         self.nz, self.ny, self.nx = mask.shape
-        assert rho.shape == (2,) + mask.shape
+        if rho.shape != (2,) + mask.shape:
+            raise ValueError(f"rho_init must have shape {(2,) + mask.shape}, got {rho.shape}")
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         with torch.cuda.device(device):
             stream = torch.cuda.current_stream().cuda_stream
@@ -803,6 +818,9 @@ class Simulation3:
 
     def load(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64)
+        if f.shape != (2, 19, self.nz, self.ny, self.nx):
+            raise ValueError(f"load: expected populations of shape {(2, 19, self.nz, self.ny, self.nx)}, "
+                             f"got {f.shape}")
         _check3(library().lbm3d_load(self.h, _dptr(f)), self.h)
 
     def close(self):

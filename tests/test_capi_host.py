@@ -311,3 +311,24 @@ def test_channel_spec_defaults_and_limits(lib):
     assert _shape(lib, slug_len_over_lambda=3.0)[0] == lbm.LBM_OK
     assert _shape(lib, n_slugs=2, slug_len_over_lambda=1.75)[0] == lbm.LBM_OK
     assert _shape(lib, lam=128, n_periods=6, amp_ratio=0.2)[1:] == (768, 2 * 29 + 2)
+
+
+def test_binding_checks_host_array_shapes(lib):
+    """The binding refuses host arrays whose shape does not match what the C
+    call will read (it reads both species' planes, or n table entries),
+    instead of letting the call read past their end."""
+    good = np.ones((2, 12, 20))
+    with pytest.raises(ValueError):
+        lbm.lbm_contact_angle(np.ones((1, 12, 20)), 1, 10)
+    with pytest.raises(ValueError):
+        lbm.lbm_meniscus_angles(np.ones((12, 20)), 4.0, 1.0, 20.0)
+    with pytest.raises(ValueError):
+        lbm.lbm_slug_area(good, np.zeros((12, 21), np.uint8))
+    with pytest.raises(ValueError):
+        lbm.lbm_wall_potentials(np.array([-0.4, 0.0, 0.4]), np.array([135.0, 90.0]), 60.0)
+    assert lbm.lbm_slug_area(good * np.array([1.0, 0.0])[:, None, None], np.zeros((12, 20), np.uint8))[0] == 240
+    inst = dict(mask=wl.periodic_box(8, 6), rho_init=np.ones((2, 6, 9)))
+    with pytest.raises(ValueError):
+        lbm.lbm_batch_create([inst])
+    with pytest.raises(ValueError):
+        lbm.lbm_load(None, np.zeros((2, 9, 6, 7)), 8, 6)
