@@ -464,8 +464,17 @@ def lbm_batch_observables(b, n, check=True):
     return [o.as_dict() for o in out]
 
 
-def lbm_batch_set_body_force(b, gx):
-    gx = np.ascontiguousarray(gx, dtype=np.float64)
+def _per_instance(values, n, name):
+    """values as a C-contiguous float64 array of exactly n entries (the C
+    calls read, and write results for, every instance of the batch)."""
+    v = np.ascontiguousarray(values, dtype=np.float64).ravel()
+    if n is not None and v.shape != (n,):
+        raise ValueError(f"{name}: expected {n} values, one per instance, got {v.shape[0]}")
+    return v
+
+
+def lbm_batch_set_body_force(b, gx, n=None):
+    gx = _per_instance(gx, n, "lbm_batch_set_body_force")
     _bcheck(library().lbm_batch_set_body_force(b, _dptr(gx)), b)
 
 
@@ -482,9 +491,9 @@ def lbm_batch_kernel_info(b) -> dict:
 
 
 def lbm_critical_pressure_batch(b, g_lo, g_hi, rel_bracket=0.02, t_eq=1000, t_obs=2000, max_probes=24,
-                                check_bracket=True, timeout_s=0.0, check=True):
-    g_lo = np.ascontiguousarray(g_lo, dtype=np.float64)
-    g_hi = np.ascontiguousarray(g_hi, dtype=np.float64)
+                                check_bracket=True, timeout_s=0.0, check=True, n=None):
+    g_lo = _per_instance(g_lo, n, "lbm_critical_pressure_batch")
+    g_hi = _per_instance(g_hi, len(g_lo), "lbm_critical_pressure_batch")
     n = len(g_lo)
     out = (CritResult * n)()
     o = BisectOpts(float(rel_bracket), int(t_eq), int(t_obs), int(max_probes), int(bool(check_bracket)),
@@ -520,7 +529,7 @@ class Batch:
         return lbm_batch_observables(self.h, self.n, check)
 
     def set_body_force(self, gx):
-        lbm_batch_set_body_force(self.h, gx)
+        lbm_batch_set_body_force(self.h, gx, self.n)
 
     def save(self, i):
         ny, nx = self.shapes[i]
@@ -530,7 +539,7 @@ class Batch:
         return lbm_batch_kernel_info(self.h)
 
     def critical_pressure(self, g_lo, g_hi, **opts):
-        return lbm_critical_pressure_batch(self.h, g_lo, g_hi, **opts)
+        return lbm_critical_pressure_batch(self.h, g_lo, g_hi, n=self.n, **opts)
 
     def close(self):
         if getattr(self, "h", None):

@@ -332,3 +332,9 @@ def test_binding_checks_host_array_shapes(lib):
         lbm.lbm_batch_create([inst])
     with pytest.raises(ValueError):
         lbm.lbm_load(None, np.zeros((2, 9, 6, 7)), 8, 6)
+    with pytest.raises(ValueError):
+        lbm.lbm_critical_pressure_batch(None, [1e-5, 2e-5], [4e-5, 8e-5], n=3)
+    with pytest.raises(ValueError):
+        lbm.lbm_critical_pressure_batch(None, [1e-5, 2e-5], [4e-5])
+    with pytest.raises(ValueError):
+        lbm.lbm_batch_set_body_force(None, [1e-5], n=2)
