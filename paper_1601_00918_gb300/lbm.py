@@ -568,12 +568,32 @@ def _mcheck(rc):
         raise LbmError(rc, (library().lbm_mlp_last_error() or b"").decode())
 
 
+def _mlp_params(p):
+    p = np.ascontiguousarray(p, dtype=np.float32).ravel()
+    if p.shape != (MLP_PARAMS,):
+        raise ValueError(f"surrogate: expected {MLP_PARAMS} parameters, got {p.shape[0]}")
+    return p
+
+
+def _mlp_data(x, y=None):
+    """Features x [B, 5] and targets y [B] as the C calls read them."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if x.ndim != 2 or x.shape[1] != 5 or x.shape[0] < 1:
+        raise ValueError(f"surrogate: features must have shape (B, 5), B >= 1, got {x.shape}")
+    if y is None:
+        return x
+    y = np.ascontiguousarray(y, dtype=np.float32).ravel()
+    if y.shape != (x.shape[0],):
+        raise ValueError(f"surrogate: {x.shape[0]} feature rows but {y.shape[0]} targets")
+    return x, y
+
+
 class Surrogate:
     """The 5 -> 128 -> 128 -> 128 -> 2 network on the device (C ABI lbm_mlp_*)."""
 
     def __init__(self, params=None, seed=0, stream=None):
         h = ctypes.c_void_p()
-        p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+        p = None if params is None else _mlp_params(params)
         _mcheck(library().lbm_mlp_create(_fptr(p) if p is not None else None, int(seed),
                                          ctypes.c_void_p(stream) if stream else None, ctypes.byref(h)))
         self.h = h.value
@@ -584,18 +604,17 @@ class Surrogate:
         return out
 
     def set_params(self, p):
-        p = np.ascontiguousarray(p, dtype=np.float32)
+        p = _mlp_params(p)
         _mcheck(library().lbm_mlp_params(self.h, None, _fptr(p)))
 
     def forward(self, x):
-        x = np.ascontiguousarray(x, dtype=np.float32)
+        x = _mlp_data(x)
         out = np.empty((x.shape[0], 2), dtype=np.float32)
         _mcheck(library().lbm_mlp_forward(self.h, _fptr(x), x.shape[0], _fptr(out)))
         return out
 
     def loss_grad(self, x, y):
-        x = np.ascontiguousarray(x, dtype=np.float32)
-        y = np.ascontiguousarray(y, dtype=np.float32)
+        x, y = _mlp_data(x, y)
         loss = np.zeros(1, dtype=np.float32)
         g = np.empty(MLP_PARAMS, dtype=np.float32)
         _mcheck(library().lbm_mlp_loss_grad(self.h, _fptr(x), _fptr(y), x.shape[0], _fptr(loss), _fptr(g)))
@@ -605,8 +624,7 @@ class Surrogate:
         _mcheck(library().lbm_mlp_adam(self.h, float(lr)))
 
     def train(self, x, y, epochs, batch=256, lr=1e-3, seed=0):
-        x = np.ascontiguousarray(x, dtype=np.float32)
-        y = np.ascontiguousarray(y, dtype=np.float32)
+        x, y = _mlp_data(x, y)
         loss = np.zeros(1, dtype=np.float32)
         _mcheck(library().lbm_mlp_train(self.h, _fptr(x), _fptr(y), x.shape[0], int(epochs), int(batch),
                                         float(lr), int(seed), _fptr(loss)))

@@ -338,3 +338,21 @@ def test_binding_checks_host_array_shapes(lib):
         lbm.lbm_critical_pressure_batch(None, [1e-5, 2e-5], [4e-5])
     with pytest.raises(ValueError):
         lbm.lbm_batch_set_body_force(None, [1e-5], n=2)
+
+
+def test_surrogate_binding_checks_shapes(lib):
+    """Parameter vectors, features and targets are checked against what the
+    lbm_mlp_* calls read before any device work (a handle-less object is
+    enough to reach the checks)."""
+    s = object.__new__(lbm.Surrogate)
+    s.h = None
+    with pytest.raises(ValueError):
+        s.set_params(np.zeros(lbm.MLP_PARAMS - 1, np.float32))
+    with pytest.raises(ValueError):
+        s.forward(np.zeros((4, 4), np.float32))
+    with pytest.raises(ValueError):
+        s.loss_grad(np.zeros((4, 5), np.float32), np.zeros(3, np.float32))
+    with pytest.raises(ValueError):
+        s.train(np.zeros((0, 5), np.float32), np.zeros(0, np.float32), 1)
+    with pytest.raises(ValueError):
+        lbm.Surrogate(params=np.zeros(10, np.float32))
