@@ -356,3 +356,28 @@ def test_surrogate_binding_checks_shapes(lib):
         s.train(np.zeros((0, 5), np.float32), np.zeros(0, np.float32), 1)
     with pytest.raises(ValueError):
         lbm.Surrogate(params=np.zeros(10, np.float32))
+
+
+def test_sinusoidal_tube_cross_sections():
+    """The paper's tube (Section 3.4) as the input module builds it: every
+    cross section is a lattice disc about the centre line, symmetric under
+    the swap and the reflections of y and z, whose node count N lies within
+    the bounds a disc of radius r = h(x) = h0 - A cos(2 pi x / lam) fixes,
+    pi (r - sqrt(2)/2)^2 <= N <= pi (r + sqrt(2)/2)^2 (the unit squares of
+    its nodes lie inside the disc of radius r + sqrt(2)/2 and cover the one
+    of radius r - sqrt(2)/2); the narrowest section is at x = 0 and the
+    widest at lam / 2; the mask repeats with the wavelength; the boundary
+    planes are solid."""
+    nx, n, h0, amp, lam = 96, 22, 8.0, 3.0, 48.0
+    m = wl.sinusoidal_tube(nx, n, h0, amp, lam)
+    assert m.shape == (n, n, nx)
+    fluid = (m == 0)
+    counts = fluid.sum(axis=(0, 1))
+    for x in range(nx):
+        sl = fluid[:, :, x]
+        assert np.array_equal(sl, sl.T) and np.array_equal(sl, sl[::-1]) and np.array_equal(sl, sl[:, ::-1])
+        r = h0 - amp * np.cos(2 * np.pi * x / lam)
+        assert np.pi * (r - 0.5 ** 0.5) ** 2 <= counts[x] <= np.pi * (r + 0.5 ** 0.5) ** 2, (x, counts[x], r)
+    assert counts[0] == counts.min() and counts[int(lam) // 2] == counts.max()
+    assert np.array_equal(m[:, :, :int(lam)], m[:, :, int(lam):2 * int(lam)])
+    assert m[0].all() and m[-1].all() and m[:, 0].all() and m[:, -1].all()
