@@ -381,3 +381,19 @@ def test_sinusoidal_tube_cross_sections():
     assert counts[0] == counts.min() and counts[int(lam) // 2] == counts.max()
     assert np.array_equal(m[:, :, :int(lam)], m[:, :, int(lam):2 * int(lam)])
     assert m[0].all() and m[-1].all() and m[:, 0].all() and m[:, -1].all()
+
+
+def test_layered_channel_rows():
+    """The two-component Hagen-Poiseuille set-up (Section 3.2): a straight
+    channel of 64 fluid rows between two solid rows, 256 long; rows 1-12 and
+    53-64 hold the wetting species, rows 13-52 the core species (sharp
+    interfaces), with either species in the core."""
+    m = wl.straight_channel(256, 64)
+    assert m.shape == (66, 256) and m[0].all() and m[65].all() and not m[1:65].any()
+    for core in (0, 1):
+        r = wl.layered_channel(256, 64, 12, core_species=core)
+        assert r.shape == (2, 66, 256)
+        rows_core = np.nonzero(r[core, :, 0] == r[core].max())[0]
+        assert rows_core.min() == 13 and rows_core.max() == 52 and len(rows_core) == 40
+        assert np.all(r[1 - core, 1:13] == r[1 - core].max()) and np.all(r[1 - core, 53:65] == r[1 - core].max())
+        np.testing.assert_allclose(r.sum(axis=0), r.sum(axis=0)[0, 0])      # total density uniform
