@@ -219,10 +219,16 @@ def test_sinusoidal_channel_rows():
 
 
 def test_droplet_and_slug_profiles():
+    """Section 3.1's droplet: 1.0 inside, 0.03 outside, the total 1.03
+    everywhere, the interface a tanh of width 2 centred on the radius (half
+    way at r = R, a fraction (1 - tanh 1) / 2 of the jump one width out);
+    a slug fills the channel between its ends."""
     r = wl.droplet(64, 64, 10.0, 32.0, 32.0)
     assert r[0, 32, 32] == pytest.approx(1.0, abs=1e-3)
     assert r[0, 0, 0] == pytest.approx(0.03, abs=1e-6)
     np.testing.assert_allclose(r.sum(axis=0), 1.03)
+    assert r[0, 32, 42] == pytest.approx(0.515, abs=1e-12)                  # r = R
+    assert r[0, 32, 44] == pytest.approx(0.03 + 0.97 * (1 - np.tanh(1.0)) / 2, abs=1e-12)   # r = R + 2
     s = wl.slug(100, 10, 30.0, 70.0)
     assert s[0, 5, 50] == pytest.approx(1.0, abs=1e-6)
     assert s[1, 5, 5] == pytest.approx(1.0, abs=1e-6)

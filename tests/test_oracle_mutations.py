@@ -9,8 +9,10 @@ to fail.  The D3Q19 oracle (oracle/lbm3d_oracle.c) is treated the same way
 with the pins of tests/test_oracle_d3q19.py, and the Python modules of the
 oracle (the planar critical force and the contact angle, the closed forms
 and fits, the bisection protocol, the surrogate's FP64 reference) by
-replacing their functions with those of a mutated copy of the source.
-Control cases compile the unchanged C sources the same way and check that
+replacing their functions with those of a mutated copy of the source.  The
+input module (paper_1601_00918_gb300/workloads.py) feeds both the oracle and
+the CUDA path, so a mistake in it would pass every parity test: its own pins
+are tested the same way.  Control cases compile the unchanged C sources the same way and check that
 every pin of their battery passes, so a failure under a mutation is the
 mistake's doing and not the harness's.
 
@@ -22,6 +24,7 @@ import importlib
 import importlib.util
 import os
 import subprocess
+import sys
 import types
 
 import pytest
@@ -357,14 +360,16 @@ PY_MUTATIONS = [
 
 
 def _mutate_python(monkeypatch, modname, old, new):
-    """Replace every function of oracle.<modname> by its counterpart from a
-    copy of the module's source with `old` replaced by `new`."""
-    real = importlib.import_module(f"oracle.{modname}")
+    """Replace every function of oracle.<modname> (or of the module of that
+    dotted name) by its counterpart from a copy of the module's source with
+    `old` replaced by `new`."""
+    real = importlib.import_module(modname if "." in modname else f"oracle.{modname}")
     with open(real.__file__) as fh:
         src = fh.read()
     assert src.count(old) == 1, f"{modname}: the text to replace must occur exactly once"
-    mut = types.ModuleType(f"oracle.{modname}_mutated")
+    mut = types.ModuleType(f"{real.__name__}_mutated")
     mut.__file__ = real.__file__
+    monkeypatch.setitem(sys.modules, mut.__name__, mut)      # dataclasses look their module up
     exec(compile(src.replace(old, new), real.__file__, "exec"), mut.__dict__)
     for name, value in vars(mut).items():
         if callable(value) and getattr(value, "__module__", None) == mut.__name__:
@@ -382,4 +387,65 @@ def test_a_planted_mistake_in_the_python_oracle_fails_a_pin(monkeypatch, modname
         except Exception:
             failed.append(name)
             break
+    assert failed, f"no pin caught: {what}"
+
+
+# ----------------------------------------------------------------------------
+# the input module (workloads.py): it feeds both the oracle and the CUDA path,
+# so a mistake in it would pass every parity test; its own pins must fail
+# ----------------------------------------------------------------------------
+CAPI = _pins("test_capi_host")
+WETTING = _pins("test_wetting_host")
+
+
+def _input_battery():
+    c, w, p = CAPI, WETTING, PINS
+    return [
+        ("channel rows", c.test_sinusoidal_channel_rows),
+        ("droplet and slug profiles", c.test_droplet_and_slug_profiles),
+        ("layered channel rows", c.test_layered_channel_rows),
+        ("tube cross sections", c.test_sinusoidal_tube_cross_sections),
+        ("channel geometry = library", lambda: [w.test_channel_geometry_is_the_input_module_channel(*a) for a in
+                                                ((32, 0.2, 1.0, 4), (48, 0.37, 1.3, 3))]),
+        ("flat-interface coexistence", p.test_flat_interface_coexistence_at_the_chosen_g),
+    ]
+
+
+WL = "paper_1601_00918_gb300.workloads"
+INPUT_MUTATIONS = [
+    ("half_width_sign", "h(x) = h0 + A cos: bulges where the necks are",
+     "return h0 - amp * np.cos(2.0 * np.pi", "return h0 + amp * np.cos(2.0 * np.pi"),
+    ("channel_centre", "the channel centred on ny / 2 instead of (ny - 1) / 2",
+     "        yc = (ny - 1) / 2.0\n", "        yc = ny / 2.0\n"),
+    ("tube_centre", "the tube's axis off the middle of its cross section",
+     "    c = (n_cross - 1) / 2.0\n", "    c = n_cross / 2.0\n"),
+    ("layered_rows", "the wetting layers one row short",
+     "core = (y >= 1 + outer) & (y <= width - outer)", "core = (y >= outer) & (y <= width - outer)"),
+    ("droplet_inside_out", "species o outside the droplet instead of inside",
+     "s = _step(radius - r)", "s = _step(r - radius)"),
+    ("tanh_width", "interfaces of width 1 instead of 2",
+     "np.tanh(np.asarray(d, dtype=np.float64) / 2.0)", "np.tanh(np.asarray(d, dtype=np.float64))"),
+    ("slug_front", "the slug's front end reversed",
+     "s = _step(x - x_rear) - _step(x - x_front)\n    ro = rho_lo + (rho_hi - rho_lo) * s\n    return np.stack([ro, rho_hi + rho_lo - ro])\n\n\ndef uniform",
+     "s = _step(x - x_rear) - _step(x_front - x)\n    ro = rho_lo + (rho_hi - rho_lo) * s\n    return np.stack([ro, rho_hi + rho_lo - ro])\n\n\ndef uniform"),
+    ("first_slug_neck", "the first slug centred one neck too far",
+     "first = float(spec.lam * (spec.n_periods // (2 * k)))", "first = float(spec.lam * (spec.n_periods // k))"),
+    ("flat_band", "the oil band of the flat interface half as wide",
+     "s = _step(x - nx / 4.0) - _step(x - 3.0 * nx / 4.0)", "s = _step(x - nx / 4.0) - _step(x - nx / 2.0)"),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mid,what,old,new", INPUT_MUTATIONS, ids=[m[0] for m in INPUT_MUTATIONS])
+def test_a_planted_mistake_in_the_input_module_fails_a_pin(monkeypatch, mid, what, old, new):
+    _mutate_python(monkeypatch, WL, old, new)
+    PINS._flat_interface.cache_clear()
+    failed = []
+    for name, call in _input_battery():
+        try:
+            call()
+        except Exception:
+            failed.append(name)
+            break
+    PINS._flat_interface.cache_clear()
     assert failed, f"no pin caught: {what}"
