@@ -95,13 +95,19 @@ def layered(nx=256, width=64, outer=12, core=0):
 @pytest.mark.parametrize("core", [0, 1])
 def test_layered_poiseuille_profile(lbm, tau_core, tau_wall, core, bound):
     """Steady flow of a core fluid (species `core`) between wall layers of the
-    other species: the x-averaged velocity matches the analytic layered
-    profile (walls half a node outside the last fluid rows, interface at
-    |y| = 20, viscosities mu = rho nu_mix of each layer's bulk) to `bound` in
-    relative L2 (measured: 3.5 % at ratio 1, the diffuse interfaces and the
-    halfway-bounce-back slip).  Viscosity ratios 1, 2, 2.9 and 5.7; ratios 5
-    and 10 at tau = 0.6 make this plain-BGK model with G = -1.79 lose
-    positivity (the regularised collision covers them, tested separately)."""
+    other species: the x-averaged velocity matches the sharp-interface
+    layered profile (walls half a node outside the last fluid rows,
+    interface at |y| = 20, viscosities mu = rho nu_mix of each layer's bulk)
+    to `bound` in relative L2, the same context bound the oracle is held to
+    (it gives 3.5 %, 1.8 % and 2.4 %).  The derived check of this flow is the
+    oracle's (tests/test_oracle_pins.py: the profile against the momentum
+    balance over its own diffuse density profile, to 1e-3 of the centre
+    velocity in the bulk layers and within the second-order Taylor remainder
+    across the interfaces), and the FP64 parity tests tie this step to that
+    oracle; what is left here is the gap between a diffuse interface and the
+    sharp closed form.  Viscosity ratios 1, 2, 2.9 and 5.7; ratios 5 and 10
+    at tau = 0.6 make this plain-BGK model with G = -1.79 lose positivity
+    (the regularised collision covers them, tested separately)."""
     mask, rho = layered(core=core)
     tau = [0.0, 0.0]
     tau[core], tau[1 - core] = tau_core, tau_wall
