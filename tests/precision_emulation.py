@@ -219,7 +219,15 @@ def _first_order_ref(rh, ux, uy):
                     axis=1).astype(np.float32)
 
 
-def _run16_first_order(rho_init, steps, G, fmt, work=np.float32, **kw):
+def _solid_zero(mask, *arrays):
+    """Zero solid nodes (the last two axes) of each array in place."""
+    if mask is not None:
+        solid = mask != 0
+        for a in arrays:
+            a[..., solid] = 0
+
+
+def _run16_first_order(rho_init, steps, G, fmt, work=np.float32, mask=None, **kw):
     """16-bit storage shifted by the storing node's first-order equilibrium,
     s_i = f*_i - w_i rhohat (1 + 3 c_i . uhat^a), with rhohat and the
     species' post-collision velocity uhat^a = j*^a / rho^a kept in 16 bits
@@ -229,48 +237,56 @@ def _run16_first_order(rho_init, steps, G, fmt, work=np.float32, **kw):
     rh = to16(rho_init, fmt)
     ux = np.zeros_like(rh)
     uy = np.zeros_like(rh)
+    _solid_zero(mask, f, rh)
     s = to16(f - _first_order_ref(rh, ux, uy), fmt)
     for _ in range(steps):
         full = s.astype(m) + _first_order_ref(rh, ux, uy).astype(m)     # decoded at the storing node
-        out, rho = collide(pull(full).astype(m), G, work=m, **kw)
-        out = out.astype(m)
-        jx = (out[:, 1] - out[:, 3]) + ((out[:, 5] - out[:, 7]) + (out[:, 8] - out[:, 6]))
-        jy = (out[:, 2] - out[:, 4]) + ((out[:, 5] - out[:, 7]) + (out[:, 6] - out[:, 8]))
-        rh, ux, uy = to16(rho, fmt), to16(jx / rho, fmt), to16(jy / rho, fmt)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            out, rho = collide(pull(full, mask).astype(m), G, work=m, mask=mask, **kw)
+            out = out.astype(m)
+            jx = (out[:, 1] - out[:, 3]) + ((out[:, 5] - out[:, 7]) + (out[:, 8] - out[:, 6]))
+            jy = (out[:, 2] - out[:, 4]) + ((out[:, 5] - out[:, 7]) + (out[:, 6] - out[:, 8]))
+            ux, uy = jx / rho, jy / rho
+        _solid_zero(mask, out, rho, ux, uy)
+        rh, ux, uy = to16(rho, fmt), to16(ux, fmt), to16(uy, fmt)
         s = to16(out - _first_order_ref(rh, ux, uy), fmt)
     return s.astype(np.float64) + _first_order_ref(rh, ux, uy)
 
 
-def run16(rho_init, steps, G, fmt="fp16", shift="node", work=np.float32, **kw):
+def run16(rho_init, steps, G, fmt="fp16", shift="node", work=np.float32, mask=None, **kw):
     """`steps` steps with the populations stored in 16 bits as
     s_i = f*_i - w_i rhohat, rhohat the 16-bit density of the storing node
     ("node"), of the node that pulls the population next ("destination",
     which knows it as its own previous density), or each species' initial
     mean ("constant"); rhohat is stored too; "first_order" also removes the
     storing node's first-order velocity term (see _run16_first_order).
+    Each stored part is decoded with the reference it was stored with (the
+    pulling node adds the same one), then pulled; mask as in run.
     Returns f* decoded (float64)."""
     if shift == "first_order":
-        return _run16_first_order(rho_init, steps, G, fmt, work, **kw)
+        return _run16_first_order(rho_init, steps, G, fmt, work, mask=mask, **kw)
     rho_init = np.asarray(rho_init, dtype=np.float64)
     f = W[None, :, None, None] * rho_init[:, None]
+    kind = "node" if shift == "constant" else shift
     if shift == "constant":
-        rh = np.broadcast_to(rho_init.mean(axis=(1, 2))[:, None, None], rho_init.shape).astype(np.float32)
+        fluid = np.ones(rho_init.shape[1:], bool) if mask is None else mask == 0
+        rh = np.broadcast_to(rho_init[:, fluid].mean(axis=1)[:, None, None], rho_init.shape).astype(np.float32)
     else:
         rh = to16(rho_init, fmt)
-    s = to16(f - _shifted_w(rh, "node" if shift == "constant" else shift), fmt)
+        _solid_zero(mask, rh)
+    _solid_zero(mask, f)
+    s = to16(f - _shifted_w(rh, kind), fmt)
     m = work
     for _ in range(steps):
-        # decode the pulled populations: s_i(x - c_i) + w_i rhohat
-        ps = pull(s).astype(m)
-        if shift == "node":
-            ref = pull(_shifted_w(rh, "node"))
-        else:
-            ref = _shifted_w(rh, "node")        # the pulling node's own rhohat
-        out, rho = collide(ps + ref.astype(m), G, work=m, **kw)
+        full = s.astype(m) + _shifted_w(rh, kind).astype(m)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            out, rho = collide(pull(full, mask).astype(m), G, work=m, mask=mask, **kw)
+        out = out.astype(m)
+        _solid_zero(mask, out, rho)
         if shift != "constant":
             rh = to16(rho, fmt)
-        s = to16(out.astype(m) - _shifted_w(rh, "node" if shift == "constant" else shift).astype(m), fmt)
-    return s.astype(np.float64) + _shifted_w(rh, "node" if shift == "constant" else shift)
+        s = to16(out - _shifted_w(rh, kind).astype(m), fmt)
+    return s.astype(np.float64) + _shifted_w(rh, kind)
 
 
 # ----------------------------------------------------------------------------
@@ -297,5 +313,5 @@ def run_case(job):
     mask, rho, kw = case_inputs(case)
     opts = dict(opts)
     if "fmt" in opts:
-        return run16(rho, steps, G, **opts)
+        return run16(rho, steps, G, mask=mask, **kw, **opts)
     return run(rho, steps, G, mask=mask, **kw, **opts)
