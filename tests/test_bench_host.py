@@ -87,3 +87,17 @@ def test_reference_line_has_the_native_config(monkeypatch, capsys):
     assert line["higher_is_better"] is True and line["steps"] == 4 and line["warmup"] == 3
     assert line["e2e"]["value"] == line["value"] and line["cpu_baseline"]["kind"] == "oracle"
     assert line["config"]["fluid_nodes"] == int((w.mask == 0).sum())
+
+
+def test_reference_arm_runs_on_rank_0_only(monkeypatch, capsys):
+    """Launched under torchrun with several ranks, only rank 0 times the
+    oracle and prints the line; the other ranks exit 0 without work."""
+    import argparse
+    b = load_bench()
+    called = []
+    monkeypatch.setattr(b, "oracle_all_cores", lambda *a: called.append(a) or (0.04, 2.5, 123))
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+    assert b.reference_arm(argparse.Namespace(steps=4, warmup=3)) == 0
+    assert called == [] and capsys.readouterr().out == ""
